@@ -1,0 +1,368 @@
+"""Benchmark of the coupled Eulerian-Lagrangian hot path on one B300.
+
+Workload (one "step" = one coupled step of Algorithm 1 over the whole batch):
+decaying 2-D turbulence on a 1024^2 grid (nu = 1e-4, dt = 5e-4), 1M passive
+tracers and 1M inertial particles at each of St = 0.1, 1, 10, all resident
+in HBM, interpolation scheme selectable (bilinear by default, the paper's
+production scheme).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--scheme bilinear|catmull_rom|bspline]
+                  [--impl ours|reference]
+
+Prints one JSON line.  `value` is particle-steps/s of the whole coupled step
+(fluid included), timed with CUDA events on the flow's stream, one event
+pair per step with an L2 flush (a 256 MiB write) before each step outside
+the event pair.  `--impl reference` times the FP64 CPU oracle instead.
+Under torchrun (N > 1) each rank runs an independent replica (weak scaling;
+the path has no exchange step) and rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_17836_b300 import inputs  # noqa: E402
+
+SCHEMES = {"bilinear": 0, "catmull_rom": 1, "bspline": 2}
+METRIC = "particle-steps/s (RK4+interp) & fluid steps/s at 1024^2; p50/p99 solve latency"
+SORT_EVERY = 20
+# Algorithmic bytes per particle-step of the RK4 kernel: state read + written
+# once (cell 4 B + offset 8 B, plus velocity 8 B for inertial particles).
+BYTES_TRACER = 2 * (4 + 8)
+BYTES_INERTIAL = 2 * (4 + 8 + 8)
+FLUSH_BYTES = 256 << 20
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2607_17836_b300/csrc/particles.cu", "paper_2607_17836_b300/csrc/interp.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(scheme_name):
+    """DRAM bytes per particle-step of the RK4 kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", f"k_rk4_{scheme_name}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as fh:
+        for line in fh:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_particle_step"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------------
+def cpu_oracle_rate(wl, scheme, budget_s=12.0, subsample=64, max_steps=40):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sample
+    of the workload: the full-grid fluid step plus every `subsample`-th
+    particle of each species; particle time is scaled back up to the full
+    counts.  Returns (particle-steps/s, fluid steps/s, cores, description)."""
+    import oracle
+    w0 = wl.omega0()
+    flow = oracle.Flow(wl.n, wl.nu, wl.dt, w0)
+    f = flow.fields(("u", "v"))
+    lvl = (f["u"], f["v"])
+    sets = []
+    for sp in wl.species:
+        xy = inputs.uniform_positions(sp.count, sp.seed)[::subsample]
+        x, y = xy[:, 0].copy(), xy[:, 1].copy()
+        vx = vy = None
+        if sp.st > 0:
+            vx = oracle.interp(lvl[0], scheme, x, y) if scheme != 2 else np.zeros_like(x)
+            vy = oracle.interp(lvl[1], scheme, x, y) if scheme != 2 else np.zeros_like(x)
+        sets.append((sp, x, y, vx, vy))
+    t_fluid = t_part = 0.0
+    steps = 0
+    t_start = time.perf_counter()
+    while steps < max_steps and (time.perf_counter() - t_start) < budget_s:
+        t0 = time.perf_counter()
+        flow.step(1)
+        f = flow.fields(("u", "v"))
+        un1, vn1 = f["u"], f["v"]
+        if scheme == 2:
+            a, b = oracle.bspline_prefilter(lvl[0]), oracle.bspline_prefilter(lvl[1])
+            c, d = oracle.bspline_prefilter(un1), oracle.bspline_prefilter(vn1)
+        else:
+            a, b, c, d = lvl[0], lvl[1], un1, vn1
+        t1 = time.perf_counter()
+        for sp, x, y, vx, vy in sets:
+            oracle.particles_rk4(scheme, wl.dt, sp.st, a, b, c, d, x, y, vx, vy)
+        t2 = time.perf_counter()
+        lvl = (un1, vn1)
+        t_fluid += t1 - t0
+        t_part += t2 - t1
+        steps += 1
+    per_step = t_fluid / steps + (t_part / steps) * subsample
+    ps = wl.particles / per_step
+    desc = (f"{steps} coupled steps of the {wl.n}^2 fluid solve plus every {subsample}th particle "
+            f"of each species ({sum(len(s[1]) for s in sets)} particles); particle time scaled "
+            f"x{subsample} to the full {wl.particles} particles")
+    return ps, steps / t_fluid, oracle.num_threads(), desc
+
+
+def run_reference(args, wl, scheme, world, rank):
+    if rank != 0:
+        return
+    ps, fluid_sps, cores, desc = cpu_oracle_rate(wl, scheme, budget_s=8.0, max_steps=40)
+    # --steps K --warmup W: W + K bounded samples, each one coupled step.
+    import oracle
+    rates = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(wl, scheme, budget_s=1.0, max_steps=1)
+    for _ in range(args.steps):
+        r, _, _, _ = cpu_oracle_rate(wl, scheme, budget_s=2.0, max_steps=2)
+        rates.append(r)
+    value = float(statistics.median(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wl.particles / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, args.scheme),
+            "fluid_steps_per_s": fluid_sps,
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl, scheme_name):
+    return {"workload": wl.name, "n": wl.n, "nu": wl.nu, "dt": wl.dt,
+            "species": [{"count": s.count, "st": s.st} for s in wl.species],
+            "particles": wl.particles, "scheme": scheme_name, "sort_every": SORT_EVERY,
+            "positions": "split precision: int32 image + cell index + fp32 offset",
+            "l2": "flushed (256 MiB write) before every timed step, outside the events",
+            "parallelism": "replicas (one independent simulation per GPU)"}
+
+
+def run_ours(args, wl, scheme, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2607_17836_b300 import elpath
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w0 = wl.omega0()
+    flow = elpath.Flow(wl.n, wl.nu, wl.dt, w0, interp=scheme, max_species=len(wl.species),
+                       max_particles=wl.particles, sort_every=SORT_EVERY, device=dev)
+    xys = [inputs.uniform_positions(s.count, s.seed + 1000 * rank) for s in wl.species]
+    for k, s in enumerate(wl.species):
+        flow.set_particles(k, xys[k], s.st)
+    stream = flow.stream
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        flow.step(1)
+    stream.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = flow.kernel_launches()
+    with ClockSampler(local) as clocks:
+        t_wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                starts[k].record(stream)
+                flow.step(1)
+                ends[k].record(stream)
+        stream.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    torch.cuda.synchronize(dev)
+    launches = flow.kernel_launches() - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # Per-stage times (direct launches with events between the stages).
+    prof = [flow.profile_step() for _ in range(min(args.steps, 20))]
+    fluid_ms = statistics.mean(p["fluid"] for p in prof)
+    spec_ms = [statistics.mean(p["species"][k] for p in prof) for k in range(len(wl.species))]
+    part_ms = float(sum(spec_ms))
+    bytes_part = sum(s.count * (BYTES_INERTIAL if s.st > 0 else BYTES_TRACER) for s in wl.species)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_part / (part_ms * 1e-3) / 1e9
+    traffic_pps = recorded_traffic(args.scheme)
+    traffic = traffic_pps * wl.particles / len(wl.species) if traffic_pps is not None else None
+
+    # End to end through the public API: particles from pinned host memory,
+    # K coupled steps, statistics and every particle state back to pinned memory.
+    pinned_in = [torch.from_numpy(xy).pin_memory() for xy in xys]
+    pinned_xy = [torch.empty((s.count, 2), dtype=torch.float64).pin_memory() for s in wl.species]
+    pinned_v = [torch.empty((s.count, 2), dtype=torch.float64).pin_memory() for s in wl.species]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k, s in enumerate(wl.species):
+        flow.set_particles(k, pinned_in[k].numpy(), s.st)
+    flow.step(args.steps)
+    st = flow.stats()
+    for k, s in enumerate(wl.species):
+        flow.particles_into(k, pinned_xy[k].numpy(), pinned_v[k].numpy() if s.st > 0 else None)
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(xy.nbytes for xy in xys)
+    d2h = sum(s.count * 16 * (2 if s.st > 0 else 1) for s in wl.species)
+    e2e_value = wl.particles * args.steps / e2e_s
+
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = wl.particles * args.steps * world / float(t.item())
+
+    if rank != 0:
+        return
+    value = wl.particles * args.steps * world / (total_ms * 1e-3)
+    srt = sorted(step_ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_of(wl, args.scheme),
+            "fluid_steps_per_s": 1e3 / fluid_ms,
+            "coupled_steps_per_s": 1e3 * args.steps / total_ms,
+            "latency_ms": {"p50": p50, "p99": p99, "what": "one coupled step, device time"},
+            "stage_ms": {"fluid": fluid_ms, "particles": spec_ms},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_rk4 (all species launches of one step)",
+                         "peak_kind": peak_kind,
+                         "bytes_per_particle_step": {"tracer": BYTES_TRACER,
+                                                     "inertial": BYTES_INERTIAL}},
+            "e2e": {"value": e2e_value, "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "what": "set_particles from pinned host + K steps + stats + particles back"},
+            "gpu_launches": launches, "wall_s": t_wall,
+            "clocks": clocks.summary(), "energy": st["energy"]}
+    if not args.no_cpu_baseline:
+        ps, fsps, cores, desc = cpu_oracle_rate(wl, scheme)
+        line["cpu_baseline"] = {"value": ps, "unit": "particle-steps/s", "cores": cores,
+                                "kind": "oracle", "sample": desc, "fluid_steps_per_s": fsps}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--scheme", default="bilinear", choices=sorted(SCHEMES))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    wl = inputs.decaying_turbulence_1024()
+    scheme = SCHEMES[args.scheme]
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, wl, scheme, world, rank)
+        else:
+            run_ours(args, wl, scheme, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * elpath.h -- C ABI of the B300 (sm_103a) one-way coupled Eulerian-Lagrangian
+ * particle library.
+ *
+ * The method is that of "A coupled Eulerian-Lagrangian approach for fluid
+ * and particle dynamics" (arxiv 2607.17836):
+ *   - a Fourier pseudospectral vorticity-streamfunction solver on the periodic
+ *     square [0, 2 pi)^2 advanced by second-order Adams-Bashforth
+ *     (Sec. 3.1, Eqs. 1, 4-10);
+ *   - passive tracers dx/dt = u(x, t) (Sec. 2.2, Eq. 2) and Stokes-drag
+ *     inertial particles dx/dt = v, dv/dt = (u(x, t) - v) / St (Sec. 2.3,
+ *     Eq. 3), both advanced by classical RK4 (Eqs. 12, 14);
+ *   - the fluid velocity at a particle from bilinear, Catmull-Rom or cubic
+ *     B-spline interpolation in space (Sec. 3.4, Eqs. 15-22) and linear
+ *     interpolation in time between two fluid levels (Eqs. 23-24);
+ *   - one coupled step = Algorithm 1: fluid n -> n+1, then every particle
+ *     by one RK4 step between levels n and n+1.
+ *
+ * Conventions (for every call):
+ *   - grid nodes x_i = i * 2 pi / n, arrays row-major [j][i] (y slow, x fast);
+ *   - host arrays are owned by the caller and copied in/out during the call;
+ *   - the device workspace is owned by the caller, must stay allocated until
+ *     el_destroy_flow returns, and must be at least el_workspace_bytes(desc)
+ *     bytes, 256-byte aligned; the library places every device array of the
+ *     flow inside it (cuFFT's plan-internal tables excepted);
+ *   - work is issued on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream); el_step_coupled returns without
+ *     waiting, every call that returns host data synchronises that stream;
+ *   - every call returns an el_status; a failed call leaves the flow as it
+ *     was, except EL_ECUDA / EL_ECUFFT, after which the flow should be
+ *     destroyed.  el_last_error gives a one-line reason.  No call exits,
+ *     throws across the ABI or traps on the device.
+ */
+#ifndef ELPATH_H
+#define ELPATH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct el_flow el_flow;
+
+typedef enum {
+    EL_OK = 0,
+    EL_EINVAL = 1,      /* bad argument (NULL, size, range, capacity)          */
+    EL_ENOMEM = 2,      /* workspace smaller than el_workspace_bytes(desc)      */
+    EL_ECUDA = 3,       /* a CUDA runtime call failed                          */
+    EL_ECUFFT = 4,      /* a cuFFT call failed                                 */
+    EL_ESTATE = 5,      /* call not valid in the flow's current state          */
+    EL_ENONFINITE = 6,  /* a NaN/Inf appeared in the fields or particle state  */
+    EL_ETIMEOUT = 7     /* a bounded device-side wait ran out                  */
+} el_status;
+
+typedef enum {
+    EL_BILINEAR = 0,     /* Eq. 16, 2 x 2 nodes                                 */
+    EL_CATMULL_ROM = 1,  /* Eqs. 18-19, 4 x 4 nodes i-1..i+2, periodic wrap     */
+    EL_BSPLINE = 2       /* Eqs. 21-22, 4 x 4 nodes, periodic wrap              */
+} el_interp;
+
+#define EL_MAX_SPECIES 8
+
+typedef struct {
+    int32_t n;                  /* grid points per side: power of two, 16..4096          */
+    int32_t interp;             /* el_interp                                             */
+    double nu;                  /* kinematic viscosity (1/Re of Eq. 1), >= 0             */
+    double dt;                  /* common fluid and particle step (Sec. 3.1), > 0        */
+    int32_t ab2_mode;           /* 0: viscous integrating factor (default);
+                                   1: Eq. 10 as printed, viscous term inside R           */
+    int32_t bspline_prefilter;  /* EL_BSPLINE only.  1: stencil weights act on
+                                   interpolating spline coefficients (default);
+                                   0: on raw samples, as Eq. 21 reads (approximating)    */
+    int32_t max_species;        /* 0..EL_MAX_SPECIES                                     */
+    int32_t sort_every;         /* re-bin particles by cell every k steps; 0 = never     */
+    int64_t max_particles;      /* capacity summed over all species                      */
+} el_flow_desc;
+
+/* Bytes of device workspace a flow with this description needs (0 if the
+ * description is invalid).  Cheap; usable for HBM admission control. */
+size_t el_workspace_bytes(const el_flow_desc* desc);
+
+/* Create a flow from the initial vorticity omega0 (host, n*n doubles, [j][i]).
+ * The field is projected (mean removed, 2/3 rule of Sec. 3.1 applied), its
+ * velocity reconstructed (Eqs. 5-6) and its nonlinear term evaluated, so that
+ * the first el_step_coupled can run.  cuFFT plans are made here, once
+ * (Sec. 3.1).  On success *out owns the flow; on failure *out is NULL. */
+el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* dev_workspace,
+                         size_t workspace_bytes, void* cuda_stream, el_flow** out);
+
+/* Place np particles in species slot `species` (0..max_species-1).
+ * st = 0: passive tracers (Eq. 2); st > 0: inertial particles (Eq. 3).
+ * xy: host, 2*np doubles (x0, y0, x1, y1, ...), any real value: positions are
+ * unwrapped and mapped periodically for field evaluation (Sec. 3.2).
+ * vxy: host, 2*np doubles of initial particle velocity, or NULL for zero slip
+ * (velocity = interpolated fluid velocity at the position, current level).
+ * Re-placing a slot replaces its particles; the positions passed become the
+ * reference x(0) of the mean-square displacement.  Synchronises the stream. */
+el_status el_set_particles(el_flow* flow, int32_t species, int64_t np, double st,
+                           const double* xy, const double* vxy);
+
+/* Advance nsteps coupled steps (Algorithm 1), asynchronously on the stream. */
+el_status el_step_coupled(el_flow* flow, int32_t nsteps);
+
+typedef struct {
+    double t;                         /* simulated time                                 */
+    int64_t step;                     /* steps taken                                    */
+    double energy;                    /* E = 1/2 <u^2 + v^2>                            */
+    double enstrophy;                 /* Z = 1/2 <omega^2>                              */
+    double palinstrophy;              /* P = 1/2 <|grad omega|^2>                       */
+    double msd[EL_MAX_SPECIES][2];    /* <(x - x0)^2>, <(y - y0)^2>, unwrapped          */
+    double cluster[EL_MAX_SPECIES];   /* Var(n)/mean(n) - 1 on a 64 x 64 box grid       */
+    int64_t np[EL_MAX_SPECIES];       /* particles per species (0 = empty slot)         */
+    int32_t finite;                   /* 1 if every reduced quantity is finite          */
+} el_stats;
+
+/* Diagnostics of the current state, reduced in FP64 in a fixed order (the
+ * same inputs give the same bits).  Synchronises the stream.  Returns
+ * EL_ENONFINITE (with *out filled) if a NaN/Inf was found. */
+el_status el_get_stats(el_flow* flow, el_stats* out);
+
+/* Particles of one species in their original order: unwrapped positions
+ * (2*np doubles) and velocities (2*np doubles; the fluid-following
+ * velocity is not stored for tracers, so vxy is zero-filled for st = 0).
+ * Either pointer may be NULL.  Synchronises the stream. */
+el_status el_get_particles(el_flow* flow, int32_t species, double* xy, double* vxy);
+
+/* One field of the current level into host memory (n*n doubles):
+ * 0 = vorticity, 1 = u, 2 = v, 3/4 = the u/v node values the particle
+ * stencil weights (the spline coefficients when prefiltering, else u/v).
+ * Synchronises the stream. */
+el_status el_get_field(el_flow* flow, int32_t which, double* host_nn);
+
+/* Fluid velocity at np arbitrary points by the flow's interpolant, blended
+ * linearly in time between the previous (theta = 0) and the current level
+ * (theta = 1): exactly the gather the particle step uses.  d_xy and d_uv are
+ * DEVICE arrays of 2*np doubles.  Asynchronous on the stream. */
+el_status el_sample_velocity(el_flow* flow, int64_t np, const double* d_xy, double theta,
+                             double* d_uv);
+
+/* Run ONE coupled step exactly as el_step_coupled does (re-binning first
+ * if it is due), but by direct launches with CUDA events on the flow's
+ * stream around each stage, then synchronise and report the stage times:
+ * stage_ms[0] = fluid step (Sec. 3.1), stage_ms[1 + s] = RK4 step of
+ * species s (0 for an empty slot), stage_ms[1 + max_species] = re-binning
+ * (0 if not due).  nstage must be >= 2 + max_species. */
+el_status el_profile_step(el_flow* flow, double* stage_ms, int32_t nstage);
+
+/* Number of kernel launches of the library (not cuFFT) issued so far by
+ * this flow; lets a caller count the launches inside a timed region. */
+int64_t el_kernel_launches(const el_flow* flow);
+
+/* Destroy the flow (plans, graphs, host state).  The workspace is the
+ * caller's to free afterwards. */
+el_status el_destroy_flow(el_flow* flow);
+
+/* One-line reason for the last failure of a call on this flow (or of the
+ * last el_create_flow when flow is NULL).  Never NULL. */
+const char* el_last_error(const el_flow* flow);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELPATH_H */

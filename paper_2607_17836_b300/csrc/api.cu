@@ -1,0 +1,495 @@
+// The C ABI of include/elpath.h: argument checks, the workspace layout,
+// cuFFT plans, the captured step graph and the coupled step of Algorithm 1.
+#include "common.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <new>
+#include <utility>
+#include <vector>
+
+namespace el {
+
+void fluid_tables(const el_flow_desc& d, std::vector<double>& ex, std::vector<double>& ey,
+                  std::vector<float>& px, std::vector<float>& py);
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+const char* check_desc(const el_flow_desc* d) {
+    if (!d) return "desc is NULL";
+    if (!is_pow2(d->n) || d->n < 16 || d->n > 4096) return "n must be a power of two in [16, 4096]";
+    if (d->interp < 0 || d->interp > 2) return "interp must be 0, 1 or 2";
+    if (!std::isfinite(d->nu) || d->nu < 0.0) return "nu must be finite and >= 0";
+    if (!std::isfinite(d->dt) || d->dt <= 0.0) return "dt must be finite and > 0";
+    if (d->ab2_mode != 0 && d->ab2_mode != 1) return "ab2_mode must be 0 or 1";
+    if (d->bspline_prefilter != 0 && d->bspline_prefilter != 1) return "bspline_prefilter must be 0 or 1";
+    if (d->max_species < 0 || d->max_species > EL_MAX_SPECIES) return "max_species out of range";
+    if (d->max_particles < 0 || d->max_particles > ((int64_t)1 << 31)) return "max_particles out of range";
+    if (d->max_particles > 0 && d->max_species == 0) return "max_particles > 0 needs max_species > 0";
+    if (d->sort_every < 0) return "sort_every must be >= 0";
+    return nullptr;
+}
+
+int planes_of(const el_flow_desc& d) {
+    return (d.interp == EL_BSPLINE && d.bspline_prefilter) ? 6 : 4;
+}
+
+// Bytes one species of np particles takes from the pool: 12 arrays, each
+// 256-byte aligned.  The sort block (index 1 of each pair) is carved as one
+// contiguous run of at least 32 * np bytes, which also serves as staging.
+size_t species_bytes(int64_t np) {
+    size_t n = (size_t)np;
+    size_t a = align_up(n * 4) + align_up(n * 8) + align_up(n * 8) + align_up(n * 8) + align_up(n * 4);
+    return 2 * a + align_up(n * 16) + align_up(n * 4);
+}
+
+// cuFFT work-area bytes for (n, planes), cached.
+std::mutex g_fft_mutex;
+std::map<std::pair<int, int>, size_t> g_fft_bytes;
+
+cufftResult make_plans(int n, int planes, cufftHandle* c2r, cufftHandle* r2c, cufftHandle* c2r1,
+                       size_t* work) {
+    int dims[2] = {n, n};
+    size_t w0 = 0, w1 = 0, w2 = 0;
+    cufftResult r;
+    *c2r = *r2c = *c2r1 = 0;
+    if ((r = cufftCreate(c2r)) != CUFFT_SUCCESS) return r;
+    if ((r = cufftCreate(r2c)) != CUFFT_SUCCESS) return r;
+    if ((r = cufftCreate(c2r1)) != CUFFT_SUCCESS) return r;
+    cufftSetAutoAllocation(*c2r, 0);
+    cufftSetAutoAllocation(*r2c, 0);
+    cufftSetAutoAllocation(*c2r1, 0);
+    if ((r = cufftMakePlanMany(*c2r, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, planes, &w0)) !=
+        CUFFT_SUCCESS)
+        return r;
+    if ((r = cufftMakePlanMany(*r2c, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, &w1)) !=
+        CUFFT_SUCCESS)
+        return r;
+    if ((r = cufftMakePlanMany(*c2r1, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1, &w2)) !=
+        CUFFT_SUCCESS)
+        return r;
+    *work = std::max(w0, std::max(w1, w2));
+    return CUFFT_SUCCESS;
+}
+
+void destroy_plans(cufftHandle a, cufftHandle b, cufftHandle c) {
+    if (a) cufftDestroy(a);
+    if (b) cufftDestroy(b);
+    if (c) cufftDestroy(c);
+}
+
+bool fft_work_bytes(int n, int planes, size_t* out) {
+    std::lock_guard<std::mutex> g(g_fft_mutex);
+    auto key = std::make_pair(n, planes);
+    auto it = g_fft_bytes.find(key);
+    if (it != g_fft_bytes.end()) {
+        *out = it->second;
+        return true;
+    }
+    cufftHandle a, b, c;
+    size_t w = 0;
+    cufftResult r = make_plans(n, planes, &a, &b, &c, &w);
+    destroy_plans(a, b, c);
+    if (r != CUFFT_SUCCESS) return false;
+    g_fft_bytes[key] = w;
+    *out = w;
+    return true;
+}
+
+// The workspace layout.  With base == nullptr only the size is computed.
+size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
+    size_t cur = 0;
+    auto take = [&](size_t bytes) -> char* {
+        size_t o = align_up(cur);
+        cur = o + bytes;
+        return base ? base + o : nullptr;
+    };
+    size_t n = (size_t)d.n, nh = n / 2 + 1, n2 = n * n, nm = n * nh;
+    int planes = planes_of(d);
+    char* what = take(nm * 8);
+    char* hist = take(nm * 8);
+    char* nhat = take(nm * 8);
+    char* spec = take((size_t)planes * nm * 8);
+    char* phys = take((size_t)planes * n2 * 4);
+    char* nl = take(n2 * 4);
+    char* snap = take(n2 * 16);
+    char* aux_spec = take(nm * 8);
+    char* aux_phys = take(n2 * 4);
+    char* stage64 = take(n2 * 8);
+    char* ex = take(nh * 8);
+    char* ey = take(n * 8);
+    char* px = take(nh * 4);
+    char* py = take(n * 4);
+    char* dstep = take(8);
+    char* red = take((size_t)kRedBlocks * 3 * 8);
+    char* red_out = take(64 * 8);
+    char* boxes = take((size_t)kBoxes * kBoxes * 8);
+    bool parts = d.max_particles > 0;
+    char* bins = parts ? take(n2 * 4) : nullptr;
+    char* bin_sums = parts ? take((4096 + 64) * 4) : nullptr;
+    char* fft = take(fft_bytes);
+    size_t pool_bytes = parts ? species_bytes(d.max_particles) + (size_t)d.max_species * 12 * kAlign : 0;
+    char* pool = take(pool_bytes);
+    if (f) {
+        f->what = (float2*)what;
+        f->hist = (float2*)hist;
+        f->nhat = (float2*)nhat;
+        f->spec = (float2*)spec;
+        f->phys = (float*)phys;
+        f->nl = (float*)nl;
+        f->snap = (float4*)snap;
+        f->aux_spec = (float2*)aux_spec;
+        f->aux_phys = (float*)aux_phys;
+        f->stage64 = (double*)stage64;
+        f->ex = (double*)ex;
+        f->ey = (double*)ey;
+        f->pre_x = (float*)px;
+        f->pre_y = (float*)py;
+        f->d_step = (int64_t*)dstep;
+        f->red = (double*)red;
+        f->red_out = (double*)red_out;
+        f->boxes = (unsigned long long*)boxes;
+        f->bins = (uint32_t*)bins;
+        f->bin_sums = (uint32_t*)bin_sums;
+        f->fft_work = fft;
+        f->pool = pool;
+        f->pool_bytes = pool_bytes;
+        f->pool_used = 0;
+    }
+    return align_up(cur);
+}
+
+// Give species slot s room for np particles from the pool.
+bool carve_species(el_flow* f, Species& sp, int64_t np) {
+    if (np <= sp.cap) return true;
+    size_t need = species_bytes(np);
+    size_t start = align_up(f->pool_used);
+    if (start + need > f->pool_bytes) return false;
+    char* base = f->pool + start;
+    size_t cur = 0;
+    auto take = [&](size_t bytes) -> char* {
+        size_t o = align_up(cur);
+        cur = o + bytes;
+        return base + o;
+    };
+    size_t n = (size_t)np;
+    for (int k = 0; k < 2; k++) {
+        sp.cell[k] = (uint32_t*)take(n * 4);
+        sp.off[k] = (float2*)take(n * 8);
+        sp.vel[k] = (float2*)take(n * 8);
+        sp.img[k] = (int2*)take(n * 8);
+        sp.id[k] = (uint32_t*)take(n * 4);
+    }
+    sp.x0 = (double2*)take(n * 16);
+    sp.rank = (uint32_t*)take(n * 4);
+    f->pool_used = start + align_up(cur);
+    sp.cap = np;
+    return true;
+}
+
+// One coupled step (Algorithm 1): fluid n -> n+1, every species by RK4
+// between levels n and n+1, then the device step counter.
+el_status step_body(el_flow* f) {
+    EL_TRY(fluid_step(f));
+    for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_step(f, s));
+    EL_TRY(step_increment(f));
+    return EL_OK;
+}
+
+el_status build_graph(el_flow* f) {
+    if (f->graph) {
+        cudaGraphExecDestroy(f->graph);
+        f->graph = nullptr;
+    }
+    f->graph_valid = false;
+    int64_t before = f->launches;
+    cudaGraph_t g = nullptr;
+    EL_CUDA_OK(f, cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal));
+    el_status s = step_body(f);
+    cudaError_t e = cudaStreamEndCapture(f->stream, &g);
+    if (s != EL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(f, EL_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&f->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(f, EL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    f->graph_kernels = f->launches - before;
+    f->launches = before;  // nothing ran yet; replays add graph_kernels each
+    f->graph_valid = true;
+    return EL_OK;
+}
+
+}  // namespace
+
+el_status fail(el_flow* f, el_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (f)
+        f->err = buf;
+    else
+        g_create_error = buf;
+    return s;
+}
+
+}  // namespace el
+
+using namespace el;
+
+extern "C" {
+
+size_t el_workspace_bytes(const el_flow_desc* desc) {
+    if (check_desc(desc)) return 0;
+    size_t fft = 0;
+    if (!fft_work_bytes(desc->n, planes_of(*desc), &fft)) return 0;
+    return carve(*desc, fft, nullptr, nullptr);
+}
+
+el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* dev_workspace,
+                         size_t workspace_bytes, void* cuda_stream, el_flow** out) {
+    if (!out) return fail(nullptr, EL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (const char* why = check_desc(desc)) return fail(nullptr, EL_EINVAL, "%s", why);
+    if (!omega0) return fail(nullptr, EL_EINVAL, "omega0 is NULL");
+    if (!dev_workspace) return fail(nullptr, EL_EINVAL, "workspace is NULL");
+    if ((uintptr_t)dev_workspace % kAlign) return fail(nullptr, EL_EINVAL, "workspace not 256-byte aligned");
+    for (size_t q = 0, nn = (size_t)desc->n * desc->n; q < nn; q++)
+        if (!std::isfinite(omega0[q])) return fail(nullptr, EL_EINVAL, "omega0 has a non-finite value");
+    size_t fft = 0;
+    if (!fft_work_bytes(desc->n, planes_of(*desc), &fft))
+        return fail(nullptr, EL_ECUFFT, "cuFFT plan creation failed for n=%d", desc->n);
+    size_t need = carve(*desc, fft, nullptr, nullptr);
+    if (workspace_bytes < need)
+        return fail(nullptr, EL_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, need);
+
+    el_flow* f = new (std::nothrow) el_flow();
+    if (!f) return fail(nullptr, EL_ENOMEM, "host allocation failed");
+    f->d = *desc;
+    f->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&f->device);
+    f->n = desc->n;
+    f->nh = desc->n / 2 + 1;
+    f->log2n = 0;
+    while ((1 << f->log2n) < f->n) f->log2n++;
+    f->n2 = (size_t)f->n * f->n;
+    f->nmodes = (size_t)f->n * f->nh;
+    f->nplanes = planes_of(*desc);
+    f->stencil_plane = f->nplanes == 6 ? 4 : 0;
+    f->ws = (char*)dev_workspace;
+    f->ws_bytes = workspace_bytes;
+    carve(*desc, fft, f, f->ws);
+
+    auto bail = [&](el_status s) {
+        g_create_error = f->err;
+        destroy_plans(f->plan_c2r, f->plan_r2c, f->plan_c2r1);
+        delete f;
+        return s;
+    };
+    size_t w = 0;
+    cufftResult r = make_plans(f->n, f->nplanes, &f->plan_c2r, &f->plan_r2c, &f->plan_c2r1, &w);
+    if (r != CUFFT_SUCCESS || w > fft) {
+        fail(f, EL_ECUFFT, "cuFFT plan creation failed (%d)", (int)r);
+        return bail(EL_ECUFFT);
+    }
+    cufftHandle plans[3] = {f->plan_c2r, f->plan_r2c, f->plan_c2r1};
+    for (cufftHandle p : plans) {
+        if (cufftSetWorkArea(p, f->fft_work) != CUFFT_SUCCESS || cufftSetStream(p, f->stream) != CUFFT_SUCCESS) {
+            fail(f, EL_ECUFFT, "cuFFT work area / stream binding failed");
+            return bail(EL_ECUFFT);
+        }
+    }
+    f->plans_made = true;
+
+    std::vector<double> ex, ey;
+    std::vector<float> px, py;
+    fluid_tables(*desc, ex, ey, px, py);
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMemcpyAsync(f->ex, ex.data(), ex.size() * 8, cudaMemcpyHostToDevice, f->stream);
+    e = e ? e : cudaMemcpyAsync(f->ey, ey.data(), ey.size() * 8, cudaMemcpyHostToDevice, f->stream);
+    e = e ? e : cudaMemcpyAsync(f->pre_x, px.data(), px.size() * 4, cudaMemcpyHostToDevice, f->stream);
+    e = e ? e : cudaMemcpyAsync(f->pre_y, py.data(), py.size() * 4, cudaMemcpyHostToDevice, f->stream);
+    if (e != cudaSuccess) {
+        fail(f, EL_ECUDA, "table upload: %s", cudaGetErrorString(e));
+        return bail(EL_ECUDA);
+    }
+    el_status s = fluid_init(f, omega0);
+    if (s != EL_OK) return bail(s);
+    e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) {
+        fail(f, EL_ECUDA, "create: %s", cudaGetErrorString(e));
+        return bail(EL_ECUDA);
+    }
+    *out = f;
+    return EL_OK;
+}
+
+el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, const double* xy,
+                           const double* vxy) {
+    if (!f) return EL_EINVAL;
+    if (species < 0 || species >= f->d.max_species)
+        return fail(f, EL_EINVAL, "species %d outside [0, %d)", species, f->d.max_species);
+    if (np < 0 || np > f->d.max_particles) return fail(f, EL_EINVAL, "np %lld out of range", (long long)np);
+    if (!std::isfinite(st) || st < 0.0) return fail(f, EL_EINVAL, "st must be finite and >= 0");
+    if (np > 0 && !xy) return fail(f, EL_EINVAL, "xy is NULL");
+    for (int64_t q = 0; q < 2 * np; q++)
+        if (!std::isfinite(xy[q]) || std::fabs(xy[q]) > 1e9)
+            return fail(f, EL_EINVAL, "xy[%lld] is not finite or beyond 1e9", (long long)q);
+    if (vxy && st > 0.0)
+        for (int64_t q = 0; q < 2 * np; q++)
+            if (!std::isfinite(vxy[q])) return fail(f, EL_EINVAL, "vxy[%lld] is not finite", (long long)q);
+    Species& sp = f->sp[species];
+    if (!carve_species(f, sp, np))
+        return fail(f, EL_EINVAL, "particle capacity exhausted (max_particles=%lld)",
+                    (long long)f->d.max_particles);
+    EL_TRY(particles_set(f, species, np, st, xy, vxy));
+    f->graph_valid = false;
+    return EL_OK;
+}
+
+el_status el_step_coupled(el_flow* f, int32_t nsteps) {
+    if (!f) return EL_EINVAL;
+    if (nsteps < 0) return fail(f, EL_EINVAL, "nsteps < 0");
+    static const bool no_graph = std::getenv("ELPATH_NO_GRAPH") != nullptr;
+    bool use_graph = f->stream != nullptr && !no_graph;
+    for (int32_t k = 0; k < nsteps; k++) {
+        if (f->d.sort_every > 0 && f->since_sort >= f->d.sort_every) {
+            for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_sort(f, s));
+            f->since_sort = 0;
+        }
+        if (use_graph) {
+            if (!f->graph_valid) EL_TRY(build_graph(f));
+            EL_CUDA_OK(f, cudaGraphLaunch(f->graph, f->stream));
+            f->launches += f->graph_kernels;
+        } else {
+            EL_TRY(step_body(f));
+        }
+        f->step++;
+        f->since_sort++;
+    }
+    return EL_OK;
+}
+
+el_status el_get_stats(el_flow* f, el_stats* out) {
+    if (!f || !out) return EL_EINVAL;
+    EL_TRY(fluid_diagnostics(f));
+    int ns = f->d.max_species;
+    for (int s = 0; s < ns; s++)
+        if (f->sp[s].np > 0) EL_TRY(particles_stats_into(f, s, f->red_out + 3 + 3 * s));
+    double host[3 + 3 * EL_MAX_SPECIES] = {0};
+    EL_CUDA_OK(f, cudaMemcpyAsync(host, f->red_out, sizeof(double) * (3 + 3 * ns), cudaMemcpyDeviceToHost,
+                                  f->stream));
+    EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
+    *out = el_stats{};
+    out->t = (double)f->step * f->d.dt;
+    out->step = f->step;
+    out->energy = host[0];
+    out->enstrophy = host[1];
+    out->palinstrophy = host[2];
+    bool finite = std::isfinite(host[0]) && std::isfinite(host[1]) && std::isfinite(host[2]);
+    for (int s = 0; s < ns; s++) {
+        out->np[s] = f->sp[s].np;
+        if (f->sp[s].np == 0) continue;
+        out->msd[s][0] = host[3 + 3 * s];
+        out->msd[s][1] = host[4 + 3 * s];
+        out->cluster[s] = host[5 + 3 * s];
+        finite = finite && std::isfinite(host[3 + 3 * s]) && std::isfinite(host[4 + 3 * s]);
+    }
+    out->finite = finite ? 1 : 0;
+    if (!finite) return fail(f, EL_ENONFINITE, "non-finite diagnostics at step %lld", (long long)f->step);
+    return EL_OK;
+}
+
+el_status el_get_particles(el_flow* f, int32_t species, double* xy, double* vxy) {
+    if (!f) return EL_EINVAL;
+    if (species < 0 || species >= f->d.max_species)
+        return fail(f, EL_EINVAL, "species %d outside [0, %d)", species, f->d.max_species);
+    return particles_get(f, species, xy, vxy);
+}
+
+el_status el_get_field(el_flow* f, int32_t which, double* host_nn) {
+    if (!f || !host_nn) return EL_EINVAL;
+    if (which < 0 || which > 4) return fail(f, EL_EINVAL, "which must be 0..4");
+    return fluid_get_field(f, which, host_nn);
+}
+
+el_status el_sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv) {
+    if (!f) return EL_EINVAL;
+    if (np < 0 || (np > 0 && (!d_xy || !d_uv))) return fail(f, EL_EINVAL, "bad sample arrays");
+    if (!(theta >= 0.0 && theta <= 1.0)) return fail(f, EL_EINVAL, "theta must be in [0, 1]");
+    return sample_velocity(f, np, d_xy, theta, d_uv);
+}
+
+el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
+    if (!f || !stage_ms) return EL_EINVAL;
+    int ns = f->d.max_species;
+    if (nstage < 2 + ns) return fail(f, EL_EINVAL, "nstage must be >= %d", 2 + ns);
+    cudaEvent_t ev[2 + EL_MAX_SPECIES + 2];
+    int nev = ns + 4;
+    for (int k = 0; k < nev; k++) EL_CUDA_OK(f, cudaEventCreate(&ev[k]));
+    el_status st = EL_OK;
+    bool sorted = false;
+    auto rec = [&](int k) { cudaEventRecord(ev[k], f->stream); };
+    rec(0);
+    if (f->d.sort_every > 0 && f->since_sort >= f->d.sort_every) {
+        for (int s = 0; s < ns && st == EL_OK; s++) st = particles_sort(f, s);
+        f->since_sort = 0;
+        sorted = true;
+    }
+    rec(1);
+    if (st == EL_OK) st = fluid_step(f);
+    rec(2);
+    for (int s = 0; s < ns && st == EL_OK; s++) {
+        st = particles_step(f, s);
+        rec(3 + s);
+    }
+    if (st == EL_OK) st = step_increment(f);
+    cudaError_t e = cudaStreamSynchronize(f->stream);
+    if (st == EL_OK && e != cudaSuccess) st = fail(f, EL_ECUDA, "profile: %s", cudaGetErrorString(e));
+    if (st == EL_OK) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[1], ev[2]);
+        stage_ms[0] = ms;
+        for (int s = 0; s < ns; s++) {
+            cudaEventElapsedTime(&ms, ev[2 + s], ev[3 + s]);
+            stage_ms[1 + s] = f->sp[s].np > 0 ? ms : 0.0;
+        }
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        stage_ms[1 + ns] = sorted ? ms : 0.0;
+        f->step++;
+        f->since_sort++;
+    }
+    for (int k = 0; k < nev; k++) cudaEventDestroy(ev[k]);
+    return st;
+}
+
+int64_t el_kernel_launches(const el_flow* f) { return f ? f->launches : 0; }
+
+el_status el_destroy_flow(el_flow* f) {
+    if (!f) return EL_EINVAL;
+    cudaStreamSynchronize(f->stream);
+    if (f->graph) cudaGraphExecDestroy(f->graph);
+    destroy_plans(f->plan_c2r, f->plan_r2c, f->plan_c2r1);
+    delete f;
+    return EL_OK;
+}
+
+const char* el_last_error(const el_flow* f) {
+    if (!f) return g_create_error.c_str();
+    return f->err.c_str();
+}
+
+}  // extern "C"

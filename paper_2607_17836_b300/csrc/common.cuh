@@ -1,0 +1,152 @@
+// Internal declarations shared by the translation units of libelpath.so.
+// Nothing here is part of the public ABI (include/elpath.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/elpath.h"
+
+namespace el {
+
+constexpr int kMaxSpecies = EL_MAX_SPECIES;
+constexpr int kBoxes = 64;          // clustering-index box grid (kBoxes x kBoxes)
+constexpr int kRedBlocks = 512;     // fixed grid of the FP64 reductions (fixed order)
+constexpr int kRedThreads = 256;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// One particle species.  Structure-of-arrays, current buffers [0] and sort
+// buffers [1] (the sort scatters [0] -> [1] and copies back, so the pointers
+// the step kernels see never change).
+struct Species {
+    int64_t np = 0;
+    int64_t cap = 0;
+    double st = 0.0;
+    uint32_t* cell[2] = {nullptr, nullptr};  // i | j << 16
+    float2* off[2] = {nullptr, nullptr};     // in-cell offset, [0, 1)^2
+    float2* vel[2] = {nullptr, nullptr};     // particle velocity (inertial only)
+    int2* img[2] = {nullptr, nullptr};       // periodic image count per axis
+    uint32_t* id[2] = {nullptr, nullptr};    // original index
+    double2* x0 = nullptr;                   // reference position, indexed by id
+    uint32_t* rank = nullptr;                // sort scratch
+};
+
+}  // namespace el
+
+struct el_flow {
+    el_flow_desc d{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    // geometry
+    int n = 0, nh = 0, log2n = 0;
+    size_t n2 = 0, nmodes = 0;
+    int nplanes = 4;         // 4: u, v, wx, wy; 6: + prefiltered cu, cv
+    int stencil_plane = 0;   // plane holding the u the particle stencil weights
+
+    // workspace carve-out
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+
+    // fluid state (device)
+    float2* what = nullptr;   // omega-hat, half spectrum [ky][kx], n x (n/2+1)
+    float2* hist = nullptr;   // AB2 history
+    float2* nhat = nullptr;   // nonlinear term of the latest level
+    float2* spec = nullptr;   // nplanes half spectra (C2R input)
+    float* phys = nullptr;    // nplanes physical planes (C2R output)
+    float* nl = nullptr;      // physical nonlinear term (R2C input)
+    float4* snap = nullptr;   // (u_a, v_a, u_b, v_b) per node: two time levels
+    float2* aux_spec = nullptr;
+    float* aux_phys = nullptr;
+    double* stage64 = nullptr;  // n^2 doubles: host <-> device field staging
+    double* ex = nullptr;     // exp(-nu kx^2 dt), kx = 0..n/2
+    double* ey = nullptr;     // exp(-nu ky^2 dt), row index 0..n-1
+    float* pre_x = nullptr;   // spline prefilter 3/(2 + cos(k dx)) per kx
+    float* pre_y = nullptr;   // ... per row index
+    int64_t* d_step = nullptr;
+    double* red = nullptr;        // reduction partials
+    double* red_out = nullptr;    // reduced scalars (device)
+    unsigned long long* boxes = nullptr;  // kBoxes^2 counters
+    uint32_t* bins = nullptr;     // n^2 sort bins
+    uint32_t* bin_sums = nullptr; // scan block sums
+    void* fft_work = nullptr;
+    char* pool = nullptr;         // particle pool
+    size_t pool_bytes = 0, pool_used = 0;
+
+    cufftHandle plan_c2r = 0, plan_r2c = 0, plan_c2r1 = 0;
+    bool plans_made = false;
+
+    el::Species sp[el::kMaxSpecies];
+
+    int64_t step = 0;          // host mirror of *d_step
+    int64_t since_sort = 0;
+    int64_t launches = 0;
+
+    // captured step graph
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_kernels = 0;
+    bool graph_valid = false;
+
+    std::string err;
+};
+
+namespace el {
+
+// ---- launch helpers -------------------------------------------------------
+inline unsigned blocks_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+el_status fail(el_flow* f, el_status s, const char* fmt, ...);
+
+#define EL_CUDA_OK(f, call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return ::el::fail((f), EL_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                              __FILE__, __LINE__);                                       \
+    } while (0)
+
+#define EL_LAUNCHED(f)                                                                   \
+    do {                                                                                 \
+        (f)->launches++;                                                                 \
+        cudaError_t e_ = cudaGetLastError();                                             \
+        if (e_ != cudaSuccess)                                                           \
+            return ::el::fail((f), EL_ECUDA, "kernel launch: %s (%s:%d)",                \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);               \
+    } while (0)
+
+#define EL_TRY(call)                      \
+    do {                                  \
+        el_status s_ = (call);            \
+        if (s_ != EL_OK) return s_;       \
+    } while (0)
+
+// ---- fluid (fluid.cu) -------------------------------------------------------
+el_status fluid_init(el_flow* f, const double* omega0_host);
+el_status fluid_step(el_flow* f);                 // K5, K1, C2R, K3, R2C
+el_status fluid_diagnostics(el_flow* f);          // E, Z, P -> red_out[0..2]
+el_status fluid_get_field(el_flow* f, int which, double* host_nn);
+el_status step_increment(el_flow* f);
+
+// ---- particles (particles.cu) ---------------------------------------------------
+el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
+                        const double* vxy);
+el_status particles_step(el_flow* f, int s);      // K6
+el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
+el_status particles_stats_into(el_flow* f, int s, double* out3);  // msd x, msd y, cluster
+el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv);
+
+// ---- sort (sort.cu) -------------------------------------------------------------
+el_status particles_sort(el_flow* f, int s);      // K7
+
+// ---- reductions (reduce.cu) ---------------------------------------------------------
+// Means of `count` consecutive double2 values, summed in a fixed order, into out2 (device).
+el_status reduce_double2(el_flow* f, const double2* in, int64_t count, double* out2);
+
+}  // namespace el

@@ -1,0 +1,91 @@
+// Device-side spatial + temporal interpolation of the fluid velocity
+// (Sec. 3.4, Eqs. 15-24), shared by the particle step and the sampling hook.
+//
+// The field is the snapshot pair: per node a float4 (u_a, v_a, u_b, v_b)
+// holding two time levels, so one 16-byte load fetches both.  A node's value
+// at a stage is wa * (u_a, v_a) + wb * (u_b, v_b) (Eq. 23); the caller picks
+// (wa, wb) from theta and from which half holds level n.  Blending the nodes
+// before the spatial weights is the same linear map as Eq. 23 applied to the
+// two spatially interpolated values.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace el {
+
+// Catmull-Rom weights (Eq. 19), nodes i-1, i, i+1, i+2.
+__device__ __forceinline__ void weights_catmull_rom(float s, float w[4]) {
+    w[0] = s * fmaf(s, fmaf(-0.5f, s, 1.0f), -0.5f);
+    w[1] = fmaf(s * s, fmaf(1.5f, s, -2.5f), 1.0f);
+    w[2] = s * fmaf(s, fmaf(-1.5f, s, 2.0f), 0.5f);
+    w[3] = s * s * fmaf(0.5f, s, -0.5f);
+}
+
+// Cubic B-spline weights (Eq. 22), nodes i-1, i, i+1, i+2.
+__device__ __forceinline__ void weights_bspline(float s, float w[4]) {
+    float r = 1.0f - s;
+    w[0] = r * r * r * (1.0f / 6.0f);
+    w[1] = fmaf(s * s, fmaf(0.5f, s, -1.0f), 2.0f / 3.0f);
+    w[2] = fmaf(s, fmaf(s, fmaf(-0.5f, s, 0.5f), 0.5f), 1.0f / 6.0f);
+    w[3] = s * s * s * (1.0f / 6.0f);
+}
+
+__device__ __forceinline__ float4 node_ld(const float4* __restrict__ snap, int idx) {
+    return __ldg(snap + idx);
+}
+
+// Velocity at grid-unit position (ci + lx, cj + ly), lx, ly any small reals:
+// the containing cell is (ci + floor(lx), cj + floor(ly)) wrapped
+// periodically (n a power of two), the offsets lx - floor(lx), ly - floor(ly).
+// SCHEME: 0 bilinear (Eq. 16), 1 Catmull-Rom (Eq. 18), 2 B-spline (Eq. 21).
+template <int SCHEME>
+__device__ __forceinline__ float2 fluid_at(const float4* __restrict__ snap, int n, int ci, int cj,
+                                           float lx, float ly, float wa, float wb) {
+    const int m = n - 1;
+    float flx = floorf(lx), fly = floorf(ly);
+    int i = ci + (int)flx, j = cj + (int)fly;
+    float sx = lx - flx, sy = ly - fly;
+    if (SCHEME == 0) {
+        int i0 = i & m, i1 = (i + 1) & m;
+        int r0 = (j & m) * n, r1 = ((j + 1) & m) * n;
+        float4 a = node_ld(snap, r0 + i0), b = node_ld(snap, r0 + i1);
+        float4 c = node_ld(snap, r1 + i0), d = node_ld(snap, r1 + i1);
+        float au = fmaf(wa, a.x, wb * a.z), av = fmaf(wa, a.y, wb * a.w);
+        float bu = fmaf(wa, b.x, wb * b.z), bv = fmaf(wa, b.y, wb * b.w);
+        float cu = fmaf(wa, c.x, wb * c.z), cv = fmaf(wa, c.y, wb * c.w);
+        float du = fmaf(wa, d.x, wb * d.z), dv = fmaf(wa, d.y, wb * d.w);
+        // Eq. 16 as two lerps per axis
+        float lo_u = fmaf(sx, bu - au, au), hi_u = fmaf(sx, du - cu, cu);
+        float lo_v = fmaf(sx, bv - av, av), hi_v = fmaf(sx, dv - cv, cv);
+        return make_float2(fmaf(sy, hi_u - lo_u, lo_u), fmaf(sy, hi_v - lo_v, lo_v));
+    } else {
+        float wx[4], wy[4];
+        if (SCHEME == 1) {
+            weights_catmull_rom(sx, wx);
+            weights_catmull_rom(sy, wy);
+        } else {
+            weights_bspline(sx, wx);
+            weights_bspline(sy, wy);
+        }
+        int ii[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) ii[a] = (i + a - 1) & m;
+        float u = 0.f, v = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            int row = ((j + b - 1) & m) * n;
+            float ru = 0.f, rv = 0.f;
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                float4 t = node_ld(snap, row + ii[a]);
+                ru = fmaf(wx[a], fmaf(wa, t.x, wb * t.z), ru);
+                rv = fmaf(wx[a], fmaf(wa, t.y, wb * t.w), rv);
+            }
+            u = fmaf(wy[b], ru, u);
+            v = fmaf(wy[b], rv, v);
+        }
+        return make_float2(u, v);
+    }
+}
+
+}  // namespace el

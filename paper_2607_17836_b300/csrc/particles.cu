@@ -1,0 +1,359 @@
+// Lagrangian particles (Secs. 2.2, 2.3, 3.2, 3.3; Algorithm 1).
+//
+// State per particle, split precision: cell (i, j) packed i | j << 16, the
+// FP32 offset in the cell in [0, 1)^2, and an int32 periodic image count per
+// axis; the unwrapped position is 2 pi * img + (2 pi / n) * (cell + offset).
+// Inertial particles also carry their FP32 velocity.  RK4 works in grid
+// units relative to the cell origin, so every stage position is a small
+// number whatever the particle's distance from the origin, and the carry
+// into cell and image is exact integer arithmetic.
+//
+//   K6 k_rk4       : one RK4 step of one species (Eq. 12 tracers, Eq. 14
+//                    inertial) between levels n and n+1, fused with the
+//                    gathers, the time blend and the wrap/carry write-back
+//   K9 k_init      : FP64 positions -> split state; zero-slip velocity
+//   k_unsplit      : split state -> FP64 unwrapped positions, original order
+//   k_msd / k_box  : per-particle terms of the statistics
+#include "common.cuh"
+#include "interp.cuh"
+
+namespace el {
+namespace {
+
+// Carry an offset that left [0, 1) into the cell index and the image count.
+__device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off, int& cell,
+                                           int& dimg) {
+    float fl = floorf(x);
+    float o = x - fl;
+    int k = (int)fl;
+    if (o >= 1.0f) {  // x - floor(x) rounded up to 1 for x just below an integer
+        o = 0.0f;
+        k += 1;
+    }
+    int c2 = c + k;
+    dimg = c2 >> log2n;              // floor division by n
+    cell = c2 - (dimg << log2n);
+    off = o;
+}
+
+template <int SCHEME, bool INERTIAL>
+__global__ void __launch_bounds__(256) k_rk4(const float4* __restrict__ snap, int n, int log2n,
+                                             const int64_t* __restrict__ d_step,
+                                             uint32_t* __restrict__ cell, float2* __restrict__ off,
+                                             float2* __restrict__ vel, int2* __restrict__ img,
+                                             int64_t np, float dt, float h, float inv_st) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    // level n sits in half (step & 1) of the snapshot pair, level n+1 in the other
+    const float wa0 = (*d_step & 1) ? 0.0f : 1.0f, wb0 = 1.0f - wa0;  // theta = 0
+    const float wa1 = wb0, wb1 = wa0;                                 // theta = 1
+    uint32_t c = cell[p];
+    int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
+    float2 o = off[p];
+    float nx, ny;
+    float2 vnew;
+    if (!INERTIAL) {
+        // Eq. 12 with stage times t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
+        float2 k1 = fluid_at<SCHEME>(snap, n, ci, cj, o.x, o.y, wa0, wb0);
+        float2 k2 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(0.5f * h, k1.x, o.x),
+                                     fmaf(0.5f * h, k1.y, o.y), 0.5f, 0.5f);
+        float2 k3 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(0.5f * h, k2.x, o.x),
+                                     fmaf(0.5f * h, k2.y, o.y), 0.5f, 0.5f);
+        float2 k4 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(h, k3.x, o.x), fmaf(h, k3.y, o.y),
+                                     wa1, wb1);
+        const float h6 = h * (1.0f / 6.0f);
+        nx = fmaf(h6, k1.x + 2.0f * (k2.x + k3.x) + k4.x, o.x);
+        ny = fmaf(h6, k1.y + 2.0f * (k2.y + k3.y) + k4.y, o.y);
+    } else {
+        // Eq. 14: x and v jointly; stage s has x_s = x + c_s dt v_{s-1},
+        // v_s = v + c_s dt a_{s-1}, a_s = (u(x_s, t_s) - v_s) / St (Eq. 13).
+        float2 v = vel[p];
+        float2 u1 = fluid_at<SCHEME>(snap, n, ci, cj, o.x, o.y, wa0, wb0);
+        float2 a1 = make_float2((u1.x - v.x) * inv_st, (u1.y - v.y) * inv_st);
+        float2 v2 = make_float2(fmaf(0.5f * dt, a1.x, v.x), fmaf(0.5f * dt, a1.y, v.y));
+        float2 u2 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(0.5f * h, v.x, o.x),
+                                     fmaf(0.5f * h, v.y, o.y), 0.5f, 0.5f);
+        float2 a2 = make_float2((u2.x - v2.x) * inv_st, (u2.y - v2.y) * inv_st);
+        float2 v3 = make_float2(fmaf(0.5f * dt, a2.x, v.x), fmaf(0.5f * dt, a2.y, v.y));
+        float2 u3 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(0.5f * h, v2.x, o.x),
+                                     fmaf(0.5f * h, v2.y, o.y), 0.5f, 0.5f);
+        float2 a3 = make_float2((u3.x - v3.x) * inv_st, (u3.y - v3.y) * inv_st);
+        float2 v4 = make_float2(fmaf(dt, a3.x, v.x), fmaf(dt, a3.y, v.y));
+        float2 u4 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(h, v3.x, o.x), fmaf(h, v3.y, o.y),
+                                     wa1, wb1);
+        float2 a4 = make_float2((u4.x - v4.x) * inv_st, (u4.y - v4.y) * inv_st);
+        const float h6 = h * (1.0f / 6.0f), d6 = dt * (1.0f / 6.0f);
+        nx = fmaf(h6, v.x + 2.0f * (v2.x + v3.x) + v4.x, o.x);
+        ny = fmaf(h6, v.y + 2.0f * (v2.y + v3.y) + v4.y, o.y);
+        vnew = make_float2(fmaf(d6, a1.x + 2.0f * (a2.x + a3.x) + a4.x, v.x),
+                           fmaf(d6, a1.y + 2.0f * (a2.y + a3.y) + a4.y, v.y));
+    }
+    float ox, oy;
+    int ni, nj, dix, diy;
+    carry_axis(nx, ci, log2n, ox, ni, dix);
+    carry_axis(ny, cj, log2n, oy, nj, diy);
+    cell[p] = (uint32_t)ni | ((uint32_t)nj << 16);
+    off[p] = make_float2(ox, oy);
+    if (INERTIAL) vel[p] = vnew;
+    if (dix | diy) {  // crossed the periodic boundary: rare read-modify-write
+        int2 m = img[p];
+        img[p] = make_int2(m.x + dix, m.y + diy);
+    }
+}
+
+// FP64 position -> (cell, offset, image), Sec. 3.2: mapped periodically onto
+// [0, 2 pi); a point on a node belongs to the cell on its right.
+__device__ __forceinline__ void split_position(double x, int n, int& cell, float& off, int& image) {
+    double k = floor(x / kTwoPi);
+    double xw = x - kTwoPi * k;
+    double s = xw * ((double)n / kTwoPi);
+    double c = floor(s);
+    float o = (float)(s - c);
+    int ci = (int)c, im = (int)k;
+    if (o >= 1.0f) {
+        o = 0.0f;
+        ci += 1;
+    }
+    while (ci >= n) {
+        ci -= n;
+        im += 1;
+    }
+    while (ci < 0) {
+        ci += n;
+        im -= 1;
+    }
+    cell = ci;
+    off = o;
+    image = im;
+}
+
+template <int SCHEME>
+__device__ float2 fluid_at_dispatch(const float4* snap, int n, int ci, int cj, float ox, float oy,
+                                    float wa, float wb) {
+    return fluid_at<SCHEME>(snap, n, ci, cj, ox, oy, wa, wb);
+}
+
+__device__ float2 fluid_at_scheme(int scheme, const float4* snap, int n, int ci, int cj, float ox,
+                                  float oy, float wa, float wb) {
+    if (scheme == 0) return fluid_at_dispatch<0>(snap, n, ci, cj, ox, oy, wa, wb);
+    if (scheme == 1) return fluid_at_dispatch<1>(snap, n, ci, cj, ox, oy, wa, wb);
+    return fluid_at_dispatch<2>(snap, n, ci, cj, ox, oy, wa, wb);
+}
+
+// K9: split-precision state from FP64 positions; velocity from vxy, or zero
+// slip (the interpolated fluid velocity of the current level, half `cur`).
+__global__ void k_init(const double* __restrict__ xy, const double* __restrict__ vxy, int64_t np,
+                       int n, int scheme, int inertial, int cur, const float4* __restrict__ snap,
+                       uint32_t* __restrict__ cell, float2* __restrict__ off,
+                       float2* __restrict__ vel, int2* __restrict__ img, uint32_t* __restrict__ id,
+                       double2* __restrict__ x0) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    double x = xy[2 * p], y = xy[2 * p + 1];
+    int ci, cj, ix, iy;
+    float ox, oy;
+    split_position(x, n, ci, ox, ix);
+    split_position(y, n, cj, oy, iy);
+    cell[p] = (uint32_t)ci | ((uint32_t)cj << 16);
+    off[p] = make_float2(ox, oy);
+    img[p] = make_int2(ix, iy);
+    id[p] = (uint32_t)p;
+    x0[p] = make_double2(x, y);
+    if (inertial) {
+        if (vxy) {
+            vel[p] = make_float2((float)vxy[2 * p], (float)vxy[2 * p + 1]);
+        } else {
+            float wa = cur ? 0.0f : 1.0f;
+            vel[p] = fluid_at_scheme(scheme, snap, n, ci, cj, ox, oy, wa, 1.0f - wa);
+        }
+    }
+}
+
+__device__ __forceinline__ double2 unwrapped(uint32_t c, float2 o, int2 m, double dx) {
+    double x = kTwoPi * (double)m.x + dx * ((double)(c & 0xffffu) + (double)o.x);
+    double y = kTwoPi * (double)m.y + dx * ((double)(c >> 16) + (double)o.y);
+    return make_double2(x, y);
+}
+
+__global__ void k_unsplit(const uint32_t* __restrict__ cell, const float2* __restrict__ off,
+                          const float2* __restrict__ vel, const int2* __restrict__ img,
+                          const uint32_t* __restrict__ id, int64_t np, double dx, int inertial,
+                          double2* __restrict__ xy_out, double2* __restrict__ v_out) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    uint32_t k = id[p];
+    xy_out[k] = unwrapped(cell[p], off[p], img[p], dx);
+    float2 v = inertial ? vel[p] : make_float2(0.f, 0.f);
+    v_out[k] = make_double2((double)v.x, (double)v.y);
+}
+
+// Squared displacement per particle, stored by original index so that the
+// fixed-order reduction that follows does not depend on the sort order.
+__global__ void k_msd(const uint32_t* __restrict__ cell, const float2* __restrict__ off,
+                      const int2* __restrict__ img, const uint32_t* __restrict__ id,
+                      const double2* __restrict__ x0, int64_t np, double dx,
+                      double2* __restrict__ out) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    uint32_t k = id[p];
+    double2 x = unwrapped(cell[p], off[p], img[p], dx);
+    double2 r = x0[k];
+    double ddx = x.x - r.x, ddy = x.y - r.y;
+    out[k] = make_double2(ddx * ddx, ddy * ddy);
+}
+
+// Particle counts on the kBoxes x kBoxes box grid (integer atomics: exact).
+__global__ void k_box(const uint32_t* __restrict__ cell, const float2* __restrict__ off, int64_t np,
+                      int n, unsigned long long* __restrict__ boxes) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    uint32_t c = cell[p];
+    float2 o = off[p];
+    double scale = (double)kBoxes / (double)n;  // power of two: exact products
+    int bx = (int)(((double)(c & 0xffffu) + (double)o.x) * scale);
+    int by = (int)(((double)(c >> 16) + (double)o.y) * scale);
+    bx = bx > kBoxes - 1 ? kBoxes - 1 : bx;
+    by = by > kBoxes - 1 ? kBoxes - 1 : by;
+    atomicAdd(boxes + by * kBoxes + bx, 1ull);
+}
+
+// Var(n)/mean(n) - 1 from the integer box counts (one thread, fixed order).
+__global__ void k_cluster_final(const unsigned long long* __restrict__ boxes, double* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    unsigned long long s1 = 0, s2 = 0;
+    for (int b = 0; b < kBoxes * kBoxes; b++) {
+        s1 += boxes[b];
+        s2 += boxes[b] * boxes[b];
+    }
+    double B = (double)(kBoxes * kBoxes);
+    double mean = (double)s1 / B;
+    double var = (double)s2 / B - mean * mean;
+    *out = mean > 0.0 ? var / mean - 1.0 : 0.0;
+}
+
+// Sampling hook: the gather of K6 at arbitrary FP64 points.
+__global__ void k_sample(const double* __restrict__ xy, int64_t np, int n, int scheme, float wa,
+                         float wb, const float4* __restrict__ snap, double* __restrict__ uv) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    int ci, cj, ix, iy;
+    float ox, oy;
+    split_position(xy[2 * p], n, ci, ox, ix);
+    split_position(xy[2 * p + 1], n, cj, oy, iy);
+    float2 u = fluid_at_scheme(scheme, snap, n, ci, cj, ox, oy, wa, wb);
+    uv[2 * p] = (double)u.x;
+    uv[2 * p + 1] = (double)u.y;
+}
+
+}  // namespace
+
+el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
+                        const double* vxy) {
+    Species& sp = f->sp[s];
+    const int T = 256;
+    double* stage = reinterpret_cast<double*>(sp.cell[1]);  // sort block: 32 B per particle
+    EL_CUDA_OK(f, cudaMemcpyAsync(stage, xy, (size_t)np * 2 * sizeof(double),
+                                  cudaMemcpyHostToDevice, f->stream));
+    const double* d_vxy = nullptr;
+    if (vxy && st > 0.0) {
+        EL_CUDA_OK(f, cudaMemcpyAsync(stage + 2 * np, vxy, (size_t)np * 2 * sizeof(double),
+                                      cudaMemcpyHostToDevice, f->stream));
+        d_vxy = stage + 2 * np;
+    }
+    if (np > 0) {
+        k_init<<<blocks_for(np, T), T, 0, f->stream>>>(
+            stage, d_vxy, np, f->n, f->d.interp, st > 0.0 ? 1 : 0, (int)(f->step & 1), f->snap,
+            sp.cell[0], sp.off[0], sp.vel[0], sp.img[0], sp.id[0], sp.x0);
+        EL_LAUNCHED(f);
+    }
+    EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
+    sp.np = np;
+    sp.st = st;
+    return EL_OK;
+}
+
+template <int SCHEME>
+static el_status launch_rk4(el_flow* f, Species& sp, unsigned grid, int T, float dt, float h) {
+    if (sp.st > 0.0) {
+        k_rk4<SCHEME, true><<<grid, T, 0, f->stream>>>(f->snap, f->n, f->log2n, f->d_step,
+                                                       sp.cell[0], sp.off[0], sp.vel[0],
+                                                       sp.img[0], sp.np, dt, h,
+                                                       (float)(1.0 / sp.st));
+    } else {
+        k_rk4<SCHEME, false><<<grid, T, 0, f->stream>>>(f->snap, f->n, f->log2n, f->d_step,
+                                                        sp.cell[0], sp.off[0], sp.vel[0],
+                                                        sp.img[0], sp.np, dt, h, 0.0f);
+    }
+    EL_LAUNCHED(f);
+    return EL_OK;
+}
+
+el_status particles_step(el_flow* f, int s) {
+    Species& sp = f->sp[s];
+    if (sp.np == 0) return EL_OK;
+    const int T = 256;
+    unsigned grid = blocks_for(sp.np, T);
+    float dt = (float)f->d.dt;
+    float h = (float)(f->d.dt * (double)f->n / kTwoPi);  // grid units per unit velocity
+    switch (f->d.interp) {
+        case EL_BILINEAR: return launch_rk4<0>(f, sp, grid, T, dt, h);
+        case EL_CATMULL_ROM: return launch_rk4<1>(f, sp, grid, T, dt, h);
+        default: return launch_rk4<2>(f, sp, grid, T, dt, h);
+    }
+}
+
+el_status particles_get(el_flow* f, int s, double* xy, double* vxy) {
+    Species& sp = f->sp[s];
+    const int T = 256;
+    double2* out_xy = reinterpret_cast<double2*>(sp.cell[1]);
+    double2* out_v = out_xy + sp.np;
+    if (sp.np > 0) {
+        k_unsplit<<<blocks_for(sp.np, T), T, 0, f->stream>>>(
+            sp.cell[0], sp.off[0], sp.vel[0], sp.img[0], sp.id[0], sp.np, kTwoPi / f->n,
+            sp.st > 0.0 ? 1 : 0, out_xy, out_v);
+        EL_LAUNCHED(f);
+        if (xy)
+            EL_CUDA_OK(f, cudaMemcpyAsync(xy, out_xy, (size_t)sp.np * sizeof(double2),
+                                          cudaMemcpyDeviceToHost, f->stream));
+        if (vxy)
+            EL_CUDA_OK(f, cudaMemcpyAsync(vxy, out_v, (size_t)sp.np * sizeof(double2),
+                                          cudaMemcpyDeviceToHost, f->stream));
+    }
+    EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
+    return EL_OK;
+}
+
+// Mean-square displacement (out3[0], out3[1]) and clustering index (out3[2])
+// of species s, into device memory.
+el_status particles_stats_into(el_flow* f, int s, double* out3) {
+    Species& sp = f->sp[s];
+    const int T = 256;
+    double2* terms = reinterpret_cast<double2*>(sp.cell[1]);
+    k_msd<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[0], sp.off[0], sp.img[0], sp.id[0],
+                                                     sp.x0, sp.np, kTwoPi / f->n, terms);
+    EL_LAUNCHED(f);
+    EL_TRY(reduce_double2(f, terms, sp.np, out3));
+    EL_CUDA_OK(f, cudaMemsetAsync(f->boxes, 0, sizeof(unsigned long long) * kBoxes * kBoxes,
+                                  f->stream));
+    k_box<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[0], sp.off[0], sp.np, f->n, f->boxes);
+    EL_LAUNCHED(f);
+    k_cluster_final<<<1, 32, 0, f->stream>>>(f->boxes, out3 + 2);
+    EL_LAUNCHED(f);
+    return EL_OK;
+}
+
+el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv) {
+    if (np == 0) return EL_OK;
+    const int T = 256;
+    // previous level in half (step + 1) & 1, current level in half step & 1
+    int cur = (int)(f->step & 1);
+    float th = (float)theta;
+    float w_cur = th, w_prev = 1.0f - th;
+    float wa = cur == 0 ? w_cur : w_prev, wb = cur == 0 ? w_prev : w_cur;
+    k_sample<<<blocks_for(np, T), T, 0, f->stream>>>(d_xy, np, f->n, f->d.interp, wa, wb, f->snap,
+                                                      d_uv);
+    EL_LAUNCHED(f);
+    return EL_OK;
+}
+
+}  // namespace el

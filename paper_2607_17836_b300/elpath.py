@@ -1,0 +1,228 @@
+"""ctypes binding of libelpath.so (include/elpath.h), same names as the C ABI.
+
+Argument marshalling only: every step of the coupled path runs in the CUDA
+library.  PyTorch provides the device workspace (a uint8 tensor) and the
+CUDA stream.  If the library is missing this module raises; there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libelpath.so")
+
+BILINEAR, CATMULL_ROM, BSPLINE = 0, 1, 2
+MAX_SPECIES = 8
+STATUS = {0: "EL_OK", 1: "EL_EINVAL", 2: "EL_ENOMEM", 3: "EL_ECUDA", 4: "EL_ECUFFT",
+          5: "EL_ESTATE", 6: "EL_ENONFINITE", 7: "EL_ETIMEOUT"}
+
+# Public C symbols, in include/elpath.h order.
+SYMBOLS = ("el_workspace_bytes", "el_create_flow", "el_set_particles", "el_step_coupled",
+           "el_get_stats", "el_get_particles", "el_get_field", "el_sample_velocity",
+           "el_profile_step", "el_kernel_launches", "el_destroy_flow", "el_last_error")
+
+
+class ElpathError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class el_flow_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("interp", ctypes.c_int32), ("nu", ctypes.c_double),
+                ("dt", ctypes.c_double), ("ab2_mode", ctypes.c_int32),
+                ("bspline_prefilter", ctypes.c_int32), ("max_species", ctypes.c_int32),
+                ("sort_every", ctypes.c_int32), ("max_particles", ctypes.c_int64)]
+
+
+class el_stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_int64), ("energy", ctypes.c_double),
+                ("enstrophy", ctypes.c_double), ("palinstrophy", ctypes.c_double),
+                ("msd", (ctypes.c_double * 2) * MAX_SPECIES),
+                ("cluster", ctypes.c_double * MAX_SPECIES), ("np", ctypes.c_int64 * MAX_SPECIES),
+                ("finite", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Open libelpath.so and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: build it with "
+                                "`python -m paper_2607_17836_b300.build` (no fallback path exists)")
+    lib = ctypes.CDLL(path)
+    P, D, I32, I64, V = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                         ctypes.c_int64, ctypes.c_void_p)
+    lib.el_workspace_bytes.argtypes = [ctypes.POINTER(el_flow_desc)]
+    lib.el_workspace_bytes.restype = ctypes.c_size_t
+    lib.el_create_flow.argtypes = [ctypes.POINTER(el_flow_desc), D, V, ctypes.c_size_t, V,
+                                   ctypes.POINTER(P)]
+    lib.el_set_particles.argtypes = [P, I32, I64, ctypes.c_double, D, D]
+    lib.el_step_coupled.argtypes = [P, I32]
+    lib.el_get_stats.argtypes = [P, ctypes.POINTER(el_stats)]
+    lib.el_get_particles.argtypes = [P, I32, D, D]
+    lib.el_get_field.argtypes = [P, I32, D]
+    lib.el_sample_velocity.argtypes = [P, I64, V, ctypes.c_double, V]
+    lib.el_profile_step.argtypes = [P, D, I32]
+    lib.el_kernel_launches.argtypes = [P]
+    lib.el_kernel_launches.restype = I64
+    lib.el_destroy_flow.argtypes = [P]
+    lib.el_last_error.argtypes = [P]
+    lib.el_last_error.restype = ctypes.c_char_p
+    for name in ("el_create_flow", "el_set_particles", "el_step_coupled", "el_get_stats",
+                 "el_get_particles", "el_get_field", "el_sample_velocity", "el_profile_step",
+                 "el_destroy_flow"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _host_f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def make_desc(n, nu, dt, interp=BILINEAR, ab2_mode=0, bspline_prefilter=True, max_species=0,
+              max_particles=0, sort_every=0) -> el_flow_desc:
+    return el_flow_desc(int(n), int(interp), float(nu), float(dt), int(ab2_mode),
+                        1 if bspline_prefilter else 0, int(max_species), int(sort_every),
+                        int(max_particles))
+
+
+def workspace_bytes(desc: el_flow_desc) -> int:
+    return int(load().el_workspace_bytes(ctypes.byref(desc)))
+
+
+class Flow:
+    """One coupled simulation (el_flow) on a CUDA device."""
+
+    def __init__(self, n, nu, dt, omega0, interp=BILINEAR, ab2_mode=0, bspline_prefilter=True,
+                 max_species=0, max_particles=0, sort_every=0, stream=None, device=None,
+                 workspace=None):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.desc = make_desc(n, nu, dt, interp, ab2_mode, bspline_prefilter, max_species,
+                              max_particles, sort_every)
+        self.n = int(n)
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = workspace_bytes(self.desc)
+        if nbytes == 0:
+            raise ElpathError(1, "invalid flow description (or no CUDA device)")
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.workspace = workspace
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        w0 = _host_f64(omega0)
+        if w0.shape != (self.n, self.n):
+            raise ValueError(f"omega0 must be {self.n}x{self.n}")
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = lib.el_create_flow(ctypes.byref(self.desc), _dptr(w0),
+                                    ctypes.c_void_p(workspace.data_ptr()),
+                                    ctypes.c_size_t(workspace.numel()),
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise ElpathError(st, lib.el_last_error(None).decode())
+        self._h = h
+
+    # -- helpers
+    def _check(self, st):
+        if st != 0:
+            raise ElpathError(st, self._lib.el_last_error(self._h).decode())
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.el_destroy_flow(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- ABI calls
+    def set_particles(self, species, xy, st, vxy=None):
+        xy = _host_f64(xy, (-1, 2))
+        v = _host_f64(vxy, (-1, 2)) if vxy is not None else None
+        if v is not None and v.shape != xy.shape:
+            raise ValueError("vxy must match xy")
+        self._check(self._lib.el_set_particles(self._h, int(species), int(xy.shape[0]),
+                                               float(st), _dptr(xy), _dptr(v)))
+
+    def step(self, nsteps=1):
+        self._check(self._lib.el_step_coupled(self._h, int(nsteps)))
+
+    def stats(self, allow_nonfinite=False) -> dict:
+        s = el_stats()
+        st = self._lib.el_get_stats(self._h, ctypes.byref(s))
+        if st != 0 and not (allow_nonfinite and st == 6):
+            self._check(st)
+        return {"t": s.t, "step": s.step, "energy": s.energy, "enstrophy": s.enstrophy,
+                "palinstrophy": s.palinstrophy,
+                "msd": [(s.msd[k][0], s.msd[k][1]) for k in range(MAX_SPECIES)],
+                "cluster": [s.cluster[k] for k in range(MAX_SPECIES)],
+                "np": [s.np[k] for k in range(MAX_SPECIES)], "finite": bool(s.finite)}
+
+    def particles(self, species, count):
+        xy = np.empty((count, 2))
+        vxy = np.empty((count, 2))
+        self._check(self._lib.el_get_particles(self._h, int(species), _dptr(xy), _dptr(vxy)))
+        return xy, vxy
+
+    def particles_into(self, species, xy=None, vxy=None):
+        """el_get_particles into caller-owned (e.g. pinned) float64 host arrays."""
+        self._check(self._lib.el_get_particles(self._h, int(species), _dptr(xy), _dptr(vxy)))
+
+    def field(self, which):
+        out = np.empty((self.n, self.n))
+        self._check(self._lib.el_get_field(self._h, int(which), _dptr(out)))
+        return out
+
+    def sample_velocity(self, xy_dev, theta=1.0, out=None):
+        """xy_dev: CUDA float64 tensor (np, 2).  Returns a CUDA float64 (np, 2) tensor."""
+        import torch
+        assert xy_dev.is_cuda and xy_dev.dtype == torch.float64 and xy_dev.is_contiguous()
+        if out is None:
+            out = torch.empty_like(xy_dev)
+        self._check(self._lib.el_sample_velocity(self._h, int(xy_dev.shape[0]),
+                                                 ctypes.c_void_p(xy_dev.data_ptr()),
+                                                 float(theta), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def profile_step(self):
+        """One coupled step with per-stage CUDA-event times (ms):
+        {"fluid": ms, "species": [ms per slot], "sort": ms}."""
+        ns = self.desc.max_species
+        buf = np.zeros(2 + ns)
+        self._check(self._lib.el_profile_step(self._h, _dptr(buf), int(buf.size)))
+        return {"fluid": float(buf[0]), "species": [float(x) for x in buf[1:1 + ns]],
+                "sort": float(buf[1 + ns])}
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.el_kernel_launches(self._h))
+
+    def synchronize(self):
+        self.stream.synchronize()

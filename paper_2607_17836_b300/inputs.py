@@ -137,7 +137,7 @@ def decaying_turbulence_1024(scale: float = 1.0) -> Workload:
 def kelvin_helmholtz_2048(scale: float = 1.0) -> Workload:
     """2048^2 double shear layer, nu=5e-5, dt=2.5e-4, 4000 steps, 16M inertial
     particles at St=1, Catmull-Rom."""
-    c = max(1, int(round(16 * 1024 * 1024 * scale)))
+    c = max(1, int(round(16_000_000 * scale)))
     return Workload("kelvin_helmholtz_2048", 2048, 5e-5, 2.5e-4, 4000, "kelvin_helmholtz", 7,
                     [SpeciesSpec(c, 1.0, 8)], (1,))
 

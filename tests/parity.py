@@ -1,0 +1,90 @@
+"""Shared helpers for the GPU-vs-oracle parity tests (test code only)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_2607_17836_b300 import elpath, inputs
+
+TWO_PI = 2.0 * np.pi
+
+# Tolerances (relative to the FP64 oracle):
+GATHER_RTOL = 2e-6        # interpolated velocity: max |err| / max |u|
+OMEGA_RTOL = 1e-5         # vorticity L-inf after 100 steps: max |err| / max |omega|
+POS_ATOL = 1e-5 * TWO_PI  # particle positions after 200 steps
+STATS_RTOL = 1e-2         # long chaotic runs: dispersion and clustering
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def oracle_stencil(u, v, scheme, prefilter=True):
+    if scheme == oracle.BSPLINE and prefilter:
+        return oracle.bspline_prefilter(u), oracle.bspline_prefilter(v)
+    return u, v
+
+
+class OracleRun:
+    """Oracle fluid + any number of (scheme, st, positions) particle sets,
+    all driven by one FP64 fluid solve (the fluid does not depend on the
+    particles or on the interpolation scheme)."""
+
+    def __init__(self, n, nu, dt, omega0, ab2_mode=0, prefilter=True):
+        self.flow = oracle.Flow(n, nu, dt, omega0, ab2_mode)
+        self.prefilter = prefilter
+        self.sets = []
+        f = self.flow.fields(("u", "v"))
+        self.level = (f["u"], f["v"])
+
+    def add(self, scheme, st, xy, vxy=None):
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        x, y = xy[:, 0].copy(), xy[:, 1].copy()
+        if st > 0:
+            if vxy is None:
+                su, sv = oracle_stencil(*self.level, scheme, self.prefilter)
+                vx, vy = oracle.interp(su, scheme, x, y), oracle.interp(sv, scheme, x, y)
+            else:
+                vxy = np.asarray(vxy, dtype=np.float64).reshape(-1, 2)
+                vx, vy = vxy[:, 0].copy(), vxy[:, 1].copy()
+        else:
+            vx = vy = None
+        self.sets.append({"scheme": scheme, "st": float(st), "x": x, "y": y, "vx": vx, "vy": vy,
+                          "x0": x.copy(), "y0": y.copy()})
+        return len(self.sets) - 1
+
+    def step(self, nsteps):
+        for _ in range(nsteps):
+            un, vn = self.level
+            self.flow.step(1)
+            f = self.flow.fields(("u", "v"))
+            un1, vn1 = f["u"], f["v"]
+            cache = {}
+            for s in self.sets:
+                sc = s["scheme"]
+                if sc not in cache:
+                    cache[sc] = (oracle_stencil(un, vn, sc, self.prefilter),
+                                 oracle_stencil(un1, vn1, sc, self.prefilter))
+                (a, b), (c, d) = cache[sc]
+                oracle.particles_rk4(sc, self.flow.dt, s["st"], a, b, c, d, s["x"], s["y"],
+                                     s["vx"], s["vy"])
+            self.level = (un1, vn1)
+
+    def positions(self, k):
+        s = self.sets[k]
+        return np.stack([s["x"], s["y"]], axis=1)
+
+    def velocities(self, k):
+        s = self.sets[k]
+        return np.stack([s["vx"], s["vy"]], axis=1)
+
+
+def gpu_flow(n, nu, dt, omega0, interp=0, max_species=1, max_particles=0, sort_every=0,
+             ab2_mode=0, prefilter=True):
+    return elpath.Flow(n, nu, dt, omega0, interp=interp, ab2_mode=ab2_mode,
+                       bspline_prefilter=prefilter, max_species=max_species,
+                       max_particles=max_particles, sort_every=sort_every)
+
+
+def decaying(n, seed=2, k0=10.0):
+    return inputs.decaying_turbulence(n, seed, k0=k0)
