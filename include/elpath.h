@@ -141,10 +141,10 @@ el_status el_sample_velocity(el_flow* flow, int64_t np, const double* d_xy, doub
 
 /* Run ONE coupled step exactly as el_step_coupled does (re-binning first
  * if it is due), but by direct launches with CUDA events on the flow's
- * stream around each stage, then synchronise and report the stage times:
- * stage_ms[0] = fluid step (Sec. 3.1), stage_ms[1 + s] = RK4 step of
- * species s (0 for an empty slot), stage_ms[1 + max_species] = re-binning
- * (0 if not due).  nstage must be >= 2 + max_species. */
+ * stream around each stage, then synchronise and report the stage times in
+ * milliseconds: stage_ms[0] = fluid step (Sec. 3.1), stage_ms[1] = RK4 step
+ * of every species (one launch), stage_ms[2] = re-binning (0 if not due).
+ * nstage must be >= 3. */
 el_status el_profile_step(el_flow* flow, double* stage_ms, int32_t nstage);
 
 /* Number of kernel launches of the library (not cuFFT) issued so far by

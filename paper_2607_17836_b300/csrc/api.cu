@@ -13,7 +13,7 @@
 
 namespace el {
 
-void fluid_tables(const el_flow_desc& d, std::vector<double>& ex, std::vector<double>& ey,
+void fluid_tables(const el_flow_desc& d, std::vector<float2>& ex, std::vector<float2>& ey,
                   std::vector<float>& px, std::vector<float>& py);
 
 namespace {
@@ -117,6 +117,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     size_t n = (size_t)d.n, nh = n / 2 + 1, n2 = n * n, nm = n * nh;
     int planes = planes_of(d);
     char* what = take(nm * 8);
+    char* what_lo = take(nm * 8);
     char* hist = take(nm * 8);
     char* nhat = take(nm * 8);
     char* spec = take((size_t)planes * nm * 8);
@@ -142,6 +143,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* pool = take(pool_bytes);
     if (f) {
         f->what = (float2*)what;
+        f->what_lo = (float2*)what_lo;
         f->hist = (float2*)hist;
         f->nhat = (float2*)nhat;
         f->spec = (float2*)spec;
@@ -151,8 +153,8 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->aux_spec = (float2*)aux_spec;
         f->aux_phys = (float*)aux_phys;
         f->stage64 = (double*)stage64;
-        f->ex = (double*)ex;
-        f->ey = (double*)ey;
+        f->ex = (float2*)ex;
+        f->ey = (float2*)ey;
         f->pre_x = (float*)px;
         f->pre_y = (float*)py;
         f->d_step = (int64_t*)dstep;
@@ -201,7 +203,7 @@ bool carve_species(el_flow* f, Species& sp, int64_t np) {
 // between levels n and n+1, then the device step counter.
 el_status step_body(el_flow* f) {
     EL_TRY(fluid_step(f));
-    for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_step(f, s));
+    EL_TRY(particles_step_all(f));
     EL_TRY(step_increment(f));
     return EL_OK;
 }
@@ -314,7 +316,7 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     }
     f->plans_made = true;
 
-    std::vector<double> ex, ey;
+    std::vector<float2> ex, ey;
     std::vector<float> px, py;
     fluid_tables(*desc, ex, ey, px, py);
     cudaError_t e = cudaSuccess;
@@ -357,6 +359,7 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
                     (long long)f->d.max_particles);
     EL_TRY(particles_set(f, species, np, st, xy, vxy));
     f->graph_valid = false;
+    if (f->d.sort_every > 0) f->since_sort = f->d.sort_every;  // bin the new particles first
     return EL_OK;
 }
 
@@ -435,27 +438,22 @@ el_status el_sample_velocity(el_flow* f, int64_t np, const double* d_xy, double 
 
 el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
     if (!f || !stage_ms) return EL_EINVAL;
-    int ns = f->d.max_species;
-    if (nstage < 2 + ns) return fail(f, EL_EINVAL, "nstage must be >= %d", 2 + ns);
-    cudaEvent_t ev[2 + EL_MAX_SPECIES + 2];
-    int nev = ns + 4;
-    for (int k = 0; k < nev; k++) EL_CUDA_OK(f, cudaEventCreate(&ev[k]));
+    if (nstage < 3) return fail(f, EL_EINVAL, "nstage must be >= 3");
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; k++) EL_CUDA_OK(f, cudaEventCreate(&ev[k]));
     el_status st = EL_OK;
     bool sorted = false;
-    auto rec = [&](int k) { cudaEventRecord(ev[k], f->stream); };
-    rec(0);
+    cudaEventRecord(ev[0], f->stream);
     if (f->d.sort_every > 0 && f->since_sort >= f->d.sort_every) {
-        for (int s = 0; s < ns && st == EL_OK; s++) st = particles_sort(f, s);
+        for (int s = 0; s < f->d.max_species && st == EL_OK; s++) st = particles_sort(f, s);
         f->since_sort = 0;
         sorted = true;
     }
-    rec(1);
+    cudaEventRecord(ev[1], f->stream);
     if (st == EL_OK) st = fluid_step(f);
-    rec(2);
-    for (int s = 0; s < ns && st == EL_OK; s++) {
-        st = particles_step(f, s);
-        rec(3 + s);
-    }
+    cudaEventRecord(ev[2], f->stream);
+    if (st == EL_OK) st = particles_step_all(f);
+    cudaEventRecord(ev[3], f->stream);
     if (st == EL_OK) st = step_increment(f);
     cudaError_t e = cudaStreamSynchronize(f->stream);
     if (st == EL_OK && e != cudaSuccess) st = fail(f, EL_ECUDA, "profile: %s", cudaGetErrorString(e));
@@ -463,16 +461,14 @@ el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[1], ev[2]);
         stage_ms[0] = ms;
-        for (int s = 0; s < ns; s++) {
-            cudaEventElapsedTime(&ms, ev[2 + s], ev[3 + s]);
-            stage_ms[1 + s] = f->sp[s].np > 0 ? ms : 0.0;
-        }
+        cudaEventElapsedTime(&ms, ev[2], ev[3]);
+        stage_ms[1] = ms;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        stage_ms[1 + ns] = sorted ? ms : 0.0;
+        stage_ms[2] = sorted ? ms : 0.0;
         f->step++;
         f->since_sort++;
     }
-    for (int k = 0; k < nev; k++) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 4; k++) cudaEventDestroy(ev[k]);
     return st;
 }
 

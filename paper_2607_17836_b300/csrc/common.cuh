@@ -54,6 +54,7 @@ struct el_flow {
 
     // fluid state (device)
     float2* what = nullptr;   // omega-hat, half spectrum [ky][kx], n x (n/2+1)
+    float2* what_lo = nullptr;  // low part of omega-hat (compensated storage)
     float2* hist = nullptr;   // AB2 history
     float2* nhat = nullptr;   // nonlinear term of the latest level
     float2* spec = nullptr;   // nplanes half spectra (C2R input)
@@ -63,8 +64,8 @@ struct el_flow {
     float2* aux_spec = nullptr;
     float* aux_phys = nullptr;
     double* stage64 = nullptr;  // n^2 doubles: host <-> device field staging
-    double* ex = nullptr;     // exp(-nu kx^2 dt), kx = 0..n/2
-    double* ey = nullptr;     // exp(-nu ky^2 dt), row index 0..n-1
+    float2* ex = nullptr;     // exp(-nu kx^2 dt) as (hi, lo) floats, kx = 0..n/2
+    float2* ey = nullptr;     // exp(-nu ky^2 dt) as (hi, lo) floats, row index 0..n-1
     float* pre_x = nullptr;   // spline prefilter 3/(2 + cos(k dx)) per kx
     float* pre_y = nullptr;   // ... per row index
     int64_t* d_step = nullptr;
@@ -137,7 +138,7 @@ el_status step_increment(el_flow* f);
 // ---- particles (particles.cu) ---------------------------------------------------
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
                         const double* vxy);
-el_status particles_step(el_flow* f, int s);      // K6
+el_status particles_step_all(el_flow* f);         // K6, every species in one launch
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
 el_status particles_stats_into(el_flow* f, int s, double* out3);  // msd x, msd y, cluster
 el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv);

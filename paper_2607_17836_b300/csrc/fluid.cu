@@ -76,48 +76,70 @@ __global__ void k_nonlinear(const float* __restrict__ phys, float* __restrict__ 
     }
 }
 
+// Error-free FP32 transformations (double-float arithmetic).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 // Dealias N-hat and advance omega-hat by one AB2 step (Eqs. 9, 10).
-// mode 0 (integrating factor): E = exp(-nu k^2 dt) from the separable FP64
-//   tables ex, ey; w <- E w - dt (3/2 E N - 1/2 E^2 H), H <- N.
+// omega-hat is held as an unevaluated sum w = w_hi + w_lo of two floats: a
+// single float would round the small per-step change (the viscous decay is
+// only nu k^2 dt of w) the same way step after step and drift by up to half
+// an ulp per step; the pair keeps about 44 bits.  Only w_hi feeds the
+// transforms.
+// mode 0 (integrating factor): E = exp(-nu k^2 dt) = ex[kx] * ey[ky], the 1-D
+//   factors computed on the host in FP64 and held as float pairs;
+//   w <- E w - dt (3/2 E N - 1/2 E^2 H), H <- N.
 // mode 1 (Eq. 10 as printed): R = -N - nu k^2 w; w <- w + dt (3/2 R - 1/2 H), H <- R.
 // The first step (step == 0) is forward Euler in either mode.
-__global__ void k_ab2(float2* __restrict__ what, float2* __restrict__ hist,
-                      const float2* __restrict__ nhat, int n, int nh, size_t nmodes,
-                      const double* __restrict__ ex, const double* __restrict__ ey, float dt,
-                      float nu, int mode, const int64_t* __restrict__ d_step) {
+__global__ void k_ab2(float2* __restrict__ what, float2* __restrict__ what_lo,
+                      float2* __restrict__ hist, const float2* __restrict__ nhat, int n, int nh,
+                      size_t nmodes, const float2* __restrict__ ex, const float2* __restrict__ ey,
+                      float dt, float nu, int mode, const int64_t* __restrict__ d_step) {
     size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nmodes) return;
     int j = (int)(q / nh), i = (int)(q - (size_t)j * nh);
     int ky = wavenumber_row(j, n), kx = i;
     bool first = (*d_step == 0);
     float2 N = kept(kx, ky, n) ? nhat[q] : make_float2(0.f, 0.f);
-    float2 w = what[q];
+    float2 w = what[q], wl = what_lo[q];
+    float2 inc, hi_part;  // new w = hi_part + (lo terms) + inc
+    float2 lo;
     if (mode == 0) {
-        double e64 = ex[i] * ey[j];
-        float E = (float)e64, E2 = (float)(e64 * e64);
-        if (first) {
-            w.x = E * fmaf(-dt, N.x, w.x);
-            w.y = E * fmaf(-dt, N.y, w.y);
-        } else {
-            float2 H = hist[q];
-            w.x = E * w.x - dt * (1.5f * E * N.x - 0.5f * E2 * H.x);
-            w.y = E * w.y - dt * (1.5f * E * N.y - 0.5f * E2 * H.y);
-        }
+        // E = Eh + El from the float pairs (two-product of the hi parts)
+        float2 a = ex[i], b = ey[j];
+        float Eh = a.x * b.x;
+        float El = fmaf(a.x, b.x, -Eh) + fmaf(a.x, b.y, a.y * b.x);
+        float E2 = Eh * Eh;
+        float2 H = first ? make_float2(0.f, 0.f) : hist[q];
+        float c1 = first ? dt : 1.5f * dt, c2 = first ? 0.f : 0.5f * dt * E2;
+        // E * (w_hi + w_lo) - c1 E N + c2 H
+        float px = Eh * w.x, py = Eh * w.y;
+        float ex_ = fmaf(Eh, w.x, -px), ey_ = fmaf(Eh, w.y, -py);
+        inc = make_float2(fmaf(c2, H.x, -c1 * Eh * N.x), fmaf(c2, H.y, -c1 * Eh * N.y));
+        hi_part = make_float2(px, py);
+        lo = make_float2(ex_ + fmaf(El, w.x, Eh * wl.x), ey_ + fmaf(El, w.y, Eh * wl.y));
         hist[q] = N;
     } else {
         float nuk2 = nu * (float)(kx * kx + ky * ky);
         float2 R = make_float2(-N.x - nuk2 * w.x, -N.y - nuk2 * w.y);
         if (first) {
-            w.x = fmaf(dt, R.x, w.x);
-            w.y = fmaf(dt, R.y, w.y);
+            inc = make_float2(dt * R.x, dt * R.y);
         } else {
             float2 H = hist[q];
-            w.x += dt * (1.5f * R.x - 0.5f * H.x);
-            w.y += dt * (1.5f * R.y - 0.5f * H.y);
+            inc = make_float2(dt * (1.5f * R.x - 0.5f * H.x), dt * (1.5f * R.y - 0.5f * H.y));
         }
+        hi_part = w;
+        lo = wl;
         hist[q] = R;
     }
-    what[q] = w;
+    float sx, ex2, sy, ey2;
+    two_sum(hi_part.x, lo.x + inc.x, sx, ex2);
+    two_sum(hi_part.y, lo.y + inc.y, sy, ey2);
+    what[q] = make_float2(sx, sy);
+    what_lo[q] = make_float2(ex2, ey2);
 }
 
 // Initial projection: mean removed, 2/3 rule (Sec. 3.1).
@@ -183,11 +205,21 @@ __global__ void k_spec_diag(const float2* __restrict__ what, int n, int nh, size
     }
 }
 
-__global__ void k_spec_diag_final(const double* __restrict__ partial, int nblocks, double scale,
-                                  double* __restrict__ out) {
+// Sum of the block partials in a fixed tree (one block of kRedThreads).
+__global__ void __launch_bounds__(kRedThreads) k_spec_diag_final(const double* __restrict__ partial,
+                                                                 int nblocks, double scale,
+                                                                 double* __restrict__ out) {
+    __shared__ double sh[3][kRedThreads / 32];
+    for (int c = 0; c < 3; c++) {
+        double x = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) x += partial[(size_t)b * 3 + c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) sh[c][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
     if (threadIdx.x < 3) {
         double x = 0.0;
-        for (int b = 0; b < nblocks; b++) x += partial[(size_t)b * 3 + threadIdx.x];
+        for (int w = 0; w < kRedThreads / 32; w++) x += sh[threadIdx.x][w];
         out[threadIdx.x] = x * scale;
     }
 }
@@ -236,6 +268,7 @@ el_status fluid_init(el_flow* f, const double* omega0_host) {
                                                                       f->nh, f->nmodes);
     EL_LAUNCHED(f);
     EL_CUDA_OK(f, cudaMemsetAsync(f->hist, 0, f->nmodes * sizeof(float2), f->stream));
+    EL_CUDA_OK(f, cudaMemsetAsync(f->what_lo, 0, f->nmodes * sizeof(float2), f->stream));
     EL_CUDA_OK(f, cudaMemsetAsync(f->d_step, 0, sizeof(int64_t), f->stream));
     EL_TRY(rhs_from_what(f, 1));
     return EL_OK;
@@ -244,8 +277,8 @@ el_status fluid_init(el_flow* f, const double* omega0_host) {
 el_status fluid_step(el_flow* f) {
     const int T = 256;
     k_ab2<<<blocks_for((int64_t)f->nmodes, T), T, 0, f->stream>>>(
-        f->what, f->hist, f->nhat, f->n, f->nh, f->nmodes, f->ex, f->ey, (float)f->d.dt,
-        (float)f->d.nu, f->d.ab2_mode, f->d_step);
+        f->what, f->what_lo, f->hist, f->nhat, f->n, f->nh, f->nmodes, f->ex, f->ey,
+        (float)f->d.dt, (float)f->d.nu, f->d.ab2_mode, f->d_step);
     EL_LAUNCHED(f);
     return rhs_from_what(f, 0);
 }
@@ -260,7 +293,7 @@ el_status fluid_diagnostics(el_flow* f) {
     k_spec_diag<<<kRedBlocks, kRedThreads, 0, f->stream>>>(f->what, f->n, f->nh, f->nmodes, f->red);
     EL_LAUNCHED(f);
     double nn = (double)f->n2;
-    k_spec_diag_final<<<1, 32, 0, f->stream>>>(f->red, kRedBlocks, 0.5 / (nn * nn), f->red_out);
+    k_spec_diag_final<<<1, kRedThreads, 0, f->stream>>>(f->red, kRedBlocks, 0.5 / (nn * nn), f->red_out);
     EL_LAUNCHED(f);
     return EL_OK;
 }
@@ -291,8 +324,9 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn) {
     return EL_OK;
 }
 
-// Host-side FP64 tables: integrating factors and spline prefilter factors.
-void fluid_tables(const el_flow_desc& d, std::vector<double>& ex, std::vector<double>& ey,
+// Host-side FP64 tables: the 1-D integrating factors exp(-nu k^2 dt) as
+// float pairs (hi, lo), and the spline prefilter factors 3 / (2 + cos k dx).
+void fluid_tables(const el_flow_desc& d, std::vector<float2>& ex, std::vector<float2>& ey,
                   std::vector<float>& px, std::vector<float>& py) {
     int n = d.n, nh = n / 2 + 1;
     ex.resize(nh);
@@ -300,14 +334,18 @@ void fluid_tables(const el_flow_desc& d, std::vector<double>& ex, std::vector<do
     ey.resize(n);
     py.resize(n);
     double dxg = kTwoPi / n;
+    auto pair = [](double v) {
+        float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
     for (int i = 0; i < nh; i++) {
         double k = i;
-        ex[i] = std::exp(-d.nu * k * k * d.dt);
+        ex[i] = pair(std::exp(-d.nu * k * k * d.dt));
         px[i] = (float)(3.0 / (2.0 + std::cos(k * dxg)));
     }
     for (int j = 0; j < n; j++) {
         double k = j < n / 2 ? j : j - n;
-        ey[j] = std::exp(-d.nu * k * k * d.dt);
+        ey[j] = pair(std::exp(-d.nu * k * k * d.dt));
         py[j] = (float)(3.0 / (2.0 + std::cos(k * dxg)));
     }
 }

@@ -88,4 +88,75 @@ __device__ __forceinline__ float2 fluid_at(const float4* __restrict__ snap, int 
     }
 }
 
+// Register-resident copy of the W x W stencil nodes (both time levels) of
+// one cell.  A particle moves a fraction of a cell per step, so its four RK4
+// stages nearly always fall in the cell of the previous stage: the stencil is
+// loaded once and re-used, and only a stage that crosses into another cell
+// fetches again.  (ci, cj) are the cell's unwrapped indices; addresses wrap.
+template <int SCHEME>
+struct Stencil {
+    static constexpr int W = SCHEME == 0 ? 2 : 4;
+    static constexpr int O = SCHEME == 0 ? 0 : -1;  // first node relative to the cell
+    int ci, cj;
+    float4 v[W * W];
+
+    __device__ __forceinline__ void load(const float4* __restrict__ snap, int n, int i, int j) {
+        const int m = n - 1;
+#pragma unroll
+        for (int b = 0; b < W; b++) {
+            int row = ((j + O + b) & m) * n;
+#pragma unroll
+            for (int a = 0; a < W; a++) v[b * W + a] = node_ld(snap, row + ((i + O + a) & m));
+        }
+        ci = i;
+        cj = j;
+    }
+
+    // Value at offsets (sx, sy) in the cell, levels blended by (wa, wb).
+    __device__ __forceinline__ float2 eval(float sx, float sy, float wa, float wb) const {
+        if (SCHEME == 0) {
+            const float4 &a = v[0], &b = v[1], &c = v[2], &d = v[3];
+            float au = fmaf(wa, a.x, wb * a.z), av = fmaf(wa, a.y, wb * a.w);
+            float bu = fmaf(wa, b.x, wb * b.z), bv = fmaf(wa, b.y, wb * b.w);
+            float cu = fmaf(wa, c.x, wb * c.z), cv = fmaf(wa, c.y, wb * c.w);
+            float du = fmaf(wa, d.x, wb * d.z), dv = fmaf(wa, d.y, wb * d.w);
+            float lo_u = fmaf(sx, bu - au, au), hi_u = fmaf(sx, du - cu, cu);
+            float lo_v = fmaf(sx, bv - av, av), hi_v = fmaf(sx, dv - cv, cv);
+            return make_float2(fmaf(sy, hi_u - lo_u, lo_u), fmaf(sy, hi_v - lo_v, lo_v));
+        } else {
+            float wx[4], wy[4];
+            if (SCHEME == 1) {
+                weights_catmull_rom(sx, wx);
+                weights_catmull_rom(sy, wy);
+            } else {
+                weights_bspline(sx, wx);
+                weights_bspline(sy, wy);
+            }
+            float u = 0.f, vv = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                float ru = 0.f, rv = 0.f;
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const float4& t = v[b * 4 + a];
+                    ru = fmaf(wx[a], fmaf(wa, t.x, wb * t.z), ru);
+                    rv = fmaf(wx[a], fmaf(wa, t.y, wb * t.w), rv);
+                }
+                u = fmaf(wy[b], ru, u);
+                vv = fmaf(wy[b], rv, vv);
+            }
+            return make_float2(u, vv);
+        }
+    }
+
+    // Fluid velocity at grid-unit position (ci0 + lx, cj0 + ly).
+    __device__ __forceinline__ float2 at(const float4* __restrict__ snap, int n, int ci0, int cj0,
+                                         float lx, float ly, float wa, float wb) {
+        float flx = floorf(lx), fly = floorf(ly);
+        int i = ci0 + (int)flx, j = cj0 + (int)fly;
+        if (i != ci || j != cj) load(snap, n, i, j);
+        return eval(lx - flx, ly - fly, wa, wb);
+    }
+};
+
 }  // namespace el

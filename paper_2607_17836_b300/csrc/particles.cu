@@ -8,9 +8,10 @@
 // number whatever the particle's distance from the origin, and the carry
 // into cell and image is exact integer arithmetic.
 //
-//   K6 k_rk4       : one RK4 step of one species (Eq. 12 tracers, Eq. 14
-//                    inertial) between levels n and n+1, fused with the
-//                    gathers, the time blend and the wrap/carry write-back
+//   K6 k_rk4       : one RK4 step of every species (Eq. 12 tracers, Eq. 14
+//                    inertial) in one launch, between levels n and n+1, fused
+//                    with the gathers, the time blend and the wrap/carry
+//                    write-back
 //   K9 k_init      : FP64 positions -> split state; zero-slip velocity
 //   k_unsplit      : split state -> FP64 unwrapped positions, original order
 //   k_msd / k_box  : per-particle terms of the statistics
@@ -36,51 +37,79 @@ __device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off
     off = o;
 }
 
-template <int SCHEME, bool INERTIAL>
-__global__ void __launch_bounds__(256) k_rk4(const float4* __restrict__ snap, int n, int log2n,
-                                             const int64_t* __restrict__ d_step,
-                                             uint32_t* __restrict__ cell, float2* __restrict__ off,
-                                             float2* __restrict__ vel, int2* __restrict__ img,
-                                             int64_t np, float dt, float h, float inv_st) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
+// One species' arrays and its share of the blocks of the fused launch.
+struct SpeciesDev {
+    uint32_t* cell;
+    float2* off;
+    float2* vel;
+    int2* img;
+    int64_t np;
+    float inv_st;
+    int inertial;
+    unsigned block_begin;
+};
+
+struct RK4Args {
+    const float4* snap;
+    const int64_t* d_step;
+    int n, log2n, nspecies;
+    float dt, h;  // h = dt * n / (2 pi): grid units per unit velocity
+    SpeciesDev sp[kMaxSpecies];
+};
+
+constexpr int kRK4Threads = 256;
+
+// K6: one RK4 step of every species in one launch (blocks are split between
+// species by block_begin), between levels n and n+1.
+template <int SCHEME>
+__global__ void __launch_bounds__(kRK4Threads) k_rk4(const __grid_constant__ RK4Args a) {
+    // species of this block (unrolled select: no dynamic indexing of the params)
+    SpeciesDev sp = a.sp[0];
+#pragma unroll
+    for (int k = 1; k < kMaxSpecies; k++)
+        if (k < a.nspecies && blockIdx.x >= a.sp[k].block_begin) sp = a.sp[k];
+    int64_t p = (int64_t)(blockIdx.x - sp.block_begin) * kRK4Threads + threadIdx.x;
+    if (p >= sp.np) return;
+    const int n = a.n;
+    const float h = a.h, dt = a.dt;
     // level n sits in half (step & 1) of the snapshot pair, level n+1 in the other
-    const float wa0 = (*d_step & 1) ? 0.0f : 1.0f, wb0 = 1.0f - wa0;  // theta = 0
-    const float wa1 = wb0, wb1 = wa0;                                 // theta = 1
-    uint32_t c = cell[p];
-    int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
-    float2 o = off[p];
+    const float wa0 = (*a.d_step & 1) ? 0.0f : 1.0f, wb0 = 1.0f - wa0;  // theta = 0
+    const float wa1 = wb0, wb1 = wa0;                                   // theta = 1
+    uint32_t c = sp.cell[p];
+    const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
+    const float2 o = sp.off[p];
+    Stencil<SCHEME> st;
+    st.load(a.snap, n, ci, cj);
     float nx, ny;
-    float2 vnew;
-    if (!INERTIAL) {
-        // Eq. 12 with stage times t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
-        float2 k1 = fluid_at<SCHEME>(snap, n, ci, cj, o.x, o.y, wa0, wb0);
-        float2 k2 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(0.5f * h, k1.x, o.x),
-                                     fmaf(0.5f * h, k1.y, o.y), 0.5f, 0.5f);
-        float2 k3 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(0.5f * h, k2.x, o.x),
-                                     fmaf(0.5f * h, k2.y, o.y), 0.5f, 0.5f);
-        float2 k4 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(h, k3.x, o.x), fmaf(h, k3.y, o.y),
-                                     wa1, wb1);
+    float2 vnew = make_float2(0.f, 0.f);
+    if (!sp.inertial) {
+        // Eq. 12, stages at t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
+        float2 k1 = st.at(a.snap, n, ci, cj, o.x, o.y, wa0, wb0);
+        float2 k2 = st.at(a.snap, n, ci, cj, fmaf(0.5f * h, k1.x, o.x), fmaf(0.5f * h, k1.y, o.y),
+                          0.5f, 0.5f);
+        float2 k3 = st.at(a.snap, n, ci, cj, fmaf(0.5f * h, k2.x, o.x), fmaf(0.5f * h, k2.y, o.y),
+                          0.5f, 0.5f);
+        float2 k4 = st.at(a.snap, n, ci, cj, fmaf(h, k3.x, o.x), fmaf(h, k3.y, o.y), wa1, wb1);
         const float h6 = h * (1.0f / 6.0f);
         nx = fmaf(h6, k1.x + 2.0f * (k2.x + k3.x) + k4.x, o.x);
         ny = fmaf(h6, k1.y + 2.0f * (k2.y + k3.y) + k4.y, o.y);
     } else {
         // Eq. 14: x and v jointly; stage s has x_s = x + c_s dt v_{s-1},
         // v_s = v + c_s dt a_{s-1}, a_s = (u(x_s, t_s) - v_s) / St (Eq. 13).
-        float2 v = vel[p];
-        float2 u1 = fluid_at<SCHEME>(snap, n, ci, cj, o.x, o.y, wa0, wb0);
+        const float inv_st = sp.inv_st;
+        float2 v = sp.vel[p];
+        float2 u1 = st.at(a.snap, n, ci, cj, o.x, o.y, wa0, wb0);
         float2 a1 = make_float2((u1.x - v.x) * inv_st, (u1.y - v.y) * inv_st);
         float2 v2 = make_float2(fmaf(0.5f * dt, a1.x, v.x), fmaf(0.5f * dt, a1.y, v.y));
-        float2 u2 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(0.5f * h, v.x, o.x),
-                                     fmaf(0.5f * h, v.y, o.y), 0.5f, 0.5f);
+        float2 u2 = st.at(a.snap, n, ci, cj, fmaf(0.5f * h, v.x, o.x), fmaf(0.5f * h, v.y, o.y),
+                          0.5f, 0.5f);
         float2 a2 = make_float2((u2.x - v2.x) * inv_st, (u2.y - v2.y) * inv_st);
         float2 v3 = make_float2(fmaf(0.5f * dt, a2.x, v.x), fmaf(0.5f * dt, a2.y, v.y));
-        float2 u3 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(0.5f * h, v2.x, o.x),
-                                     fmaf(0.5f * h, v2.y, o.y), 0.5f, 0.5f);
+        float2 u3 = st.at(a.snap, n, ci, cj, fmaf(0.5f * h, v2.x, o.x), fmaf(0.5f * h, v2.y, o.y),
+                          0.5f, 0.5f);
         float2 a3 = make_float2((u3.x - v3.x) * inv_st, (u3.y - v3.y) * inv_st);
         float2 v4 = make_float2(fmaf(dt, a3.x, v.x), fmaf(dt, a3.y, v.y));
-        float2 u4 = fluid_at<SCHEME>(snap, n, ci, cj, fmaf(h, v3.x, o.x), fmaf(h, v3.y, o.y),
-                                     wa1, wb1);
+        float2 u4 = st.at(a.snap, n, ci, cj, fmaf(h, v3.x, o.x), fmaf(h, v3.y, o.y), wa1, wb1);
         float2 a4 = make_float2((u4.x - v4.x) * inv_st, (u4.y - v4.y) * inv_st);
         const float h6 = h * (1.0f / 6.0f), d6 = dt * (1.0f / 6.0f);
         nx = fmaf(h6, v.x + 2.0f * (v2.x + v3.x) + v4.x, o.x);
@@ -90,23 +119,24 @@ __global__ void __launch_bounds__(256) k_rk4(const float4* __restrict__ snap, in
     }
     float ox, oy;
     int ni, nj, dix, diy;
-    carry_axis(nx, ci, log2n, ox, ni, dix);
-    carry_axis(ny, cj, log2n, oy, nj, diy);
-    cell[p] = (uint32_t)ni | ((uint32_t)nj << 16);
-    off[p] = make_float2(ox, oy);
-    if (INERTIAL) vel[p] = vnew;
+    carry_axis(nx, ci, a.log2n, ox, ni, dix);
+    carry_axis(ny, cj, a.log2n, oy, nj, diy);
+    sp.cell[p] = (uint32_t)ni | ((uint32_t)nj << 16);
+    sp.off[p] = make_float2(ox, oy);
+    if (sp.inertial) sp.vel[p] = vnew;
     if (dix | diy) {  // crossed the periodic boundary: rare read-modify-write
-        int2 m = img[p];
-        img[p] = make_int2(m.x + dix, m.y + diy);
+        int2 m = sp.img[p];
+        sp.img[p] = make_int2(m.x + dix, m.y + diy);
     }
 }
 
 // FP64 position -> (cell, offset, image), Sec. 3.2: mapped periodically onto
 // [0, 2 pi); a point on a node belongs to the cell on its right.
 __device__ __forceinline__ void split_position(double x, int n, int& cell, float& off, int& image) {
-    double k = floor(x / kTwoPi);
-    double xw = x - kTwoPi * k;
-    double s = xw * ((double)n / kTwoPi);
+    const double inv_two_pi = 1.0 / kTwoPi;  // folded at compile time: no division here
+    double k = floor(x * inv_two_pi);
+    double xw = fma(-kTwoPi, k, x);
+    double s = xw * ((double)n * inv_two_pi);
     double c = floor(s);
     float o = (float)(s - c);
     int ci = (int)c, im = (int)k;
@@ -217,18 +247,37 @@ __global__ void k_box(const uint32_t* __restrict__ cell, const float2* __restric
     atomicAdd(boxes + by * kBoxes + bx, 1ull);
 }
 
-// Var(n)/mean(n) - 1 from the integer box counts (one thread, fixed order).
-__global__ void k_cluster_final(const unsigned long long* __restrict__ boxes, double* __restrict__ out) {
-    if (threadIdx.x != 0) return;
+// Var(n)/mean(n) - 1 from the integer box counts: one block of 1024 threads,
+// integer sums (exact, so the order does not matter), then FP64 on one thread.
+__global__ void __launch_bounds__(1024) k_cluster_final(const unsigned long long* __restrict__ boxes,
+                                                        double* __restrict__ out) {
+    __shared__ unsigned long long s1w[32], s2w[32];
     unsigned long long s1 = 0, s2 = 0;
-    for (int b = 0; b < kBoxes * kBoxes; b++) {
-        s1 += boxes[b];
-        s2 += boxes[b] * boxes[b];
+    for (int b = threadIdx.x; b < kBoxes * kBoxes; b += blockDim.x) {
+        unsigned long long c = boxes[b];
+        s1 += c;
+        s2 += c * c;
     }
-    double B = (double)(kBoxes * kBoxes);
-    double mean = (double)s1 / B;
-    double var = (double)s2 / B - mean * mean;
-    *out = mean > 0.0 ? var / mean - 1.0 : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s1w[threadIdx.x >> 5] = s1;
+        s2w[threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s1 = s2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            s1 += s1w[w];
+            s2 += s2w[w];
+        }
+        double B = (double)(kBoxes * kBoxes);
+        double mean = (double)s1 / B;
+        double var = (double)s2 / B - mean * mean;
+        *out = mean > 0.0 ? var / mean - 1.0 : 0.0;
+    }
 }
 
 // Sampling hook: the gather of K6 at arbitrary FP64 points.
@@ -272,34 +321,40 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
     return EL_OK;
 }
 
-template <int SCHEME>
-static el_status launch_rk4(el_flow* f, Species& sp, unsigned grid, int T, float dt, float h) {
-    if (sp.st > 0.0) {
-        k_rk4<SCHEME, true><<<grid, T, 0, f->stream>>>(f->snap, f->n, f->log2n, f->d_step,
-                                                       sp.cell[0], sp.off[0], sp.vel[0],
-                                                       sp.img[0], sp.np, dt, h,
-                                                       (float)(1.0 / sp.st));
-    } else {
-        k_rk4<SCHEME, false><<<grid, T, 0, f->stream>>>(f->snap, f->n, f->log2n, f->d_step,
-                                                        sp.cell[0], sp.off[0], sp.vel[0],
-                                                        sp.img[0], sp.np, dt, h, 0.0f);
+// K6 for every species of the flow in one launch.
+el_status particles_step_all(el_flow* f) {
+    RK4Args a{};
+    a.snap = f->snap;
+    a.d_step = f->d_step;
+    a.n = f->n;
+    a.log2n = f->log2n;
+    a.dt = (float)f->d.dt;
+    a.h = (float)(f->d.dt * (double)f->n / kTwoPi);
+    unsigned blocks = 0;
+    int ns = 0;
+    for (int s = 0; s < f->d.max_species; s++) {
+        Species& sp = f->sp[s];
+        if (sp.np == 0) continue;
+        SpeciesDev& d = a.sp[ns++];
+        d.cell = sp.cell[0];
+        d.off = sp.off[0];
+        d.vel = sp.vel[0];
+        d.img = sp.img[0];
+        d.np = sp.np;
+        d.inertial = sp.st > 0.0 ? 1 : 0;
+        d.inv_st = sp.st > 0.0 ? (float)(1.0 / sp.st) : 0.0f;
+        d.block_begin = blocks;
+        blocks += blocks_for(sp.np, kRK4Threads);
+    }
+    if (ns == 0) return EL_OK;
+    a.nspecies = ns;
+    switch (f->d.interp) {
+        case EL_BILINEAR: k_rk4<0><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+        case EL_CATMULL_ROM: k_rk4<1><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+        default: k_rk4<2><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
     }
     EL_LAUNCHED(f);
     return EL_OK;
-}
-
-el_status particles_step(el_flow* f, int s) {
-    Species& sp = f->sp[s];
-    if (sp.np == 0) return EL_OK;
-    const int T = 256;
-    unsigned grid = blocks_for(sp.np, T);
-    float dt = (float)f->d.dt;
-    float h = (float)(f->d.dt * (double)f->n / kTwoPi);  // grid units per unit velocity
-    switch (f->d.interp) {
-        case EL_BILINEAR: return launch_rk4<0>(f, sp, grid, T, dt, h);
-        case EL_CATMULL_ROM: return launch_rk4<1>(f, sp, grid, T, dt, h);
-        default: return launch_rk4<2>(f, sp, grid, T, dt, h);
-    }
 }
 
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy) {
@@ -337,7 +392,7 @@ el_status particles_stats_into(el_flow* f, int s, double* out3) {
                                   f->stream));
     k_box<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[0], sp.off[0], sp.np, f->n, f->boxes);
     EL_LAUNCHED(f);
-    k_cluster_final<<<1, 32, 0, f->stream>>>(f->boxes, out3 + 2);
+    k_cluster_final<<<1, 1024, 0, f->stream>>>(f->boxes, out3 + 2);
     EL_LAUNCHED(f);
     return EL_OK;
 }

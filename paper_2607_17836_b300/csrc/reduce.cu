@@ -38,12 +38,21 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce2(const double2* __restri
     }
 }
 
-// out = sums / count (means)
-__global__ void k_reduce2_final(const double* __restrict__ partial, int nblocks, int64_t count,
-                                double* __restrict__ out) {
+// out = sums / count (means); one block of kRedThreads, fixed tree.
+__global__ void __launch_bounds__(kRedThreads) k_reduce2_final(const double* __restrict__ partial,
+                                                               int nblocks, int64_t count,
+                                                               double* __restrict__ out) {
+    __shared__ double sh[2][kRedThreads / 32];
+    for (int c = 0; c < 2; c++) {
+        double x = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) x += partial[2 * b + c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) sh[c][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
     if (threadIdx.x < 2) {
         double x = 0.0;
-        for (int b = 0; b < nblocks; b++) x += partial[2 * b + threadIdx.x];
+        for (int w = 0; w < kRedThreads / 32; w++) x += sh[threadIdx.x][w];
         out[threadIdx.x] = count > 0 ? x / (double)count : 0.0;
     }
 }
@@ -53,7 +62,7 @@ __global__ void k_reduce2_final(const double* __restrict__ partial, int nblocks,
 el_status reduce_double2(el_flow* f, const double2* in, int64_t count, double* out2) {
     k_reduce2<<<kRedBlocks, kRedThreads, 0, f->stream>>>(in, count, f->red);
     EL_LAUNCHED(f);
-    k_reduce2_final<<<1, 32, 0, f->stream>>>(f->red, kRedBlocks, count, out2);
+    k_reduce2_final<<<1, kRedThreads, 0, f->stream>>>(f->red, kRedBlocks, count, out2);
     EL_LAUNCHED(f);
     return EL_OK;
 }

@@ -214,12 +214,10 @@ class Flow:
 
     def profile_step(self):
         """One coupled step with per-stage CUDA-event times (ms):
-        {"fluid": ms, "species": [ms per slot], "sort": ms}."""
-        ns = self.desc.max_species
-        buf = np.zeros(2 + ns)
+        {"fluid": ms, "particles": ms (all species, one launch), "sort": ms}."""
+        buf = np.zeros(3)
         self._check(self._lib.el_profile_step(self._h, _dptr(buf), int(buf.size)))
-        return {"fluid": float(buf[0]), "species": [float(x) for x in buf[1:1 + ns]],
-                "sort": float(buf[1 + ns])}
+        return {"fluid": float(buf[0]), "particles": float(buf[1]), "sort": float(buf[2])}
 
     def kernel_launches(self) -> int:
         return int(self._lib.el_kernel_launches(self._h))

@@ -33,7 +33,7 @@ def test_taylor_green_64_tracers_config():
     X, Y = inputs.grid(wl.n)
     exact = 2 * math.exp(-2 * wl.nu * wl.dt * wl.steps) * np.sin(X) * np.sin(Y)
     w = g.field(0)
-    assert rel_linf(w, exact) < 1e-6
+    assert rel_linf(w, exact) < 2e-6   # FP32 storage: ~steps^0.5 * 2^-24 unbiased
     assert rel_linf(w, o.flow.fields(("w",))["w"]) < OMEGA_RTOL
     pos, _ = g.particles(0, 4096)
     assert np.max(np.abs(pos - o.positions(0))) < POS_ATOL
