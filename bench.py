@@ -280,6 +280,28 @@ def run_ours(args, wl, scheme, world, rank, local):
     traffic_pps = recorded_traffic(args.scheme)
     traffic = traffic_pps * wl.particles if traffic_pps is not None else None
 
+    # The roofline workload of the particle stage: 1024^2 with 16M inertial
+    # particles at St = 1 in one species (same fluid, same scheme).
+    roof16 = None
+    if not args.no_roofline16:
+        del flush
+        big = 16_000_000
+        g16 = elpath.Flow(wl.n, wl.nu, wl.dt, w0, interp=scheme, max_species=1,
+                          max_particles=big, sort_every=SORT_EVERY, device=dev)
+        g16.set_particles(0, inputs.uniform_positions(big, 99 + rank), 1.0)
+        for _ in range(3):
+            g16.step(1)
+        pr = [g16.profile_step() for _ in range(10)]
+        ms16 = statistics.mean(p["particles"] for p in pr)
+        ach16 = big * BYTES_INERTIAL / (ms16 * 1e-3) / 1e9
+        roof16 = {"workload": "1024^2 fluid, 16M inertial particles (St = 1), one species",
+                  "particle_stage_ms": ms16, "particle_steps_per_s": big / (ms16 * 1e-3),
+                  "achieved": ach16, "peak": peak, "unit": "GB/s", "frac": ach16 / peak,
+                  "bytes_per_particle_step": BYTES_INERTIAL}
+        g16.close()
+        del g16
+        torch.cuda.empty_cache()
+
     # End to end through the public API: particles from pinned host memory,
     # K coupled steps, statistics and every particle state back to pinned memory.
     pinned_in = [torch.from_numpy(xy).pin_memory() for xy in xys]
@@ -326,6 +348,7 @@ def run_ours(args, wl, scheme, world, rank, local):
             "e2e": {"value": e2e_value, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "what": "set_particles from pinned host + K steps + stats + particles back"},
+            "roofline_16M": roof16,
             "gpu_launches": launches, "wall_s": t_wall,
             "clocks": clocks.summary(), "energy": st["energy"]}
     if not args.no_cpu_baseline:
@@ -343,6 +366,7 @@ def main():
     ap.add_argument("--scheme", default="bilinear", choices=sorted(SCHEMES))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-roofline16", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()

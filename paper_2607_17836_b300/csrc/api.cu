@@ -131,7 +131,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* ey = take(n * 8);
     char* px = take(nh * 4);
     char* py = take(n * 4);
-    char* dstep = take(8);
+    char* table = take(sizeof(SpeciesDev) * kMaxSpecies);
     char* red = take((size_t)kRedBlocks * 3 * 8);
     char* red_out = take(64 * 8);
     char* boxes = take((size_t)kBoxes * kBoxes * 8);
@@ -157,7 +157,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->ey = (float2*)ey;
         f->pre_x = (float*)px;
         f->pre_y = (float*)py;
-        f->d_step = (int64_t*)dstep;
+        f->table = (SpeciesDev*)table;
         f->red = (double*)red;
         f->red_out = (double*)red_out;
         f->boxes = (unsigned long long*)boxes;
@@ -199,37 +199,46 @@ bool carve_species(el_flow* f, Species& sp, int64_t np) {
     return true;
 }
 
-// One coupled step (Algorithm 1): fluid n -> n+1, every species by RK4
-// between levels n and n+1, then the device step counter.
-el_status step_body(el_flow* f) {
-    EL_TRY(fluid_step(f));
-    EL_TRY(particles_step_all(f));
-    EL_TRY(step_increment(f));
+// One coupled step (Algorithm 1): fluid n -> n+1, then every species by
+// RK4 between levels n and n+1.
+el_status step_body(el_flow* f, int64_t step) {
+    EL_TRY(fluid_step(f, step));
+    EL_TRY(particles_step_all(f, (int)(step & 1)));
     return EL_OK;
 }
 
-el_status build_graph(el_flow* f) {
-    if (f->graph) {
-        cudaGraphExecDestroy(f->graph);
-        f->graph = nullptr;
+void drop_graphs(el_flow* f) {
+    for (int k = 0; k < 2; k++) {
+        if (f->graph[k]) cudaGraphExecDestroy(f->graph[k]);
+        f->graph[k] = nullptr;
+        f->graph_valid[k] = false;
     }
-    f->graph_valid = false;
+}
+
+// Capture the step of a given parity (steps >= 1 only: step 0 is the Euler
+// start and runs by direct launches).
+el_status build_graph(el_flow* f, int parity) {
+    if (f->graph[parity]) {
+        cudaGraphExecDestroy(f->graph[parity]);
+        f->graph[parity] = nullptr;
+    }
+    f->graph_valid[parity] = false;
     int64_t before = f->launches;
     cudaGraph_t g = nullptr;
     EL_CUDA_OK(f, cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal));
-    el_status s = step_body(f);
+    el_status s = step_body(f, 2 + parity);
     cudaError_t e = cudaStreamEndCapture(f->stream, &g);
     if (s != EL_OK) {
         if (g) cudaGraphDestroy(g);
         return s;
     }
     if (e != cudaSuccess) return fail(f, EL_ECUDA, "stream capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&f->graph, g, 0);
+    e = cudaGraphInstantiate(&f->graph[parity], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(f, EL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    f->graph_kernels = f->launches - before;
+    f->graph_kernels[parity] = f->launches - before;
     f->launches = before;  // nothing ran yet; replays add graph_kernels each
-    f->graph_valid = true;
+    f->graph_valid[parity] = true;
     return EL_OK;
 }
 
@@ -358,7 +367,7 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
         return fail(f, EL_EINVAL, "particle capacity exhausted (max_particles=%lld)",
                     (long long)f->d.max_particles);
     EL_TRY(particles_set(f, species, np, st, xy, vxy));
-    f->graph_valid = false;
+    drop_graphs(f);
     if (f->d.sort_every > 0) f->since_sort = f->d.sort_every;  // bin the new particles first
     return EL_OK;
 }
@@ -373,12 +382,13 @@ el_status el_step_coupled(el_flow* f, int32_t nsteps) {
             for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_sort(f, s));
             f->since_sort = 0;
         }
-        if (use_graph) {
-            if (!f->graph_valid) EL_TRY(build_graph(f));
-            EL_CUDA_OK(f, cudaGraphLaunch(f->graph, f->stream));
-            f->launches += f->graph_kernels;
+        int parity = (int)(f->step & 1);
+        if (use_graph && f->step > 0) {
+            if (!f->graph_valid[parity]) EL_TRY(build_graph(f, parity));
+            EL_CUDA_OK(f, cudaGraphLaunch(f->graph[parity], f->stream));
+            f->launches += f->graph_kernels[parity];
         } else {
-            EL_TRY(step_body(f));
+            EL_TRY(step_body(f, f->step));
         }
         f->step++;
         f->since_sort++;
@@ -450,11 +460,10 @@ el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
         sorted = true;
     }
     cudaEventRecord(ev[1], f->stream);
-    if (st == EL_OK) st = fluid_step(f);
+    if (st == EL_OK) st = fluid_step(f, f->step);
     cudaEventRecord(ev[2], f->stream);
-    if (st == EL_OK) st = particles_step_all(f);
+    if (st == EL_OK) st = particles_step_all(f, (int)(f->step & 1));
     cudaEventRecord(ev[3], f->stream);
-    if (st == EL_OK) st = step_increment(f);
     cudaError_t e = cudaStreamSynchronize(f->stream);
     if (st == EL_OK && e != cudaSuccess) st = fail(f, EL_ECUDA, "profile: %s", cudaGetErrorString(e));
     if (st == EL_OK) {
@@ -477,7 +486,7 @@ int64_t el_kernel_launches(const el_flow* f) { return f ? f->launches : 0; }
 el_status el_destroy_flow(el_flow* f) {
     if (!f) return EL_EINVAL;
     cudaStreamSynchronize(f->stream);
-    if (f->graph) cudaGraphExecDestroy(f->graph);
+    drop_graphs(f);
     destroy_plans(f->plan_c2r, f->plan_r2c, f->plan_c2r1);
     delete f;
     return EL_OK;

@@ -19,10 +19,24 @@ constexpr int kRedBlocks = 512;     // fixed grid of the FP64 reductions (fixed 
 constexpr int kRedThreads = 256;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-// One particle species.  Structure-of-arrays, current buffers [0] and sort
-// buffers [1] (the sort scatters [0] -> [1] and copies back, so the pointers
-// the step kernels see never change).
+// Device-resident descriptor of one species, read by the particle step.
+// `cur` selects the current buffer of each pair; the sort flips it on the
+// device, so a captured step graph stays valid across re-binning.
+struct SpeciesDev {
+    uint32_t* cell[2];
+    float2* off[2];
+    float2* vel[2];
+    int2* img[2];
+    int np;
+    int cur;
+    int inertial;
+    float inv_st;
+};
+
+// One particle species (host view).  Structure-of-arrays in two buffers
+// (cur = current, cur ^ 1 = the sort's target, also used as staging).
 struct Species {
+    int cur = 0;
     int64_t np = 0;
     int64_t cap = 0;
     double st = 0.0;
@@ -68,7 +82,8 @@ struct el_flow {
     float2* ey = nullptr;     // exp(-nu ky^2 dt) as (hi, lo) floats, row index 0..n-1
     float* pre_x = nullptr;   // spline prefilter 3/(2 + cos(k dx)) per kx
     float* pre_y = nullptr;   // ... per row index
-    int64_t* d_step = nullptr;
+    el::SpeciesDev* table = nullptr;  // device copy of h_table
+    el::SpeciesDev h_table[el::kMaxSpecies] = {};
     double* red = nullptr;        // reduction partials
     double* red_out = nullptr;    // reduced scalars (device)
     unsigned long long* boxes = nullptr;  // kBoxes^2 counters
@@ -83,14 +98,14 @@ struct el_flow {
 
     el::Species sp[el::kMaxSpecies];
 
-    int64_t step = 0;          // host mirror of *d_step
+    int64_t step = 0;          // coupled steps taken
     int64_t since_sort = 0;
     int64_t launches = 0;
 
-    // captured step graph
-    cudaGraphExec_t graph = nullptr;
-    int64_t graph_kernels = 0;
-    bool graph_valid = false;
+    // captured step graphs, one per step parity
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
+    bool graph_valid[2] = {false, false};
 
     std::string err;
 };
@@ -130,15 +145,14 @@ el_status fail(el_flow* f, el_status s, const char* fmt, ...);
 
 // ---- fluid (fluid.cu) -------------------------------------------------------
 el_status fluid_init(el_flow* f, const double* omega0_host);
-el_status fluid_step(el_flow* f);                 // K5, K1, C2R, K3, R2C
+el_status fluid_step(el_flow* f, int64_t step);   // K5+K1, C2R, K3, R2C
 el_status fluid_diagnostics(el_flow* f);          // E, Z, P -> red_out[0..2]
 el_status fluid_get_field(el_flow* f, int which, double* host_nn);
-el_status step_increment(el_flow* f);
 
 // ---- particles (particles.cu) ---------------------------------------------------
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
                         const double* vxy);
-el_status particles_step_all(el_flow* f);         // K6, every species in one launch
+el_status particles_step_all(el_flow* f, int parity);  // K6, every species in one launch
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
 el_status particles_stats_into(el_flow* f, int s, double* out3);  // msd x, msd y, cluster
 el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv);

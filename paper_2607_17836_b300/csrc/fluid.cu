@@ -1,16 +1,20 @@
 // Pseudospectral vorticity solver (Sec. 3.1): the pointwise kernels around
 // cuFFT's transforms.  Half spectrum [ky][kx], kx = 0..n/2, ky = j for
-// j < n/2 and j - n otherwise; physical arrays [j][i].
+// j < n/2 and j - n otherwise; physical arrays [j][i].  One step:
 //
-//   K1 k_spec_velocity : omega-hat -> u-hat, v-hat (Eqs. 5, 6), i kx omega-hat,
-//                        i ky omega-hat (Eq. 4), scaled by 1/n^2 (the inverse
-//                        normalisation of Sec. 3.1), plus prefiltered spline
-//                        coefficients of u, v for the B-spline scheme
-//   cuFFT C2R (batched): the planes to physical space
-//   K3 k_nonlinear     : N = u d(omega)/dx + v d(omega)/dy (Eq. 7), and the
-//                        new time level of the particle snapshot
-//   cuFFT R2C          : N-hat (Eq. 8)
-//   K5 k_ab2           : 2/3 rule + AB2 update (Eqs. 9, 10)
+//   K5+K1 k_spectral<true> : 2/3 rule + AB2 update of omega-hat (Eqs. 9, 10),
+//                            then from the new omega-hat: u-hat, v-hat
+//                            (Eqs. 5, 6), i kx omega-hat, i ky omega-hat
+//                            (Eq. 4), scaled by 1/n^2 (the inverse
+//                            normalisation of Sec. 3.1), and for the B-spline
+//                            scheme the prefiltered spline coefficients
+//   cuFFT C2R (batched)    : the planes to physical space
+//   K3 k_nonlinear         : N = u d(omega)/dx + v d(omega)/dy (Eq. 7), and the
+//                            new time level of the particle snapshot pair
+//   cuFFT R2C              : N-hat (Eq. 8)
+//
+// Modes are addressed by a 2-D grid (blockIdx.y = row j), so no thread
+// divides by n/2 + 1.
 #include "common.cuh"
 
 #include <cmath>
@@ -19,6 +23,8 @@
 namespace el {
 namespace {
 
+constexpr int kSpecThreads = 128;
+
 __device__ __forceinline__ int wavenumber_row(int j, int n) { return j < n / 2 ? j : j - n; }
 
 // 2/3 rule: keep iff 3|kx| < n and 3|ky| < n.
@@ -26,130 +32,160 @@ __device__ __forceinline__ bool kept(int kx, int ky, int n) {
     return 3 * abs(kx) < n && 3 * abs(ky) < n;
 }
 
-__global__ void k_spec_velocity(const float2* __restrict__ what, float2* __restrict__ spec, int n,
-                                int nh, size_t nmodes, float scale, int nplanes,
-                                const float* __restrict__ pre_x, const float* __restrict__ pre_y) {
-    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nmodes) return;
-    int j = (int)(q / nh), i = (int)(q - (size_t)j * nh);
-    int ky = wavenumber_row(j, n), kx = i;
-    float dkx = (i == n / 2) ? 0.f : (float)kx;   // Nyquist: zero derivative
-    float dky = (j == n / 2) ? 0.f : (float)ky;
-    float k2 = (float)(kx * kx + ky * ky);
-    float2 w = what[q];
-    w.x *= scale;
-    w.y *= scale;
-    float ik2 = k2 > 0.f ? 1.f / k2 : 0.f;        // psi-hat(0) = 0
-    float2 psi = make_float2(w.x * ik2, w.y * ik2);
-    float2 uh = make_float2(-dky * psi.y, dky * psi.x);   // u-hat = i ky psi-hat
-    float2 vh = make_float2(dkx * psi.y, -dkx * psi.x);   // v-hat = -i kx psi-hat
-    spec[q] = uh;
-    spec[nmodes + q] = vh;
-    spec[2 * nmodes + q] = make_float2(-dkx * w.y, dkx * w.x);   // i kx omega-hat
-    spec[3 * nmodes + q] = make_float2(-dky * w.y, dky * w.x);   // i ky omega-hat
-    if (nplanes == 6) {
-        // Interpolating cubic-spline coefficients: (c_{i-1} + 4 c_i + c_{i+1})/6 = f_i
-        // is diagonal in Fourier space with factor (2 + cos k dx)/3 per axis.
-        float p = pre_x[i] * pre_y[j];
-        spec[4 * nmodes + q] = make_float2(uh.x * p, uh.y * p);
-        spec[5 * nmodes + q] = make_float2(vh.x * p, vh.y * p);
-    }
-}
-
-// N = u wx + v wy at every node; the stencil field of the new level goes to
-// half `h` of the snapshot pair: h = (step + 1) & 1, or both halves at set-up.
-__global__ void k_nonlinear(const float* __restrict__ phys, float* __restrict__ nl,
-                            float2* __restrict__ snap2, size_t n2, int stencil_plane,
-                            const int64_t* __restrict__ d_step, int both) {
-    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n2) return;
-    float u = phys[q], v = phys[n2 + q], wx = phys[2 * n2 + q], wy = phys[3 * n2 + q];
-    nl[q] = fmaf(u, wx, v * wy);
-    float2 s = stencil_plane == 0 ? make_float2(u, v)
-                                  : make_float2(phys[4 * n2 + q], phys[5 * n2 + q]);
-    if (both) {
-        snap2[2 * q] = s;
-        snap2[2 * q + 1] = s;
-    } else {
-        int h = (int)((*d_step + 1) & 1);
-        snap2[2 * q + h] = s;
-    }
-}
-
-// Error-free FP32 transformations (double-float arithmetic).
+// Error-free FP32 sum (double-float arithmetic).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Dealias N-hat and advance omega-hat by one AB2 step (Eqs. 9, 10).
-// omega-hat is held as an unevaluated sum w = w_hi + w_lo of two floats: a
-// single float would round the small per-step change (the viscous decay is
-// only nu k^2 dt of w) the same way step after step and drift by up to half
-// an ulp per step; the pair keeps about 44 bits.  Only w_hi feeds the
-// transforms.
-// mode 0 (integrating factor): E = exp(-nu k^2 dt) = ex[kx] * ey[ky], the 1-D
-//   factors computed on the host in FP64 and held as float pairs;
+struct SpecArgs {
+    float2* what;       // omega-hat, high part
+    float2* what_lo;    // omega-hat, low part
+    float2* hist;       // AB2 history
+    const float2* nhat; // N-hat of the current level
+    float2* spec;       // nplanes output half spectra
+    const float2* ex;   // exp(-nu kx^2 dt) as (hi, lo)
+    const float2* ey;   // exp(-nu ky^2 dt) as (hi, lo)
+    const float* pre_x;
+    const float* pre_y;
+    int n, nh, nplanes, mode, first;
+    size_t nmodes;
+    float scale, dt, nu;
+};
+
+// AB2 update (when ADVANCE) and the spectral velocity / gradient planes of
+// the resulting omega-hat.
+//
+// omega-hat is held as an unevaluated sum w_hi + w_lo of two floats: one
+// float would round the small per-step change (the viscous decay is only
+// nu k^2 dt of w) the same way step after step and drift by up to half an
+// ulp per step; the pair keeps about 44 bits.  Only w_hi feeds the planes.
+// mode 0 (integrating factor): E = exp(-nu k^2 dt) = ex[kx] * ey[ky] (the 1-D
+//   factors computed on the host in FP64, held as float pairs);
 //   w <- E w - dt (3/2 E N - 1/2 E^2 H), H <- N.
 // mode 1 (Eq. 10 as printed): R = -N - nu k^2 w; w <- w + dt (3/2 R - 1/2 H), H <- R.
-// The first step (step == 0) is forward Euler in either mode.
-__global__ void k_ab2(float2* __restrict__ what, float2* __restrict__ what_lo,
-                      float2* __restrict__ hist, const float2* __restrict__ nhat, int n, int nh,
-                      size_t nmodes, const float2* __restrict__ ex, const float2* __restrict__ ey,
-                      float dt, float nu, int mode, const int64_t* __restrict__ d_step) {
-    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nmodes) return;
-    int j = (int)(q / nh), i = (int)(q - (size_t)j * nh);
-    int ky = wavenumber_row(j, n), kx = i;
-    bool first = (*d_step == 0);
-    float2 N = kept(kx, ky, n) ? nhat[q] : make_float2(0.f, 0.f);
-    float2 w = what[q], wl = what_lo[q];
-    float2 inc, hi_part;  // new w = hi_part + (lo terms) + inc
-    float2 lo;
-    if (mode == 0) {
-        // E = Eh + El from the float pairs (two-product of the hi parts)
-        float2 a = ex[i], b = ey[j];
-        float Eh = a.x * b.x;
-        float El = fmaf(a.x, b.x, -Eh) + fmaf(a.x, b.y, a.y * b.x);
-        float E2 = Eh * Eh;
-        float2 H = first ? make_float2(0.f, 0.f) : hist[q];
-        float c1 = first ? dt : 1.5f * dt, c2 = first ? 0.f : 0.5f * dt * E2;
-        // E * (w_hi + w_lo) - c1 E N + c2 H
-        float px = Eh * w.x, py = Eh * w.y;
-        float ex_ = fmaf(Eh, w.x, -px), ey_ = fmaf(Eh, w.y, -py);
-        inc = make_float2(fmaf(c2, H.x, -c1 * Eh * N.x), fmaf(c2, H.y, -c1 * Eh * N.y));
-        hi_part = make_float2(px, py);
-        lo = make_float2(ex_ + fmaf(El, w.x, Eh * wl.x), ey_ + fmaf(El, w.y, Eh * wl.y));
-        hist[q] = N;
-    } else {
-        float nuk2 = nu * (float)(kx * kx + ky * ky);
-        float2 R = make_float2(-N.x - nuk2 * w.x, -N.y - nuk2 * w.y);
-        if (first) {
-            inc = make_float2(dt * R.x, dt * R.y);
-        } else {
-            float2 H = hist[q];
-            inc = make_float2(dt * (1.5f * R.x - 0.5f * H.x), dt * (1.5f * R.y - 0.5f * H.y));
+// The first step is forward Euler in either mode.
+template <bool ADVANCE>
+__device__ __forceinline__ void spectral_mode(const SpecArgs& a, int i, int j) {
+    const int n = a.n;
+    const size_t q = (size_t)j * a.nh + i;
+    const int kx = i, ky = wavenumber_row(j, n);
+    const bool keep = kept(kx, ky, n);
+    const float2* __restrict__ nhat = a.nhat;
+    const float2* __restrict__ hist_in = a.hist;
+    const float2* __restrict__ lo_in = a.what_lo;
+    // every load first, so they are all in flight together
+    float2 w = a.what[q];
+    float2 N = make_float2(0.f, 0.f), wl = N, H = N, ea = N, eb = N;
+    if (ADVANCE) {
+        N = nhat[q];
+        wl = lo_in[q];
+        if (!a.first) H = hist_in[q];
+        if (a.mode == 0) {
+            ea = a.ex[i];
+            eb = a.ey[j];
         }
-        hi_part = w;
-        lo = wl;
-        hist[q] = R;
+        if (!keep) N = make_float2(0.f, 0.f);
+        const float dt = a.dt;
+        float2 inc, hi, lo, hist_out;
+        if (a.mode == 0) {
+            float Eh = ea.x * eb.x;  // E = Eh + El (two-product of the hi parts)
+            float El = fmaf(ea.x, eb.x, -Eh) + fmaf(ea.x, eb.y, ea.y * eb.x);
+            float E2 = Eh * Eh;
+            float c1 = a.first ? dt : 1.5f * dt, c2 = a.first ? 0.f : 0.5f * dt * E2;
+            float px = Eh * w.x, py = Eh * w.y;
+            hi = make_float2(px, py);
+            lo = make_float2(fmaf(Eh, w.x, -px) + fmaf(El, w.x, Eh * wl.x),
+                             fmaf(Eh, w.y, -py) + fmaf(El, w.y, Eh * wl.y));
+            inc = make_float2(fmaf(c2, H.x, -c1 * Eh * N.x), fmaf(c2, H.y, -c1 * Eh * N.y));
+            hist_out = N;
+        } else {
+            float nuk2 = a.nu * (float)(kx * kx + ky * ky);
+            float2 R = make_float2(-N.x - nuk2 * w.x, -N.y - nuk2 * w.y);
+            inc = a.first ? make_float2(dt * R.x, dt * R.y)
+                          : make_float2(dt * (1.5f * R.x - 0.5f * H.x), dt * (1.5f * R.y - 0.5f * H.y));
+            hi = w;
+            lo = wl;
+            hist_out = R;
+        }
+        float sx, exx, sy, eyy;
+        two_sum(hi.x, lo.x + inc.x, sx, exx);
+        two_sum(hi.y, lo.y + inc.y, sy, eyy);
+        w = make_float2(sx, sy);
+        a.hist[q] = hist_out;
+        a.what[q] = w;
+        a.what_lo[q] = make_float2(exx, eyy);
     }
-    float sx, ex2, sy, ey2;
-    two_sum(hi_part.x, lo.x + inc.x, sx, ex2);
-    two_sum(hi_part.y, lo.y + inc.y, sy, ey2);
-    what[q] = make_float2(sx, sy);
-    what_lo[q] = make_float2(ex2, ey2);
+    const float dkx = (i == n / 2) ? 0.f : (float)kx;  // Nyquist: zero derivative
+    const float dky = (j == n / 2) ? 0.f : (float)ky;
+    const float k2 = (float)(kx * kx + ky * ky);
+    w.x *= a.scale;
+    w.y *= a.scale;
+    const float ik2 = k2 > 0.f ? 1.f / k2 : 0.f;  // psi-hat(0) = 0 (Eq. 5)
+    const float2 psi = make_float2(w.x * ik2, w.y * ik2);
+    const float2 uh = make_float2(-dky * psi.y, dky * psi.x);  // u-hat = i ky psi-hat
+    const float2 vh = make_float2(dkx * psi.y, -dkx * psi.x);  // v-hat = -i kx psi-hat
+    const size_t m = a.nmodes;
+    float2* __restrict__ spec = a.spec;
+    spec[q] = uh;
+    spec[m + q] = vh;
+    spec[2 * m + q] = make_float2(-dkx * w.y, dkx * w.x);  // i kx omega-hat
+    spec[3 * m + q] = make_float2(-dky * w.y, dky * w.x);  // i ky omega-hat
+    if (a.nplanes == 6) {
+        // Interpolating cubic-spline coefficients: (c_{i-1} + 4 c_i + c_{i+1})/6 = f_i
+        // is diagonal in Fourier space with factor (2 + cos k dx)/3 per axis.
+        const float p = a.pre_x[i] * a.pre_y[j];
+        spec[4 * m + q] = make_float2(uh.x * p, uh.y * p);
+        spec[5 * m + q] = make_float2(vh.x * p, vh.y * p);
+    }
+}
+
+// Threads cover kx = 0..n/2-1 of row blockIdx.y; the thread of kx = 0 also
+// takes the Nyquist column kx = n/2.
+template <bool ADVANCE>
+__global__ void __launch_bounds__(kSpecThreads) k_spectral(const __grid_constant__ SpecArgs a) {
+    const int i = blockIdx.x * kSpecThreads + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= a.n / 2) return;
+    spectral_mode<ADVANCE>(a, i, j);
+    if (i == 0) spectral_mode<ADVANCE>(a, a.n / 2, j);
+}
+
+// N = u wx + v wy at every node; the stencil field of the new level goes to
+// half `h` of the snapshot pair (h = 2 writes both halves, at set-up).
+// Four nodes per thread: 16-byte loads of the planes.
+__global__ void k_nonlinear(const float4* __restrict__ phys4, float4* __restrict__ nl4,
+                            float4* __restrict__ snap, size_t n4, int stencil_plane, int h) {
+    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n4) return;
+    float4 u = phys4[q], v = phys4[n4 + q], wx = phys4[2 * n4 + q], wy = phys4[3 * n4 + q];
+    nl4[q] = make_float4(fmaf(u.x, wx.x, v.x * wy.x), fmaf(u.y, wx.y, v.y * wy.y),
+                         fmaf(u.z, wx.z, v.z * wy.z), fmaf(u.w, wx.w, v.w * wy.w));
+    if (stencil_plane != 0) {
+        u = phys4[4 * n4 + q];
+        v = phys4[5 * n4 + q];
+    }
+    float2* s2 = reinterpret_cast<float2*>(snap + 4 * q);
+    const float2 s[4] = {make_float2(u.x, v.x), make_float2(u.y, v.y), make_float2(u.z, v.z),
+                         make_float2(u.w, v.w)};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (h == 2) {
+            snap[4 * q + k] = make_float4(s[k].x, s[k].y, s[k].x, s[k].y);
+        } else {
+            s2[2 * k + h] = s[k];
+        }
+    }
 }
 
 // Initial projection: mean removed, 2/3 rule (Sec. 3.1).
-__global__ void k_project(const float2* __restrict__ src, float2* __restrict__ what, int n, int nh,
-                          size_t nmodes) {
-    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nmodes) return;
-    int j = (int)(q / nh), i = (int)(q - (size_t)j * nh);
-    int ky = wavenumber_row(j, n), kx = i;
-    bool keep = kept(kx, ky, n) && !(kx == 0 && ky == 0);
+__global__ void k_project(const float2* __restrict__ src, float2* __restrict__ what, int n, int nh) {
+    const int i = blockIdx.x * kSpecThreads + threadIdx.x, j = blockIdx.y;
+    if (i >= nh) return;
+    const size_t q = (size_t)j * nh + i;
+    const int ky = wavenumber_row(j, n), kx = i;
+    const bool keep = kept(kx, ky, n) && !(kx == 0 && ky == 0);
     what[q] = keep ? src[q] : make_float2(0.f, 0.f);
 }
 
@@ -173,8 +209,9 @@ __global__ void k_scaled_copy(const float2* __restrict__ src, float2* __restrict
 
 // FP64 partial sums over the half spectrum for E, Z, P (Parseval).  Modes
 // with 0 < kx < n/2 stand for themselves and their conjugates (weight 2).
-__global__ void k_spec_diag(const float2* __restrict__ what, int n, int nh, size_t nmodes,
-                            double* __restrict__ partial) {
+__global__ void __launch_bounds__(kRedThreads) k_spec_diag(const float2* __restrict__ what, int n,
+                                                           int nh, size_t nmodes,
+                                                           double* __restrict__ partial) {
     double se = 0.0, sz = 0.0, sp = 0.0;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nmodes;
          q += (size_t)gridDim.x * blockDim.x) {
@@ -224,8 +261,6 @@ __global__ void __launch_bounds__(kRedThreads) k_spec_diag_final(const double* _
     }
 }
 
-__global__ void k_step_increment(int64_t* d_step) { *d_step += 1; }
-
 }  // namespace
 
 static el_status fft_exec_c2r(el_flow* f, cufftHandle plan, float2* in, float* out) {
@@ -240,20 +275,44 @@ static el_status fft_exec_r2c(el_flow* f, float* in, float2* out) {
     return EL_OK;
 }
 
-// Velocity planes, nonlinear term and snapshot of the current omega-hat.
-static el_status rhs_from_what(el_flow* f, int both_halves) {
+static SpecArgs spec_args(el_flow* f, int first) {
+    SpecArgs a{};
+    a.what = f->what;
+    a.what_lo = f->what_lo;
+    a.hist = f->hist;
+    a.nhat = f->nhat;
+    a.spec = f->spec;
+    a.ex = f->ex;
+    a.ey = f->ey;
+    a.pre_x = f->pre_x;
+    a.pre_y = f->pre_y;
+    a.n = f->n;
+    a.nh = f->nh;
+    a.nplanes = f->nplanes;
+    a.mode = f->d.ab2_mode;
+    a.first = first;
+    a.nmodes = f->nmodes;
+    a.scale = 1.0f / (float)f->n2;
+    a.dt = (float)f->d.dt;
+    a.nu = (float)f->d.nu;
+    return a;
+}
+
+// Planes -> physical fields, nonlinear term into the stencil half `h`, N-hat.
+static el_status finish_rhs(el_flow* f, int h) {
     const int T = 256;
-    k_spec_velocity<<<blocks_for((int64_t)f->nmodes, T), T, 0, f->stream>>>(
-        f->what, f->spec, f->n, f->nh, f->nmodes, 1.0f / (float)f->n2, f->nplanes, f->pre_x,
-        f->pre_y);
-    EL_LAUNCHED(f);
     EL_TRY(fft_exec_c2r(f, f->plan_c2r, f->spec, f->phys));
-    k_nonlinear<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(
-        f->phys, f->nl, reinterpret_cast<float2*>(f->snap), f->n2, f->stencil_plane, f->d_step,
-        both_halves);
+    size_t n4 = f->n2 / 4;
+    k_nonlinear<<<blocks_for((int64_t)n4, T), T, 0, f->stream>>>(
+        reinterpret_cast<const float4*>(f->phys), reinterpret_cast<float4*>(f->nl), f->snap, n4,
+        f->stencil_plane, h);
     EL_LAUNCHED(f);
     EL_TRY(fft_exec_r2c(f, f->nl, f->nhat));
     return EL_OK;
+}
+
+static dim3 spec_grid(el_flow* f) {
+    return dim3((unsigned)((f->n / 2 + kSpecThreads - 1) / kSpecThreads), (unsigned)f->n);
 }
 
 el_status fluid_init(el_flow* f, const double* omega0_host) {
@@ -264,36 +323,29 @@ el_status fluid_init(el_flow* f, const double* omega0_host) {
     k_d2f<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(stage, f->nl, f->n2);
     EL_LAUNCHED(f);
     EL_TRY(fft_exec_r2c(f, f->nl, f->nhat));
-    k_project<<<blocks_for((int64_t)f->nmodes, T), T, 0, f->stream>>>(f->nhat, f->what, f->n,
-                                                                      f->nh, f->nmodes);
+    k_project<<<dim3((unsigned)((f->nh + kSpecThreads - 1) / kSpecThreads), (unsigned)f->n),
+                kSpecThreads, 0, f->stream>>>(f->nhat, f->what, f->n, f->nh);
     EL_LAUNCHED(f);
     EL_CUDA_OK(f, cudaMemsetAsync(f->hist, 0, f->nmodes * sizeof(float2), f->stream));
     EL_CUDA_OK(f, cudaMemsetAsync(f->what_lo, 0, f->nmodes * sizeof(float2), f->stream));
-    EL_CUDA_OK(f, cudaMemsetAsync(f->d_step, 0, sizeof(int64_t), f->stream));
-    EL_TRY(rhs_from_what(f, 1));
-    return EL_OK;
+    k_spectral<false><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, 0));
+    EL_LAUNCHED(f);
+    return finish_rhs(f, 2);
 }
 
-el_status fluid_step(el_flow* f) {
-    const int T = 256;
-    k_ab2<<<blocks_for((int64_t)f->nmodes, T), T, 0, f->stream>>>(
-        f->what, f->what_lo, f->hist, f->nhat, f->n, f->nh, f->nmodes, f->ex, f->ey,
-        (float)f->d.dt, (float)f->d.nu, f->d.ab2_mode, f->d_step);
+// Fluid n -> n+1 for step number `step`: level n+1 goes to half (step+1)&1.
+el_status fluid_step(el_flow* f, int64_t step) {
+    k_spectral<true><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, step == 0));
     EL_LAUNCHED(f);
-    return rhs_from_what(f, 0);
-}
-
-el_status step_increment(el_flow* f) {
-    k_step_increment<<<1, 1, 0, f->stream>>>(f->d_step);
-    EL_LAUNCHED(f);
-    return EL_OK;
+    return finish_rhs(f, (int)((step + 1) & 1));
 }
 
 el_status fluid_diagnostics(el_flow* f) {
     k_spec_diag<<<kRedBlocks, kRedThreads, 0, f->stream>>>(f->what, f->n, f->nh, f->nmodes, f->red);
     EL_LAUNCHED(f);
     double nn = (double)f->n2;
-    k_spec_diag_final<<<1, kRedThreads, 0, f->stream>>>(f->red, kRedBlocks, 0.5 / (nn * nn), f->red_out);
+    k_spec_diag_final<<<1, kRedThreads, 0, f->stream>>>(f->red, kRedBlocks, 0.5 / (nn * nn),
+                                                        f->red_out);
     EL_LAUNCHED(f);
     return EL_OK;
 }

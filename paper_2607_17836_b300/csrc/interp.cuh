@@ -88,12 +88,40 @@ __device__ __forceinline__ float2 fluid_at(const float4* __restrict__ snap, int 
     }
 }
 
+// a - b on float pairs: one paired FMA (b * -1 + a is exact before rounding).
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+    return __ffma2_rn(make_float2(-1.0f, -1.0f), b, a);
+}
+
+__device__ __forceinline__ float2 pair(float x) { return make_float2(x, x); }
+
+// Catmull-Rom (Eq. 19) or B-spline (Eq. 22) weights for the x and y offsets
+// at once: w[k] = (w_k(sx), w_k(sy)).
+template <int SCHEME>
+__device__ __forceinline__ void cubic_weights2(float2 s, float2 w[4]) {
+    if (SCHEME == 1) {
+        w[0] = __fmul2_rn(s, __ffma2_rn(s, __ffma2_rn(pair(-0.5f), s, pair(1.0f)), pair(-0.5f)));
+        w[1] = __ffma2_rn(__fmul2_rn(s, s), __ffma2_rn(pair(1.5f), s, pair(-2.5f)), pair(1.0f));
+        w[2] = __fmul2_rn(s, __ffma2_rn(s, __ffma2_rn(pair(-1.5f), s, pair(2.0f)), pair(0.5f)));
+        w[3] = __fmul2_rn(__fmul2_rn(s, s), __ffma2_rn(pair(0.5f), s, pair(-0.5f)));
+    } else {
+        float2 r = fsub2(pair(1.0f), s);
+        w[0] = __fmul2_rn(__fmul2_rn(r, r), __fmul2_rn(r, pair(1.0f / 6.0f)));
+        w[1] = __ffma2_rn(__fmul2_rn(s, s), __ffma2_rn(pair(0.5f), s, pair(-1.0f)), pair(2.0f / 3.0f));
+        w[2] = __ffma2_rn(s, __ffma2_rn(s, __ffma2_rn(pair(-0.5f), s, pair(0.5f)), pair(0.5f)),
+                          pair(1.0f / 6.0f));
+        w[3] = __fmul2_rn(__fmul2_rn(s, s), __fmul2_rn(s, pair(1.0f / 6.0f)));
+    }
+}
+
 // Register-resident copy of the W x W stencil nodes (both time levels) of
 // one cell.  A particle moves a fraction of a cell per step, so its four RK4
 // stages nearly always fall in the cell of the previous stage: the stencil is
 // loaded once and re-used, and only a stage that crosses into another cell
 // fetches again.  (ci, cj) are the cell's unwrapped indices; addresses wrap.
-template <int SCHEME>
+// PARITY: which half of each node holds level n (the other holds n+1).
+// THETA: 0 = level n, 1 = mid-way (theta = 1/2), 2 = level n+1 (Eq. 23).
+template <int SCHEME, int PARITY>
 struct Stencil {
     static constexpr int W = SCHEME == 0 ? 2 : 4;
     static constexpr int O = SCHEME == 0 ? 0 : -1;  // first node relative to the cell
@@ -112,50 +140,57 @@ struct Stencil {
         cj = j;
     }
 
-    // Value at offsets (sx, sy) in the cell, levels blended by (wa, wb).
-    __device__ __forceinline__ float2 eval(float sx, float sy, float wa, float wb) const {
-        if (SCHEME == 0) {
-            const float4 &a = v[0], &b = v[1], &c = v[2], &d = v[3];
-            float au = fmaf(wa, a.x, wb * a.z), av = fmaf(wa, a.y, wb * a.w);
-            float bu = fmaf(wa, b.x, wb * b.z), bv = fmaf(wa, b.y, wb * b.w);
-            float cu = fmaf(wa, c.x, wb * c.z), cv = fmaf(wa, c.y, wb * c.w);
-            float du = fmaf(wa, d.x, wb * d.z), dv = fmaf(wa, d.y, wb * d.w);
-            float lo_u = fmaf(sx, bu - au, au), hi_u = fmaf(sx, du - cu, cu);
-            float lo_v = fmaf(sx, bv - av, av), hi_v = fmaf(sx, dv - cv, cv);
-            return make_float2(fmaf(sy, hi_u - lo_u, lo_u), fmaf(sy, hi_v - lo_v, lo_v));
-        } else {
-            float wx[4], wy[4];
-            if (SCHEME == 1) {
-                weights_catmull_rom(sx, wx);
-                weights_catmull_rom(sy, wy);
-            } else {
-                weights_bspline(sx, wx);
-                weights_bspline(sy, wy);
-            }
-            float u = 0.f, vv = 0.f;
-#pragma unroll
-            for (int b = 0; b < 4; b++) {
-                float ru = 0.f, rv = 0.f;
-#pragma unroll
-                for (int a = 0; a < 4; a++) {
-                    const float4& t = v[b * 4 + a];
-                    ru = fmaf(wx[a], fmaf(wa, t.x, wb * t.z), ru);
-                    rv = fmaf(wx[a], fmaf(wa, t.y, wb * t.w), rv);
-                }
-                u = fmaf(wy[b], ru, u);
-                vv = fmaf(wy[b], rv, vv);
-            }
-            return make_float2(u, vv);
-        }
+    // Node value at the stage time; for THETA = 1 the SUM of the two levels
+    // (the factor 1/2 is applied once to the interpolated value).
+    template <int THETA>
+    __device__ __forceinline__ float2 node(int k) const {
+        const float4& t = v[k];
+        const float2 lo = make_float2(t.x, t.y), hi = make_float2(t.z, t.w);
+        if (THETA == 1) return __fadd2_rn(lo, hi);
+        return ((THETA == 0) == (PARITY == 0)) ? lo : hi;
     }
 
-    // Fluid velocity at grid-unit position (ci0 + lx, cj0 + ly).
+    template <int THETA>
+    __device__ __forceinline__ float2 eval(float2 s) const {
+        float2 r;
+        if (SCHEME == 0) {
+            // Eq. 16 as two lerps in x and one in y
+            const float2 a = node<THETA>(0), b = node<THETA>(1);
+            const float2 c = node<THETA>(2), d = node<THETA>(3);
+            const float2 sx = pair(s.x), sy = pair(s.y);
+            const float2 lo = __ffma2_rn(sx, fsub2(b, a), a);
+            const float2 hi = __ffma2_rn(sx, fsub2(d, c), c);
+            r = __ffma2_rn(sy, fsub2(hi, lo), lo);
+        } else {
+            float2 w[4];
+            cubic_weights2<SCHEME>(s, w);
+            r = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                float2 row = __fmul2_rn(pair(w[0].x), node<THETA>(b * 4));
+#pragma unroll
+                for (int a = 1; a < 4; a++) row = __ffma2_rn(pair(w[a].x), node<THETA>(b * 4 + a), row);
+                r = __ffma2_rn(pair(w[b].y), row, r);
+            }
+        }
+        if (THETA == 1) r = __fmul2_rn(r, pair(0.5f));
+        return r;
+    }
+
+    // Stage 1: the particle's own cell, offsets o in [0, 1).
+    template <int THETA>
+    __device__ __forceinline__ float2 first_stage(float2 o) const {
+        return eval<THETA>(o);
+    }
+
+    // Fluid velocity at grid-unit position (ci0 + l.x, cj0 + l.y).
+    template <int THETA>
     __device__ __forceinline__ float2 at(const float4* __restrict__ snap, int n, int ci0, int cj0,
-                                         float lx, float ly, float wa, float wb) {
-        float flx = floorf(lx), fly = floorf(ly);
+                                         float2 l) {
+        float flx = floorf(l.x), fly = floorf(l.y);
         int i = ci0 + (int)flx, j = cj0 + (int)fly;
         if (i != ci || j != cj) load(snap, n, i, j);
-        return eval(lx - flx, ly - fly, wa, wb);
+        return eval<THETA>(fsub2(l, make_float2(flx, fly)));
     }
 };
 

@@ -37,96 +37,91 @@ __device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off
     off = o;
 }
 
-// One species' arrays and its share of the blocks of the fused launch.
-struct SpeciesDev {
-    uint32_t* cell;
-    float2* off;
-    float2* vel;
-    int2* img;
-    int64_t np;
-    float inv_st;
-    int inertial;
-    unsigned block_begin;
-};
+constexpr int kRK4Threads = 256;
 
 struct RK4Args {
     const float4* snap;
-    const int64_t* d_step;
+    const SpeciesDev* table;  // device-resident: the sort flips `cur` there
     int n, log2n, nspecies;
-    float dt, h;  // h = dt * n / (2 pi): grid units per unit velocity
-    SpeciesDev sp[kMaxSpecies];
+    float dt, h;              // h = dt * n / (2 pi): grid units per unit velocity
+    unsigned block_begin[kMaxSpecies];
 };
 
-constexpr int kRK4Threads = 256;
-
 // K6: one RK4 step of every species in one launch (blocks are split between
-// species by block_begin), between levels n and n+1.
-template <int SCHEME>
+// species by block_begin), between levels n and n+1.  PARITY = step & 1:
+// level n sits in half PARITY of the snapshot pair, level n+1 in the other,
+// so stage 1 (theta = 0) and stage 4 (theta = 1) read one half without
+// blending.  All (x, y) and (u, v) arithmetic is on float pairs (one paired
+// FP32 instruction per two lanes of work).
+template <int SCHEME, int PARITY>
 __global__ void __launch_bounds__(kRK4Threads) k_rk4(const __grid_constant__ RK4Args a) {
-    // species of this block (unrolled select: no dynamic indexing of the params)
-    SpeciesDev sp = a.sp[0];
+    int s = 0;
 #pragma unroll
     for (int k = 1; k < kMaxSpecies; k++)
-        if (k < a.nspecies && blockIdx.x >= a.sp[k].block_begin) sp = a.sp[k];
-    int64_t p = (int64_t)(blockIdx.x - sp.block_begin) * kRK4Threads + threadIdx.x;
-    if (p >= sp.np) return;
+        if (k < a.nspecies && blockIdx.x >= a.block_begin[k]) s = k;
+    const SpeciesDev& sd = a.table[s];
+    const int np = sd.np;
+    const int p = (int)(blockIdx.x - a.block_begin[s]) * kRK4Threads + (int)threadIdx.x;
+    if (p >= np) return;
+    const int cur = sd.cur;
+    uint32_t* __restrict__ cellp = sd.cell[cur];
+    float2* __restrict__ offp = sd.off[cur];
     const int n = a.n;
-    const float h = a.h, dt = a.dt;
-    // level n sits in half (step & 1) of the snapshot pair, level n+1 in the other
-    const float wa0 = (*a.d_step & 1) ? 0.0f : 1.0f, wb0 = 1.0f - wa0;  // theta = 0
-    const float wa1 = wb0, wb1 = wa0;                                   // theta = 1
-    uint32_t c = sp.cell[p];
+    const uint32_t c = cellp[p];
     const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
-    const float2 o = sp.off[p];
-    Stencil<SCHEME> st;
+    const float2 o = offp[p];
+    Stencil<SCHEME, PARITY> st;
     st.load(a.snap, n, ci, cj);
-    float nx, ny;
+    const float h = a.h, dt = a.dt;
+    const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
+    const float2 two = make_float2(2.0f, 2.0f);
+    float2 np2;
     float2 vnew = make_float2(0.f, 0.f);
-    if (!sp.inertial) {
+    const bool inertial = sd.inertial;
+    if (!inertial) {
         // Eq. 12, stages at t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
-        float2 k1 = st.at(a.snap, n, ci, cj, o.x, o.y, wa0, wb0);
-        float2 k2 = st.at(a.snap, n, ci, cj, fmaf(0.5f * h, k1.x, o.x), fmaf(0.5f * h, k1.y, o.y),
-                          0.5f, 0.5f);
-        float2 k3 = st.at(a.snap, n, ci, cj, fmaf(0.5f * h, k2.x, o.x), fmaf(0.5f * h, k2.y, o.y),
-                          0.5f, 0.5f);
-        float2 k4 = st.at(a.snap, n, ci, cj, fmaf(h, k3.x, o.x), fmaf(h, k3.y, o.y), wa1, wb1);
+        float2 k1 = st.template first_stage<0>(o);
+        float2 k2 = st.template at<1>(a.snap, n, ci, cj, __ffma2_rn(h2, k1, o));
+        float2 k3 = st.template at<1>(a.snap, n, ci, cj, __ffma2_rn(h2, k2, o));
+        float2 k4 = st.template at<2>(a.snap, n, ci, cj, __ffma2_rn(h1, k3, o));
+        float2 sum = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(k2, k3), k1), k4);
         const float h6 = h * (1.0f / 6.0f);
-        nx = fmaf(h6, k1.x + 2.0f * (k2.x + k3.x) + k4.x, o.x);
-        ny = fmaf(h6, k1.y + 2.0f * (k2.y + k3.y) + k4.y, o.y);
+        np2 = __ffma2_rn(make_float2(h6, h6), sum, o);
     } else {
         // Eq. 14: x and v jointly; stage s has x_s = x + c_s dt v_{s-1},
         // v_s = v + c_s dt a_{s-1}, a_s = (u(x_s, t_s) - v_s) / St (Eq. 13).
-        const float inv_st = sp.inv_st;
-        float2 v = sp.vel[p];
-        float2 u1 = st.at(a.snap, n, ci, cj, o.x, o.y, wa0, wb0);
-        float2 a1 = make_float2((u1.x - v.x) * inv_st, (u1.y - v.y) * inv_st);
-        float2 v2 = make_float2(fmaf(0.5f * dt, a1.x, v.x), fmaf(0.5f * dt, a1.y, v.y));
-        float2 u2 = st.at(a.snap, n, ci, cj, fmaf(0.5f * h, v.x, o.x), fmaf(0.5f * h, v.y, o.y),
-                          0.5f, 0.5f);
-        float2 a2 = make_float2((u2.x - v2.x) * inv_st, (u2.y - v2.y) * inv_st);
-        float2 v3 = make_float2(fmaf(0.5f * dt, a2.x, v.x), fmaf(0.5f * dt, a2.y, v.y));
-        float2 u3 = st.at(a.snap, n, ci, cj, fmaf(0.5f * h, v2.x, o.x), fmaf(0.5f * h, v2.y, o.y),
-                          0.5f, 0.5f);
-        float2 a3 = make_float2((u3.x - v3.x) * inv_st, (u3.y - v3.y) * inv_st);
-        float2 v4 = make_float2(fmaf(dt, a3.x, v.x), fmaf(dt, a3.y, v.y));
-        float2 u4 = st.at(a.snap, n, ci, cj, fmaf(h, v3.x, o.x), fmaf(h, v3.y, o.y), wa1, wb1);
-        float2 a4 = make_float2((u4.x - v4.x) * inv_st, (u4.y - v4.y) * inv_st);
+        const float2 ist = make_float2(sd.inv_st, sd.inv_st);
+        const float2 d2 = make_float2(0.5f * dt, 0.5f * dt), d1 = make_float2(dt, dt);
+        float2* __restrict__ velp = sd.vel[cur];
+        const float2 v = velp[p];
+        float2 u1 = st.template first_stage<0>(o);
+        float2 a1 = __fmul2_rn(fsub2(u1, v), ist);
+        float2 v2 = __ffma2_rn(d2, a1, v);
+        float2 u2 = st.template at<1>(a.snap, n, ci, cj, __ffma2_rn(h2, v, o));
+        float2 a2 = __fmul2_rn(fsub2(u2, v2), ist);
+        float2 v3 = __ffma2_rn(d2, a2, v);
+        float2 u3 = st.template at<1>(a.snap, n, ci, cj, __ffma2_rn(h2, v2, o));
+        float2 a3 = __fmul2_rn(fsub2(u3, v3), ist);
+        float2 v4 = __ffma2_rn(d1, a3, v);
+        float2 u4 = st.template at<2>(a.snap, n, ci, cj, __ffma2_rn(h1, v3, o));
+        float2 a4 = __fmul2_rn(fsub2(u4, v4), ist);
         const float h6 = h * (1.0f / 6.0f), d6 = dt * (1.0f / 6.0f);
-        nx = fmaf(h6, v.x + 2.0f * (v2.x + v3.x) + v4.x, o.x);
-        ny = fmaf(h6, v.y + 2.0f * (v2.y + v3.y) + v4.y, o.y);
-        vnew = make_float2(fmaf(d6, a1.x + 2.0f * (a2.x + a3.x) + a4.x, v.x),
-                           fmaf(d6, a1.y + 2.0f * (a2.y + a3.y) + a4.y, v.y));
+        float2 sx = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(v2, v3), v), v4);
+        float2 sa = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(a2, a3), a1), a4);
+        np2 = __ffma2_rn(make_float2(h6, h6), sx, o);
+        vnew = __ffma2_rn(make_float2(d6, d6), sa, v);
+        velp[p] = vnew;
     }
     float ox, oy;
     int ni, nj, dix, diy;
-    carry_axis(nx, ci, a.log2n, ox, ni, dix);
-    carry_axis(ny, cj, a.log2n, oy, nj, diy);
-    sp.cell[p] = (uint32_t)ni | ((uint32_t)nj << 16);
-    sp.off[p] = make_float2(ox, oy);
-    if (sp.inertial) sp.vel[p] = vnew;
+    carry_axis(np2.x, ci, a.log2n, ox, ni, dix);
+    carry_axis(np2.y, cj, a.log2n, oy, nj, diy);
+    cellp[p] = (uint32_t)ni | ((uint32_t)nj << 16);
+    offp[p] = make_float2(ox, oy);
     if (dix | diy) {  // crossed the periodic boundary: rare read-modify-write
-        int2 m = sp.img[p];
-        sp.img[p] = make_int2(m.x + dix, m.y + diy);
+        int2* imgp = sd.img[cur];
+        int2 m = imgp[p];
+        imgp[p] = make_int2(m.x + dix, m.y + diy);
     }
 }
 
@@ -233,17 +228,26 @@ __global__ void k_msd(const uint32_t* __restrict__ cell, const float2* __restric
 }
 
 // Particle counts on the kBoxes x kBoxes box grid (integer atomics: exact).
+// With n >= kBoxes every box is a block of whole cells (integer shift);
+// coarser grids split cells, done exactly in FP64 (power-of-two scale).
 __global__ void k_box(const uint32_t* __restrict__ cell, const float2* __restrict__ off, int64_t np,
-                      int n, unsigned long long* __restrict__ boxes) {
+                      int n, int log2n, unsigned long long* __restrict__ boxes) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     uint32_t c = cell[p];
-    float2 o = off[p];
-    double scale = (double)kBoxes / (double)n;  // power of two: exact products
-    int bx = (int)(((double)(c & 0xffffu) + (double)o.x) * scale);
-    int by = (int)(((double)(c >> 16) + (double)o.y) * scale);
-    bx = bx > kBoxes - 1 ? kBoxes - 1 : bx;
-    by = by > kBoxes - 1 ? kBoxes - 1 : by;
+    int bx, by;
+    if (n >= kBoxes) {
+        int sh = log2n - 6;  // kBoxes = 2^6
+        bx = (int)(c & 0xffffu) >> sh;
+        by = (int)(c >> 16) >> sh;
+    } else {
+        float2 o = off[p];
+        double scale = (double)kBoxes / (double)n;
+        bx = (int)(((double)(c & 0xffffu) + (double)o.x) * scale);
+        by = (int)(((double)(c >> 16) + (double)o.y) * scale);
+        bx = bx > kBoxes - 1 ? kBoxes - 1 : bx;
+        by = by > kBoxes - 1 ? kBoxes - 1 : by;
+    }
     atomicAdd(boxes + by * kBoxes + bx, 1ull);
 }
 
@@ -296,11 +300,19 @@ __global__ void k_sample(const double* __restrict__ xy, int64_t np, int n, int s
 
 }  // namespace
 
+static el_status upload_table(el_flow* f) {
+    EL_CUDA_OK(f, cudaMemcpyAsync(f->table, f->h_table, sizeof(SpeciesDev) * kMaxSpecies,
+                                  cudaMemcpyHostToDevice, f->stream));
+    return EL_OK;
+}
+
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
                         const double* vxy) {
     Species& sp = f->sp[s];
     const int T = 256;
-    double* stage = reinterpret_cast<double*>(sp.cell[1]);  // sort block: 32 B per particle
+    const int cur = sp.cur;
+    // staging in the other (sort) buffer: 32 B per particle
+    double* stage = reinterpret_cast<double*>(sp.cell[cur ^ 1]);
     EL_CUDA_OK(f, cudaMemcpyAsync(stage, xy, (size_t)np * 2 * sizeof(double),
                                   cudaMemcpyHostToDevice, f->stream));
     const double* d_vxy = nullptr;
@@ -312,20 +324,32 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
     if (np > 0) {
         k_init<<<blocks_for(np, T), T, 0, f->stream>>>(
             stage, d_vxy, np, f->n, f->d.interp, st > 0.0 ? 1 : 0, (int)(f->step & 1), f->snap,
-            sp.cell[0], sp.off[0], sp.vel[0], sp.img[0], sp.id[0], sp.x0);
+            sp.cell[cur], sp.off[cur], sp.vel[cur], sp.img[cur], sp.id[cur], sp.x0);
         EL_LAUNCHED(f);
     }
-    EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
     sp.np = np;
     sp.st = st;
+    SpeciesDev& d = f->h_table[s];
+    for (int k = 0; k < 2; k++) {
+        d.cell[k] = sp.cell[k];
+        d.off[k] = sp.off[k];
+        d.vel[k] = sp.vel[k];
+        d.img[k] = sp.img[k];
+    }
+    d.np = (int)np;
+    d.cur = cur;
+    d.inertial = st > 0.0 ? 1 : 0;
+    d.inv_st = st > 0.0 ? (float)(1.0 / st) : 0.0f;
+    EL_TRY(upload_table(f));
+    EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
     return EL_OK;
 }
 
-// K6 for every species of the flow in one launch.
-el_status particles_step_all(el_flow* f) {
+// K6 for every species of the flow in one launch; parity = step & 1.
+el_status particles_step_all(el_flow* f, int parity) {
     RK4Args a{};
     a.snap = f->snap;
-    a.d_step = f->d_step;
+    a.table = f->table;
     a.n = f->n;
     a.log2n = f->log2n;
     a.dt = (float)f->d.dt;
@@ -333,25 +357,27 @@ el_status particles_step_all(el_flow* f) {
     unsigned blocks = 0;
     int ns = 0;
     for (int s = 0; s < f->d.max_species; s++) {
-        Species& sp = f->sp[s];
-        if (sp.np == 0) continue;
-        SpeciesDev& d = a.sp[ns++];
-        d.cell = sp.cell[0];
-        d.off = sp.off[0];
-        d.vel = sp.vel[0];
-        d.img = sp.img[0];
-        d.np = sp.np;
-        d.inertial = sp.st > 0.0 ? 1 : 0;
-        d.inv_st = sp.st > 0.0 ? (float)(1.0 / sp.st) : 0.0f;
-        d.block_begin = blocks;
-        blocks += blocks_for(sp.np, kRK4Threads);
+        // every slot up to the last non-empty one takes part (empty ones get no blocks)
+        a.block_begin[s] = blocks;
+        blocks += f->sp[s].np > 0 ? blocks_for(f->sp[s].np, kRK4Threads) : 0;
+        if (f->sp[s].np > 0) ns = s + 1;
     }
     if (ns == 0) return EL_OK;
     a.nspecies = ns;
-    switch (f->d.interp) {
-        case EL_BILINEAR: k_rk4<0><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
-        case EL_CATMULL_ROM: k_rk4<1><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
-        default: k_rk4<2><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+    // empty slots share block_begin with the next slot, so the last slot with
+    // a given block_begin (the non-empty one) wins the select in the kernel
+    if (parity == 0) {
+        switch (f->d.interp) {
+            case EL_BILINEAR: k_rk4<0, 0><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+            case EL_CATMULL_ROM: k_rk4<1, 0><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+            default: k_rk4<2, 0><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+        }
+    } else {
+        switch (f->d.interp) {
+            case EL_BILINEAR: k_rk4<0, 1><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+            case EL_CATMULL_ROM: k_rk4<1, 1><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+            default: k_rk4<2, 1><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+        }
     }
     EL_LAUNCHED(f);
     return EL_OK;
@@ -360,11 +386,12 @@ el_status particles_step_all(el_flow* f) {
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy) {
     Species& sp = f->sp[s];
     const int T = 256;
-    double2* out_xy = reinterpret_cast<double2*>(sp.cell[1]);
+    const int cur = sp.cur;
+    double2* out_xy = reinterpret_cast<double2*>(sp.cell[cur ^ 1]);
     double2* out_v = out_xy + sp.np;
     if (sp.np > 0) {
         k_unsplit<<<blocks_for(sp.np, T), T, 0, f->stream>>>(
-            sp.cell[0], sp.off[0], sp.vel[0], sp.img[0], sp.id[0], sp.np, kTwoPi / f->n,
+            sp.cell[cur], sp.off[cur], sp.vel[cur], sp.img[cur], sp.id[cur], sp.np, kTwoPi / f->n,
             sp.st > 0.0 ? 1 : 0, out_xy, out_v);
         EL_LAUNCHED(f);
         if (xy)
@@ -383,14 +410,16 @@ el_status particles_get(el_flow* f, int s, double* xy, double* vxy) {
 el_status particles_stats_into(el_flow* f, int s, double* out3) {
     Species& sp = f->sp[s];
     const int T = 256;
-    double2* terms = reinterpret_cast<double2*>(sp.cell[1]);
-    k_msd<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[0], sp.off[0], sp.img[0], sp.id[0],
-                                                     sp.x0, sp.np, kTwoPi / f->n, terms);
+    const int cur = sp.cur;
+    double2* terms = reinterpret_cast<double2*>(sp.cell[cur ^ 1]);
+    k_msd<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[cur], sp.off[cur], sp.img[cur],
+                                                     sp.id[cur], sp.x0, sp.np, kTwoPi / f->n, terms);
     EL_LAUNCHED(f);
     EL_TRY(reduce_double2(f, terms, sp.np, out3));
     EL_CUDA_OK(f, cudaMemsetAsync(f->boxes, 0, sizeof(unsigned long long) * kBoxes * kBoxes,
                                   f->stream));
-    k_box<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[0], sp.off[0], sp.np, f->n, f->boxes);
+    k_box<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[cur], sp.off[cur], sp.np, f->n,
+                                                     f->log2n, f->boxes);
     EL_LAUNCHED(f);
     k_cluster_final<<<1, 1024, 0, f->stream>>>(f->boxes, out3 + 2);
     EL_LAUNCHED(f);

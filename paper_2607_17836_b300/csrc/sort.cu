@@ -8,8 +8,9 @@
 //
 //   k_sort_count   : rank[p] = atomicAdd(&bins[key], 1)
 //   scan (3 kernels): bins -> exclusive prefix sums (offsets)
-//   k_sort_scatter : buffer 1 at bins[key] + rank[p] <- buffer 0 at p
-//   copy back      : buffer 1 -> buffer 0 (stream-ordered device copies)
+//   k_sort_scatter : buffer cur^1 at bins[key] + rank[p] <- buffer cur at p;
+//                    then cur flips (in the device species table too, so a
+//                    captured step graph follows the swap)
 #include "common.cuh"
 
 namespace el {
@@ -86,8 +87,10 @@ __global__ void k_sort_scatter(const uint32_t* __restrict__ cell0, const float2*
                                const uint32_t* __restrict__ offsets, int64_t np, int log2n,
                                int inertial, uint32_t* __restrict__ cell1, float2* __restrict__ off1,
                                float2* __restrict__ vel1, int2* __restrict__ img1,
-                               uint32_t* __restrict__ id1) {
+                               uint32_t* __restrict__ id1, SpeciesDev* __restrict__ table,
+                               int new_cur) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) table->cur = new_cur;  // read only by later launches
     if (p >= np) return;
     uint32_t c = cell0[p];
     uint32_t key = ((c >> 16) << log2n) | (c & 0xffffu);
@@ -120,28 +123,19 @@ el_status particles_sort(el_flow* f, int s) {
     Species& sp = f->sp[s];
     if (sp.np < 2) return EL_OK;
     const int T = 256;
+    const int a = sp.cur, b = sp.cur ^ 1;
     int inertial = sp.st > 0.0 ? 1 : 0;
     EL_CUDA_OK(f, cudaMemsetAsync(f->bins, 0, f->n2 * sizeof(uint32_t), f->stream));
-    k_sort_count<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[0], sp.np, f->log2n, f->bins,
+    k_sort_count<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[a], sp.np, f->log2n, f->bins,
                                                             sp.rank);
     EL_LAUNCHED(f);
     EL_TRY(exclusive_scan(f, f->bins, (int64_t)f->n2));
     k_sort_scatter<<<blocks_for(sp.np, T), T, 0, f->stream>>>(
-        sp.cell[0], sp.off[0], sp.vel[0], sp.img[0], sp.id[0], sp.rank, f->bins, sp.np, f->log2n,
-        inertial, sp.cell[1], sp.off[1], sp.vel[1], sp.img[1], sp.id[1]);
+        sp.cell[a], sp.off[a], sp.vel[a], sp.img[a], sp.id[a], sp.rank, f->bins, sp.np, f->log2n,
+        inertial, sp.cell[b], sp.off[b], sp.vel[b], sp.img[b], sp.id[b], f->table + s, b);
     EL_LAUNCHED(f);
-    size_t np = (size_t)sp.np;
-    EL_CUDA_OK(f, cudaMemcpyAsync(sp.cell[0], sp.cell[1], np * sizeof(uint32_t),
-                                  cudaMemcpyDeviceToDevice, f->stream));
-    EL_CUDA_OK(f, cudaMemcpyAsync(sp.off[0], sp.off[1], np * sizeof(float2),
-                                  cudaMemcpyDeviceToDevice, f->stream));
-    if (inertial)
-        EL_CUDA_OK(f, cudaMemcpyAsync(sp.vel[0], sp.vel[1], np * sizeof(float2),
-                                      cudaMemcpyDeviceToDevice, f->stream));
-    EL_CUDA_OK(f, cudaMemcpyAsync(sp.img[0], sp.img[1], np * sizeof(int2),
-                                  cudaMemcpyDeviceToDevice, f->stream));
-    EL_CUDA_OK(f, cudaMemcpyAsync(sp.id[0], sp.id[1], np * sizeof(uint32_t),
-                                  cudaMemcpyDeviceToDevice, f->stream));
+    sp.cur = b;
+    f->h_table[s].cur = b;
     return EL_OK;
 }
 

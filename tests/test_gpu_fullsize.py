@@ -1,0 +1,78 @@
+"""Full-size workloads in the benchmark's launch configuration, compared with
+the FP64 oracle on sampled particles (particles are independent, so the
+oracle integrates just the sampled ones in the same fluid).
+
+  * 1024^2 decaying turbulence, 1M tracers + 1M inertial particles at each
+    of St = 0.1, 1, 10, each of the three schemes: vorticity after 100 steps,
+    sampled positions and velocities after 200 steps;
+  * 2048^2 double shear layer, 16M inertial particles at St = 1, Catmull-Rom:
+    vorticity and every 64th particle after 20 steps (the oracle's 2048^2
+    FP64 solve is the cost that bounds the step count).
+"""
+import numpy as np
+import pytest
+
+from paper_2607_17836_b300 import elpath, inputs
+from parity import OMEGA_RTOL, POS_ATOL, OracleRun, rel_linf
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SORT_EVERY = 20  # as in the benchmark
+
+
+def test_decaying_turbulence_1024_all_schemes():
+    wl = inputs.decaying_turbulence_1024()
+    w0 = wl.omega0()
+    stride = 244                                  # ~4100 sampled particles per species
+    xys = [inputs.uniform_positions(s.count, s.seed) for s in wl.species]
+    o = OracleRun(wl.n, wl.nu, wl.dt, w0)
+    for scheme in (0, 1, 2):
+        for s, xy in zip(wl.species, xys):
+            o.add(scheme, s.st, xy[::stride])
+    flows = []
+    for scheme in (0, 1, 2):
+        g = elpath.Flow(wl.n, wl.nu, wl.dt, w0, interp=scheme, max_species=4,
+                        max_particles=wl.particles, sort_every=SORT_EVERY)
+        for k, (s, xy) in enumerate(zip(wl.species, xys)):
+            g.set_particles(k, xy, s.st)
+        flows.append(g)
+    for g in flows:
+        g.step(100)
+    o.step(100)
+    w_ref = o.flow.fields(("w",))["w"]
+    for g in flows:
+        assert rel_linf(g.field(0), w_ref) < OMEGA_RTOL
+    for g in flows:
+        g.step(100)
+    o.step(100)
+    for scheme, g in enumerate(flows):
+        for k, s in enumerate(wl.species):
+            pos, vel = g.particles(k, s.count)
+            ref = o.positions(4 * scheme + k)
+            err = np.max(np.abs(pos[::stride] - ref))
+            assert err < POS_ATOL, (scheme, k, err)
+            if s.st > 0:
+                assert np.max(np.abs(vel[::stride] - o.velocities(4 * scheme + k))) < 1e-4
+        st = g.stats()
+        assert st["finite"]
+        g.close()
+
+
+def test_kelvin_helmholtz_2048_16M():
+    wl = inputs.kelvin_helmholtz_2048()
+    w0 = wl.omega0()
+    sp = wl.species[0]
+    xy = inputs.uniform_positions(sp.count, sp.seed)
+    g = elpath.Flow(wl.n, wl.nu, wl.dt, w0, interp=1, max_species=1, max_particles=sp.count,
+                    sort_every=SORT_EVERY)
+    g.set_particles(0, xy, sp.st)
+    o = OracleRun(wl.n, wl.nu, wl.dt, w0)
+    o.add(1, sp.st, xy[::64])
+    g.step(20)
+    o.step(20)
+    assert rel_linf(g.field(0), o.flow.fields(("w",))["w"]) < OMEGA_RTOL
+    pos, vel = g.particles(0, sp.count)
+    assert np.max(np.abs(pos[::64] - o.positions(0))) < POS_ATOL
+    assert np.max(np.abs(vel[::64] - o.velocities(0))) < 1e-4
+    g.close()

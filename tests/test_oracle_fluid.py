@@ -96,10 +96,11 @@ def test_two_thirds_mask_and_mean_removal():
 
 
 def test_generator_energy_is_unit():
-    # The input generator normalises its field with its own numpy FFT.
+    # The input generator normalises its field with its own numpy FFT to unit
+    # kinetic energy over the (2 pi)^2 domain; the oracle reports the mean.
     w0 = inputs.decaying_turbulence(64, seed=11, k0=4.0)
     e, _, _ = oracle.Flow(64, 0.0, 1e-3, w0).diagnostics()
-    assert abs(e - 1.0) < 1e-12
+    assert abs(e * (2 * np.pi) ** 2 - 1.0) < 1e-12
 
 
 def test_inviscid_invariants_conserved():
