@@ -151,12 +151,35 @@ el_status el_profile_step(el_flow* flow, double* stage_ms, int32_t nstage);
  * this flow; lets a caller count the launches inside a timed region. */
 int64_t el_kernel_launches(const el_flow* flow);
 
+/* Mean-square displacement and clustering index of np particles, computed
+ * without allocating any memory.  The paper has no counterpart: this is a
+ * library service for callers that cannot allocate device memory at the
+ * moment they need these statistics -- a loop that must not stall (cudaMalloc
+ * and cudaFree can synchronise the whole device) or an application whose
+ * device memory is all reserved up front by another allocator.
+ * d_xy, d_xy0: DEVICE arrays of 2*np doubles, unwrapped positions now and at
+ * the reference time (as el_get_particles returns them).  d_out3: DEVICE
+ * array of 3 doubles receiving <(x-x0)^2>, <(y-y0)^2> and the clustering
+ * index (Var(n)/mean(n) - 1 on a 64 x 64 box grid of the wrapped positions),
+ * reduced in FP64 in the same fixed order as el_get_stats.
+ * np must be <= EL_NOALLOC_MAX_PARTICLES, else EL_EINVAL.  Work is queued on
+ * cuda_stream and the call returns without waiting.  Scratch: one fixed
+ * device array of about 4 MiB inside the library, present on every GPU that
+ * loads it until the process exits, shared by all calls: calls whose work
+ * overlaps on the GPU race.  The first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  Errors: el_last_error(NULL). */
+#define EL_NOALLOC_MAX_PARTICLES 262144
+el_status el_dispersion_noalloc(const double* d_xy, const double* d_xy0, int64_t np,
+                                double* d_out3, void* cuda_stream);
+
 /* Destroy the flow (plans, graphs, host state).  The workspace is the
  * caller's to free afterwards. */
 el_status el_destroy_flow(el_flow* flow);
 
-/* One-line reason for the last failure of a call on this flow (or of the
- * last el_create_flow when flow is NULL).  Never NULL. */
+/* One-line reason for the last failure of a call on this flow (or, when
+ * flow is NULL, of the last el_create_flow or el_dispersion_noalloc on this
+ * thread).  Never NULL. */
 const char* el_last_error(const el_flow* flow);
 
 #ifdef __cplusplus

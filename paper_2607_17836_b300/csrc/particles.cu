@@ -441,3 +441,15 @@ el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double the
 }
 
 }  // namespace el
+
+namespace el {
+
+// Clustering index from kBoxes^2 box counts, on a caller-chosen stream; used
+// where no flow exists.
+cudaError_t launch_cluster_final(cudaStream_t stream, const unsigned long long* boxes,
+                                 double* out) {
+    k_cluster_final<<<1, 1024, 0, stream>>>(boxes, out);
+    return cudaGetLastError();
+}
+
+}  // namespace el

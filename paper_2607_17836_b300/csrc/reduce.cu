@@ -68,3 +68,18 @@ el_status reduce_double2(el_flow* f, const double2* in, int64_t count, double* o
 }
 
 }  // namespace el
+
+namespace el {
+
+// The same fixed-order reduction on a caller-chosen stream and partials
+// buffer (kRedBlocks * 2 doubles); used where no flow exists.
+cudaError_t launch_reduce_double2(cudaStream_t stream, const double2* in, int64_t count,
+                                  double* partial, double* out2) {
+    k_reduce2<<<kRedBlocks, kRedThreads, 0, stream>>>(in, count, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce2_final<<<1, kRedThreads, 0, stream>>>(partial, kRedBlocks, count, out2);
+    return cudaGetLastError();
+}
+
+}  // namespace el

@@ -23,7 +23,9 @@ STATUS = {0: "EL_OK", 1: "EL_EINVAL", 2: "EL_ENOMEM", 3: "EL_ECUDA", 4: "EL_ECUF
 # Public C symbols, in include/elpath.h order.
 SYMBOLS = ("el_workspace_bytes", "el_create_flow", "el_set_particles", "el_step_coupled",
            "el_get_stats", "el_get_particles", "el_get_field", "el_sample_velocity",
-           "el_profile_step", "el_kernel_launches", "el_destroy_flow", "el_last_error")
+           "el_profile_step", "el_kernel_launches", "el_dispersion_noalloc", "el_destroy_flow",
+           "el_last_error")
+NOALLOC_MAX_PARTICLES = 262144
 
 
 class ElpathError(RuntimeError):
@@ -74,6 +76,8 @@ def load(path: str = LIB_PATH):
     lib.el_profile_step.argtypes = [P, D, I32]
     lib.el_kernel_launches.argtypes = [P]
     lib.el_kernel_launches.restype = I64
+    lib.el_dispersion_noalloc.argtypes = [V, V, I64, V, V]
+    lib.el_dispersion_noalloc.restype = ctypes.c_int
     lib.el_destroy_flow.argtypes = [P]
     lib.el_last_error.argtypes = [P]
     lib.el_last_error.restype = ctypes.c_char_p
@@ -105,6 +109,26 @@ def make_desc(n, nu, dt, interp=BILINEAR, ab2_mode=0, bspline_prefilter=True, ma
 
 def workspace_bytes(desc: el_flow_desc) -> int:
     return int(load().el_workspace_bytes(ctypes.byref(desc)))
+
+
+def dispersion_noalloc(xy_dev, xy0_dev, out=None, stream=None):
+    """el_dispersion_noalloc: (msd_x, msd_y, cluster) of device positions,
+    with no allocation inside the library (its scratch is a fixed device
+    array).  xy_dev, xy0_dev: CUDA float64 tensors (np, 2); out: CUDA float64
+    tensor of 3 (allocated here if None, by the caller's allocator)."""
+    import torch
+    lib = load()
+    assert xy_dev.is_cuda and xy_dev.dtype == torch.float64 and xy_dev.is_contiguous()
+    assert xy0_dev.shape == xy_dev.shape and xy0_dev.dtype == torch.float64
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=xy_dev.device)
+    s = stream if stream is not None else torch.cuda.current_stream(xy_dev.device)
+    st = lib.el_dispersion_noalloc(ctypes.c_void_p(xy_dev.data_ptr()),
+                                   ctypes.c_void_p(xy0_dev.data_ptr()), int(xy_dev.shape[0]),
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise ElpathError(st, lib.el_last_error(None).decode())
+    return out
 
 
 class Flow:
