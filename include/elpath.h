@@ -147,9 +147,58 @@ el_status el_sample_velocity(el_flow* flow, int64_t np, const double* d_xy, doub
  * nstage must be >= 3. */
 el_status el_profile_step(el_flow* flow, double* stage_ms, int32_t nstage);
 
+/* Launch-shape and re-binning settings of a flow.  None of them changes any
+ * result: every particle's arithmetic is independent of the order particles
+ * are stored in and of the block shape. */
+typedef struct {
+    int32_t rk4_threads;  /* threads per block of the particle step: multiple of 32, 64..512 */
+    int32_t sort_every;   /* re-bin every k steps (0 = never)                                  */
+    int32_t sort_shift;   /* re-binning key = tile of 2^shift x 2^shift cells (0..4)           */
+    double ms_per_step;   /* filled by the autotuners: measured time per step of the choice   */
+} el_tuning;
+
+el_status el_get_tuning(const el_flow* flow, el_tuning* out);
+el_status el_set_tuning(el_flow* flow, const el_tuning* tuning);
+
+/* Autotuner: times trial windows of real steps (at least trial_steps, and two
+ * re-binning periods) for block sizes {128, 256, 512}, then cadences
+ * {0, 5, 10, 20, 40}, then tiles {1, 2, 4} cells, keeps the fastest and
+ * applies it.  The trial steps advance the simulation like any others.
+ * Synchronises the stream. */
+el_status el_autotune(el_flow* flow, int32_t trial_steps, el_tuning* best);
+
 /* Number of kernel launches of the library (not cuFFT) issued so far by
  * this flow; lets a caller count the launches inside a timed region. */
 int64_t el_kernel_launches(const el_flow* flow);
+
+/* ---- Batched engine --------------------------------------------------------
+ * Many independent flows (any grid sizes, species mixes, schemes and step
+ * counts) advanced together: one coupled step of the batch is one captured
+ * graph with one persistent kernel per stage over all members and every
+ * member's transforms on concurrent branches.  A member's arithmetic is the
+ * same as when it is stepped alone.  While in a batch a flow uses the batch's
+ * stream, el_step_coupled on it returns EL_ESTATE, and the other calls on it
+ * (particles, statistics, fields) work as usual.  Members join and leave at
+ * any step (continuous batching); each keeps its own step count. */
+typedef struct el_batch el_batch;
+
+/* Device workspace bytes of a batch of up to max_members flows (its tables). */
+size_t el_batch_workspace_bytes(int32_t max_members);
+el_status el_batch_create(int32_t max_members, void* dev_workspace, size_t workspace_bytes,
+                          void* cuda_stream, el_batch** out);
+/* Add a flow (same device; synchronises the flow's stream first). */
+el_status el_batch_add(el_batch* batch, el_flow* flow);
+/* Remove a member (synchronises the batch stream; the flow gets its own stream back). */
+el_status el_batch_remove(el_batch* batch, el_flow* flow);
+/* Advance every member by nsteps coupled steps, asynchronously on the batch stream. */
+el_status el_batch_step(el_batch* batch, int32_t nsteps);
+/* el_autotune over the whole batch (one setting for every member). */
+el_status el_batch_autotune(el_batch* batch, int32_t trial_steps, el_tuning* best);
+int32_t el_batch_size(const el_batch* batch);
+int64_t el_batch_kernel_launches(const el_batch* batch);
+const char* el_batch_last_error(const el_batch* batch);
+/* Remove every member and free the batch's host state. */
+el_status el_batch_destroy(el_batch* batch);
 
 /* Mean-square displacement and clustering index of np particles, computed
  * without allocating any memory.  The paper has no counterpart: this is a

@@ -13,6 +13,8 @@
 
 namespace el {
 
+void batch_member_changed(el_batch* b);
+
 void fluid_tables(const el_flow_desc& d, std::vector<float2>& ex, std::vector<float2>& ey,
                   std::vector<float>& px, std::vector<float>& py);
 
@@ -291,6 +293,7 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     if (!f) return fail(nullptr, EL_ENOMEM, "host allocation failed");
     f->d = *desc;
     f->stream = (cudaStream_t)cuda_stream;
+    f->own_stream = f->stream;
     cudaGetDevice(&f->device);
     f->n = desc->n;
     f->nh = desc->n / 2 + 1;
@@ -368,12 +371,14 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
                     (long long)f->d.max_particles);
     EL_TRY(particles_set(f, species, np, st, xy, vxy));
     drop_graphs(f);
+    batch_member_changed(f->batch);
     if (f->d.sort_every > 0) f->since_sort = f->d.sort_every;  // bin the new particles first
     return EL_OK;
 }
 
 el_status el_step_coupled(el_flow* f, int32_t nsteps) {
     if (!f) return EL_EINVAL;
+    if (f->batch) return fail(f, EL_ESTATE, "flow belongs to a batch: step it with el_batch_step");
     if (nsteps < 0) return fail(f, EL_EINVAL, "nsteps < 0");
     static const bool no_graph = std::getenv("ELPATH_NO_GRAPH") != nullptr;
     bool use_graph = f->stream != nullptr && !no_graph;
@@ -448,6 +453,7 @@ el_status el_sample_velocity(el_flow* f, int64_t np, const double* d_xy, double 
 
 el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
     if (!f || !stage_ms) return EL_EINVAL;
+    if (f->batch) return fail(f, EL_ESTATE, "flow belongs to a batch");
     if (nstage < 3) return fail(f, EL_EINVAL, "nstage must be >= 3");
     cudaEvent_t ev[4];
     for (int k = 0; k < 4; k++) EL_CUDA_OK(f, cudaEventCreate(&ev[k]));
@@ -483,8 +489,125 @@ el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
 
 int64_t el_kernel_launches(const el_flow* f) { return f ? f->launches : 0; }
 
+el_status el_get_tuning(const el_flow* f, el_tuning* out) {
+    if (!f || !out) return EL_EINVAL;
+    out->rk4_threads = f->rk4_threads;
+    out->sort_every = f->d.sort_every;
+    out->sort_shift = f->sort_shift;
+    out->ms_per_step = 0.0;
+    return EL_OK;
+}
+
+el_status el_set_tuning(el_flow* f, const el_tuning* t) {
+    if (!f || !t) return EL_EINVAL;
+    if (t->rk4_threads < 64 || t->rk4_threads > 512 || t->rk4_threads % 32)
+        return fail(f, EL_EINVAL, "rk4_threads must be a multiple of 32 in [64, 512]");
+    if (t->sort_every < 0) return fail(f, EL_EINVAL, "sort_every must be >= 0");
+    if (t->sort_shift < 0 || t->sort_shift > 4 || (1 << t->sort_shift) > f->n / 4)
+        return fail(f, EL_EINVAL, "sort_shift out of range");
+    f->rk4_threads = t->rk4_threads;
+    f->d.sort_every = t->sort_every;
+    f->sort_shift = t->sort_shift;
+    drop_graphs(f);
+    batch_member_changed(f->batch);
+    return EL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Milliseconds per step of `window` steps after two untimed ones, with
+// CUDA events on `stream` (re-binning included where it falls due).
+template <class StepFn>
+el_status time_steps(StepFn step, cudaStream_t stream, int window, double* ms, char* why) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return EL_ECUDA;
+    el_status s = step(2);
+    if (s == EL_OK) {
+        cudaEventRecord(a, stream);
+        s = step(window);
+        cudaEventRecord(b, stream);
+    }
+    if (s == EL_OK && cudaEventSynchronize(b) == cudaSuccess) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        *ms = t / window;
+    } else if (s == EL_OK) {
+        s = EL_ECUDA;
+        snprintf(why, 128, "event synchronize failed");
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return s;
+}
+
+// Coordinate search over the particle step's block size, then the
+// re-binning cadence, then the re-binning tile.  None of them changes any
+// result (every particle's arithmetic is independent of order and launch
+// shape), so the trial steps are ordinary steps of the simulation.
+template <class StepFn, class ApplyFn>
+el_status autotune(StepFn step, ApplyFn apply, cudaStream_t stream, el_tuning start, int trial,
+                   el_tuning* best_out, int n) {
+    char why[128] = {0};
+    el_tuning best = start;
+    double best_ms = 1e30;
+    auto trial_of = [&](el_tuning t) -> el_status {
+        EL_TRY(apply(t));
+        int window = std::max(trial, 2 * t.sort_every);
+        double ms = 0.0;
+        EL_TRY(time_steps(step, stream, window, &ms, why));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+        return EL_OK;
+    };
+    const int threads[] = {128, 256, 512};
+    const int cadence[] = {0, 5, 10, 20, 40};
+    const int shifts[] = {0, 1, 2};
+    for (int th : threads) {
+        el_tuning t = best;
+        t.rk4_threads = th;
+        EL_TRY(trial_of(t));
+    }
+    for (int c : cadence) {
+        el_tuning t = best;
+        t.sort_every = c;
+        if (c == best.sort_every && best_ms < 1e30) continue;
+        EL_TRY(trial_of(t));
+    }
+    if (best.sort_every > 0)
+        for (int sh : shifts) {
+            if ((1 << sh) > n / 4 || sh == best.sort_shift) continue;
+            el_tuning t = best;
+            t.sort_shift = sh;
+            EL_TRY(trial_of(t));
+        }
+    EL_TRY(apply(best));
+    best.ms_per_step = best_ms;
+    *best_out = best;
+    return EL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+el_status el_autotune(el_flow* f, int32_t trial_steps, el_tuning* best) {
+    if (!f || !best) return EL_EINVAL;
+    if (f->batch) return fail(f, EL_ESTATE, "flow belongs to a batch: use el_batch_autotune");
+    if (trial_steps < 1) return fail(f, EL_EINVAL, "trial_steps must be >= 1");
+    el_tuning start{};
+    el_get_tuning(f, &start);
+    auto step = [f](int n) { return el_step_coupled(f, n); };
+    auto apply = [f](el_tuning t) { return el_set_tuning(f, &t); };
+    return autotune(step, apply, f->stream, start, trial_steps, best, f->n);
+}
+
 el_status el_destroy_flow(el_flow* f) {
     if (!f) return EL_EINVAL;
+    if (f->batch) el_batch_remove(f->batch, f);
     cudaStreamSynchronize(f->stream);
     drop_graphs(f);
     destroy_plans(f->plan_c2r, f->plan_r2c, f->plan_c2r1);

@@ -1,0 +1,582 @@
+// Batched engine: many independent simulations (flows of any grid size,
+// species mix, scheme and step count) advanced together.  One coupled step of
+// the batch is one captured CUDA graph:
+//
+//   k_batch_spectral  (persistent, every member's modes)   AB2 + velocity planes
+//   cuFFT C2R per member, on forked branches (they run concurrently)
+//   k_batch_nonlinear (persistent, every member's nodes)   nonlinear term + snapshot
+//   cuFFT R2C per member, on forked branches
+//   k_batch_rk4       (persistent, every member's species) RK4 particle step
+//   k_batch_advance                                        per-member step counters
+//
+// The per-element arithmetic is the single-flow kernels' (stages.cuh), so a
+// member's results do not depend on what else is in the batch.  Each member
+// keeps its own step counter on the device (members join and leave at any
+// step), so the same graph serves every step until the membership changes.
+// Re-binning runs per member, outside the graph, when it is due.
+#include "common.cuh"
+#include "stages.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+namespace el {
+
+// Fluid and particle parameters of one member, device-resident.
+struct MemberDev {
+    SpecArgs spec;          // arrays and constants of k_spectral (first from `step`)
+    const float4* phys4;
+    float4* nl4;
+    float4* snap;
+    unsigned long long n4;  // n^2 / 4
+    int stencil_plane, n, log2n, scheme;
+    float dt, h;
+    long long step;
+};
+
+struct BatchArgs {
+    MemberDev* members;
+    const int* spec_begin;            // task prefix sums, nmembers + 1
+    const int* nl_begin;
+    const int* rk_begin;              // nentries + 1
+    const int* rk_member;             // member of each (member, species) entry
+    const SpeciesDev* const* rk_sp;   // that member's device species descriptor
+    int nmembers, nentries;
+    int spec_tasks, nl_tasks, rk_tasks;
+};
+
+namespace {
+
+constexpr int kBSpecThreads = 128;
+constexpr int kBNlThreads = 256;
+constexpr int kSideStreams = 4;
+
+// Largest k in [0, count) with begin[k] <= t (begin ascending, begin[0] = 0).
+__device__ __forceinline__ int owner_of(const int* __restrict__ begin, int count, int t) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__host__ __device__ __forceinline__ int spec_chunks(int n) {
+    int c = (n / 2) / kBSpecThreads;
+    return c < 1 ? 1 : c;
+}
+
+__global__ void __launch_bounds__(kBSpecThreads) k_batch_spectral(const __grid_constant__ BatchArgs b) {
+    for (int t = blockIdx.x; t < b.spec_tasks; t += gridDim.x) {
+        const int m = owner_of(b.spec_begin, b.nmembers, t);
+        const MemberDev& md = b.members[m];
+        const int local = t - b.spec_begin[m];
+        const int chunks = spec_chunks(md.n);
+        const int j = local / chunks, i = (local - j * chunks) * kBSpecThreads + threadIdx.x;
+        SpecArgs a = md.spec;
+        a.first = md.step == 0;
+        if (i < md.n / 2) {
+            spectral_mode<true>(a, i, j);
+            if (i == 0) spectral_mode<true>(a, md.n / 2, j);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_constant__ BatchArgs b) {
+    for (int t = blockIdx.x; t < b.nl_tasks; t += gridDim.x) {
+        const int m = owner_of(b.nl_begin, b.nmembers, t);
+        const MemberDev& md = b.members[m];
+        const size_t q = (size_t)(t - b.nl_begin[m]) * kBNlThreads + threadIdx.x;
+        if (q < md.n4)
+            nonlinear_quad(md.phys4, md.nl4, md.snap, md.n4, q, md.stencil_plane,
+                           (int)((md.step + 1) & 1));
+    }
+}
+
+__global__ void __launch_bounds__(512) k_batch_rk4(const __grid_constant__ BatchArgs b) {
+    for (int t = blockIdx.x; t < b.rk_tasks; t += gridDim.x) {
+        const int e = owner_of(b.rk_begin, b.nentries, t);
+        const SpeciesDev& sd = *b.rk_sp[e];
+        const MemberDev& md = b.members[b.rk_member[e]];
+        const int p = (t - b.rk_begin[e]) * (int)blockDim.x + (int)threadIdx.x;
+        if (p >= sd.np) continue;
+        const int sel = md.scheme * 2 + (int)(md.step & 1);
+        switch (sel) {
+            case 0: rk4_particle<0, 0>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+            case 1: rk4_particle<0, 1>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+            case 2: rk4_particle<1, 0>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+            case 3: rk4_particle<1, 1>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+            case 4: rk4_particle<2, 0>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+            default: rk4_particle<2, 1>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+        }
+    }
+}
+
+__global__ void k_batch_advance(MemberDev* members, int nmembers) {
+    for (int m = threadIdx.x; m < nmembers; m += blockDim.x) members[m].step += 1;
+}
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+}  // namespace el
+
+using namespace el;
+
+struct el_batch {
+    cudaStream_t stream = nullptr;
+    int max_members = 0;
+    std::vector<el_flow*> members;
+    // device tables (in the caller's workspace)
+    MemberDev* d_members = nullptr;
+    int* d_spec_begin = nullptr;
+    int* d_nl_begin = nullptr;
+    int* d_rk_begin = nullptr;
+    int* d_rk_member = nullptr;
+    const SpeciesDev** d_rk_sp = nullptr;
+    // host copies (kept alive while their upload may be pending)
+    std::vector<MemberDev> h_members;
+    std::vector<int> h_spec_begin, h_nl_begin, h_rk_begin, h_rk_member;
+    std::vector<const SpeciesDev*> h_rk_sp;
+    BatchArgs args{};
+    int grid_spec = 0, grid_nl = 0, grid_rk = 0;
+    bool tables_valid = false;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_kernels = 0;
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
+    int sms = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+el_status bfail(el_batch* b, el_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return s;
+}
+
+#define BT_CUDA(b, call)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return bfail((b), EL_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));         \
+    } while (0)
+
+size_t table_bytes(int max_members) {
+    size_t m = (size_t)max_members, e = m * kMaxSpecies;
+    return align_up(m * sizeof(MemberDev)) + 2 * align_up((m + 1) * sizeof(int)) +
+           2 * align_up((e + 1) * sizeof(int)) + align_up(e * sizeof(void*));
+}
+
+MemberDev member_of(el_flow* f) {
+    MemberDev md{};
+    SpecArgs& a = md.spec;
+    a.what = f->what;
+    a.what_lo = f->what_lo;
+    a.hist = f->hist;
+    a.nhat = f->nhat;
+    a.spec = f->spec;
+    a.ex = f->ex;
+    a.ey = f->ey;
+    a.pre_x = f->pre_x;
+    a.pre_y = f->pre_y;
+    a.n = f->n;
+    a.nh = f->nh;
+    a.nplanes = f->nplanes;
+    a.mode = f->d.ab2_mode;
+    a.first = 0;
+    a.nmodes = f->nmodes;
+    a.scale = 1.0f / (float)f->n2;
+    a.dt = (float)f->d.dt;
+    a.nu = (float)f->d.nu;
+    md.phys4 = reinterpret_cast<const float4*>(f->phys);
+    md.nl4 = reinterpret_cast<float4*>(f->nl);
+    md.snap = f->snap;
+    md.n4 = f->n2 / 4;
+    md.stencil_plane = f->stencil_plane;
+    md.n = f->n;
+    md.log2n = f->log2n;
+    md.scheme = f->d.interp;
+    md.dt = (float)f->d.dt;
+    md.h = (float)(f->d.dt * (double)f->n / kTwoPi);
+    md.step = f->step;
+    return md;
+}
+
+// Rebuild and upload the member tables, and size the persistent grids.
+el_status rebuild_tables(el_batch* b) {
+    const int M = (int)b->members.size();
+    b->h_members.clear();
+    b->h_spec_begin.assign(1, 0);
+    b->h_nl_begin.assign(1, 0);
+    b->h_rk_begin.assign(1, 0);
+    b->h_rk_member.clear();
+    b->h_rk_sp.clear();
+    int rk_threads = 256;
+    for (int m = 0; m < M; m++) {
+        el_flow* f = b->members[m];
+        rk_threads = f->rk4_threads;  // one block size for the whole batch
+        b->h_members.push_back(member_of(f));
+        b->h_spec_begin.push_back(b->h_spec_begin.back() + f->n * spec_chunks(f->n));
+        b->h_nl_begin.push_back(b->h_nl_begin.back() +
+                                (int)((f->n2 / 4 + kBNlThreads - 1) / kBNlThreads));
+    }
+    for (int m = 0; m < M; m++) {
+        el_flow* f = b->members[m];
+        if (f->rk4_threads != rk_threads)
+            return bfail(b, EL_EINVAL, "batch members must share one rk4 block size");
+        for (int s = 0; s < f->d.max_species; s++) {
+            if (f->sp[s].np == 0) continue;
+            b->h_rk_member.push_back(m);
+            b->h_rk_sp.push_back(f->table + s);
+            b->h_rk_begin.push_back(b->h_rk_begin.back() +
+                                    (int)((f->sp[s].np + rk_threads - 1) / rk_threads));
+        }
+    }
+    BatchArgs& a = b->args;
+    a.members = b->d_members;
+    a.spec_begin = b->d_spec_begin;
+    a.nl_begin = b->d_nl_begin;
+    a.rk_begin = b->d_rk_begin;
+    a.rk_member = b->d_rk_member;
+    a.rk_sp = b->d_rk_sp;
+    a.nmembers = M;
+    a.nentries = (int)b->h_rk_member.size();
+    a.spec_tasks = b->h_spec_begin.back();
+    a.nl_tasks = b->h_nl_begin.back();
+    a.rk_tasks = b->h_rk_begin.back();
+    if (M > 0) {
+        BT_CUDA(b, cudaMemcpyAsync(b->d_members, b->h_members.data(), sizeof(MemberDev) * M,
+                                   cudaMemcpyHostToDevice, b->stream));
+        BT_CUDA(b, cudaMemcpyAsync(b->d_spec_begin, b->h_spec_begin.data(), sizeof(int) * (M + 1),
+                                   cudaMemcpyHostToDevice, b->stream));
+        BT_CUDA(b, cudaMemcpyAsync(b->d_nl_begin, b->h_nl_begin.data(), sizeof(int) * (M + 1),
+                                   cudaMemcpyHostToDevice, b->stream));
+    }
+    if (a.nentries > 0) {
+        BT_CUDA(b, cudaMemcpyAsync(b->d_rk_begin, b->h_rk_begin.data(),
+                                   sizeof(int) * (a.nentries + 1), cudaMemcpyHostToDevice, b->stream));
+        BT_CUDA(b, cudaMemcpyAsync(b->d_rk_member, b->h_rk_member.data(), sizeof(int) * a.nentries,
+                                   cudaMemcpyHostToDevice, b->stream));
+        BT_CUDA(b, cudaMemcpyAsync((void*)b->d_rk_sp, b->h_rk_sp.data(),
+                                   sizeof(void*) * a.nentries, cudaMemcpyHostToDevice, b->stream));
+    }
+    // persistent grids: as many blocks as fit on the GPU at once (capped by the work)
+    int occ = 0;
+    BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_spectral, kBSpecThreads, 0));
+    b->grid_spec = std::max(1, std::min(a.spec_tasks, occ * b->sms));
+    BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_nonlinear, kBNlThreads, 0));
+    b->grid_nl = std::max(1, std::min(a.nl_tasks, occ * b->sms));
+    BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_rk4, rk_threads, 0));
+    b->grid_rk = std::max(1, std::min(a.rk_tasks, std::max(1, occ) * b->sms));
+    b->tables_valid = true;
+    return EL_OK;
+}
+
+// cuFFT of every member on forked branches of the capture.
+el_status fork_ffts(el_batch* b, bool c2r) {
+    BT_CUDA(b, cudaEventRecord(b->fork_ev, b->stream));
+    for (int k = 0; k < kSideStreams; k++) BT_CUDA(b, cudaStreamWaitEvent(b->side[k], b->fork_ev, 0));
+    for (size_t m = 0; m < b->members.size(); m++) {
+        el_flow* f = b->members[m];
+        cudaStream_t s = b->side[m % kSideStreams];
+        cufftHandle plan = c2r ? f->plan_c2r : f->plan_r2c;
+        if (cufftSetStream(plan, s) != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cufftSetStream");
+        cufftResult r = c2r ? cufftExecC2R(plan, reinterpret_cast<cufftComplex*>(f->spec), f->phys)
+                            : cufftExecR2C(plan, f->nl, reinterpret_cast<cufftComplex*>(f->nhat));
+        if (r != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cuFFT exec failed (%d)", (int)r);
+    }
+    for (int k = 0; k < kSideStreams; k++) {
+        BT_CUDA(b, cudaEventRecord(b->join_ev[k], b->side[k]));
+        BT_CUDA(b, cudaStreamWaitEvent(b->stream, b->join_ev[k], 0));
+    }
+    return EL_OK;
+}
+
+el_status capture_body(el_batch* b) {
+    const BatchArgs& a = b->args;
+    k_batch_spectral<<<b->grid_spec, kBSpecThreads, 0, b->stream>>>(a);
+    b->launches++;
+    EL_TRY(fork_ffts(b, true));
+    k_batch_nonlinear<<<b->grid_nl, kBNlThreads, 0, b->stream>>>(a);
+    b->launches++;
+    EL_TRY(fork_ffts(b, false));
+    if (a.rk_tasks > 0) {
+        int threads = b->members.empty() ? 256 : b->members[0]->rk4_threads;
+        k_batch_rk4<<<b->grid_rk, threads, 0, b->stream>>>(a);
+        b->launches++;
+    }
+    k_batch_advance<<<1, 256, 0, b->stream>>>(b->d_members, a.nmembers);
+    b->launches++;
+    BT_CUDA(b, cudaGetLastError());
+    return EL_OK;
+}
+
+el_status build_batch_graph(el_batch* b) {
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    int64_t before = b->launches;
+    cudaGraph_t g = nullptr;
+    BT_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    el_status s = capture_body(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    for (el_flow* f : b->members) {  // plans back on the batch stream
+        cufftSetStream(f->plan_c2r, b->stream);
+        cufftSetStream(f->plan_r2c, b->stream);
+    }
+    if (s != EL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return bfail(b, EL_ECUDA, "batch capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, EL_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+    b->graph_kernels = b->launches - before;
+    b->launches = before;
+    return EL_OK;
+}
+
+void invalidate(el_batch* b) {
+    b->tables_valid = false;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+}  // namespace
+
+namespace el {
+// Called when a member's particles or tuning change.
+void batch_member_changed(el_batch* b) {
+    if (b) invalidate(b);
+}
+}  // namespace el
+
+extern "C" {
+
+size_t el_batch_workspace_bytes(int32_t max_members) {
+    if (max_members <= 0 || max_members > 4096) return 0;
+    return table_bytes(max_members);
+}
+
+el_status el_batch_create(int32_t max_members, void* dev_workspace, size_t bytes,
+                          void* cuda_stream, el_batch** out) {
+    if (!out) return EL_EINVAL;
+    *out = nullptr;
+    if (max_members <= 0 || max_members > 4096) return fail(nullptr, EL_EINVAL, "max_members out of range");
+    if (!dev_workspace || (uintptr_t)dev_workspace % kAlign)
+        return fail(nullptr, EL_EINVAL, "batch workspace NULL or not 256-byte aligned");
+    if (bytes < table_bytes(max_members))
+        return fail(nullptr, EL_ENOMEM, "batch workspace has %zu bytes, needs %zu", bytes,
+                    table_bytes(max_members));
+    el_batch* b = new (std::nothrow) el_batch();
+    if (!b) return fail(nullptr, EL_ENOMEM, "host allocation failed");
+    b->stream = (cudaStream_t)cuda_stream;
+    b->max_members = max_members;
+    char* p = (char*)dev_workspace;
+    size_t m = (size_t)max_members, e = m * kMaxSpecies, off = 0;
+    auto take = [&](size_t n) { char* r = p + off; off += align_up(n); return r; };
+    b->d_members = (MemberDev*)take(m * sizeof(MemberDev));
+    b->d_spec_begin = (int*)take((m + 1) * sizeof(int));
+    b->d_nl_begin = (int*)take((m + 1) * sizeof(int));
+    b->d_rk_begin = (int*)take((e + 1) * sizeof(int));
+    b->d_rk_member = (int*)take((e + 1) * sizeof(int));
+    b->d_rk_sp = (const SpeciesDev**)take(e * sizeof(void*));
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int k = 0; k < kSideStreams && err == cudaSuccess; k++)
+        err = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    for (int k = 0; k < kSideStreams && err == cudaSuccess; k++)
+        err = cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming);
+    if (err != cudaSuccess) {
+        el_batch_destroy(b);
+        return fail(nullptr, EL_ECUDA, "batch create: %s", cudaGetErrorString(err));
+    }
+    *out = b;
+    return EL_OK;
+}
+
+el_status el_batch_add(el_batch* b, el_flow* f) {
+    if (!b || !f) return EL_EINVAL;
+    if (f->batch) return bfail(b, EL_ESTATE, "flow already belongs to a batch");
+    if ((int)b->members.size() >= b->max_members) return bfail(b, EL_EINVAL, "batch is full");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != f->device) return bfail(b, EL_EINVAL, "flow lives on another device");
+    BT_CUDA(b, cudaStreamSynchronize(f->stream));
+    if (!b->members.empty() && b->members[0]->rk4_threads != f->rk4_threads)
+        f->rk4_threads = b->members[0]->rk4_threads;
+    f->own_stream = f->stream;
+    f->stream = b->stream;
+    cufftSetStream(f->plan_c2r, b->stream);
+    cufftSetStream(f->plan_r2c, b->stream);
+    cufftSetStream(f->plan_c2r1, b->stream);
+    f->batch = b;
+    b->members.push_back(f);
+    invalidate(b);
+    return EL_OK;
+}
+
+el_status el_batch_remove(el_batch* b, el_flow* f) {
+    if (!b || !f) return EL_EINVAL;
+    auto it = std::find(b->members.begin(), b->members.end(), f);
+    if (it == b->members.end()) return bfail(b, EL_EINVAL, "flow is not a member");
+    BT_CUDA(b, cudaStreamSynchronize(b->stream));
+    b->members.erase(it);
+    f->stream = f->own_stream;
+    cufftSetStream(f->plan_c2r, f->stream);
+    cufftSetStream(f->plan_r2c, f->stream);
+    cufftSetStream(f->plan_c2r1, f->stream);
+    f->batch = nullptr;
+    for (int k = 0; k < 2; k++) {  // its own graphs were captured before it joined
+        if (f->graph[k]) cudaGraphExecDestroy(f->graph[k]);
+        f->graph[k] = nullptr;
+        f->graph_valid[k] = false;
+    }
+    invalidate(b);
+    return EL_OK;
+}
+
+el_status el_batch_step(el_batch* b, int32_t nsteps) {
+    if (!b) return EL_EINVAL;
+    if (nsteps < 0) return bfail(b, EL_EINVAL, "nsteps < 0");
+    if (b->members.empty()) return EL_OK;
+    if (!b->tables_valid) EL_TRY(rebuild_tables(b));
+    for (int32_t k = 0; k < nsteps; k++) {
+        for (el_flow* f : b->members) {
+            if (f->d.sort_every > 0 && f->since_sort >= f->d.sort_every) {
+                for (int s = 0; s < f->d.max_species; s++) {
+                    el_status st = particles_sort(f, s);
+                    if (st != EL_OK) return bfail(b, st, "re-binning: %s", f->err.c_str());
+                }
+                f->since_sort = 0;
+            }
+        }
+        if (!b->graph) EL_TRY(build_batch_graph(b));
+        BT_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
+        b->launches += b->graph_kernels;
+        for (el_flow* f : b->members) {
+            f->step++;
+            f->since_sort++;
+        }
+    }
+    return EL_OK;
+}
+
+el_status el_batch_autotune(el_batch* b, int32_t trial_steps, el_tuning* best);
+
+int32_t el_batch_size(const el_batch* b) { return b ? (int32_t)b->members.size() : 0; }
+
+int64_t el_batch_kernel_launches(const el_batch* b) { return b ? b->launches : 0; }
+
+const char* el_batch_last_error(const el_batch* b) { return b ? b->err.c_str() : ""; }
+
+el_status el_batch_destroy(el_batch* b) {
+    if (!b) return EL_EINVAL;
+    if (b->stream || !b->members.empty()) cudaStreamSynchronize(b->stream);
+    while (!b->members.empty()) el_batch_remove(b, b->members.back());
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (int k = 0; k < kSideStreams; k++) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    delete b;
+    return EL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <class StepFn>
+el_status batch_time(StepFn step, cudaStream_t stream, int window, double* ms) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return EL_ECUDA;
+    el_status s = step(2);
+    if (s == EL_OK) {
+        cudaEventRecord(a, stream);
+        s = step(window);
+        cudaEventRecord(b, stream);
+    }
+    if (s == EL_OK) {
+        if (cudaEventSynchronize(b) != cudaSuccess) s = EL_ECUDA;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        *ms = t / window;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return s;
+}
+
+el_status batch_apply(el_batch* b, const el_tuning& t) {
+    for (el_flow* f : b->members) {
+        f->rk4_threads = t.rk4_threads;
+        f->d.sort_every = t.sort_every;
+        f->sort_shift = std::min(t.sort_shift, std::max(0, f->log2n - 2));
+    }
+    invalidate(b);
+    return EL_OK;
+}
+
+}  // namespace
+
+// Same search as el_autotune, one setting for every member.
+extern "C" el_status el_batch_autotune(el_batch* b, int32_t trial_steps, el_tuning* best_out) {
+    if (!b || !best_out) return EL_EINVAL;
+    if (trial_steps < 1) return bfail(b, EL_EINVAL, "trial_steps must be >= 1");
+    if (b->members.empty()) return bfail(b, EL_ESTATE, "empty batch");
+    el_flow* f0 = b->members[0];
+    el_tuning best{f0->rk4_threads, f0->d.sort_every, f0->sort_shift, 0.0};
+    double best_ms = 1e30;
+    auto step = [b](int n) { return el_batch_step(b, n); };
+    auto trial = [&](el_tuning t) -> el_status {
+        EL_TRY(batch_apply(b, t));
+        double ms = 0.0;
+        EL_TRY(batch_time(step, b->stream, std::max(trial_steps, 2 * t.sort_every), &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+        return EL_OK;
+    };
+    for (int th : {128, 256, 512}) {
+        el_tuning t = best;
+        t.rk4_threads = th;
+        EL_TRY(trial(t));
+    }
+    for (int c : {0, 5, 10, 20, 40}) {
+        if (c == best.sort_every) continue;
+        el_tuning t = best;
+        t.sort_every = c;
+        EL_TRY(trial(t));
+    }
+    if (best.sort_every > 0)
+        for (int sh : {0, 1, 2}) {
+            if (sh == best.sort_shift) continue;
+            el_tuning t = best;
+            t.sort_shift = sh;
+            EL_TRY(trial(t));
+        }
+    EL_TRY(batch_apply(b, best));
+    best.ms_per_step = best_ms;
+    *best_out = best;
+    return EL_OK;
+}

@@ -51,6 +51,8 @@ struct Species {
 
 }  // namespace el
 
+struct el_batch;
+
 struct el_flow {
     el_flow_desc d{};
     cudaStream_t stream = nullptr;
@@ -99,6 +101,10 @@ struct el_flow {
     el::Species sp[el::kMaxSpecies];
 
     int64_t step = 0;          // coupled steps taken
+    int rk4_threads = 256;     // threads per block of the particle step (tunable)
+    int sort_shift = 0;        // re-binning key: tiles of 2^sort_shift cells per side
+    el_batch* batch = nullptr; // the batch this flow is a member of, if any
+    cudaStream_t own_stream = nullptr;  // stream given at creation (restored on batch removal)
     int64_t since_sort = 0;
     int64_t launches = 0;
 

@@ -16,28 +16,12 @@
 //   k_unsplit      : split state -> FP64 unwrapped positions, original order
 //   k_msd / k_box  : per-particle terms of the statistics
 #include "common.cuh"
-#include "interp.cuh"
+#include "stages.cuh"
 
 namespace el {
 namespace {
 
-// Carry an offset that left [0, 1) into the cell index and the image count.
-__device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off, int& cell,
-                                           int& dimg) {
-    float fl = floorf(x);
-    float o = x - fl;
-    int k = (int)fl;
-    if (o >= 1.0f) {  // x - floor(x) rounded up to 1 for x just below an integer
-        o = 0.0f;
-        k += 1;
-    }
-    int c2 = c + k;
-    dimg = c2 >> log2n;              // floor division by n
-    cell = c2 - (dimg << log2n);
-    off = o;
-}
-
-constexpr int kRK4Threads = 256;
+constexpr int kRK4MaxThreads = 512;
 
 struct RK4Args {
     const float4* snap;
@@ -48,81 +32,17 @@ struct RK4Args {
 };
 
 // K6: one RK4 step of every species in one launch (blocks are split between
-// species by block_begin), between levels n and n+1.  PARITY = step & 1:
-// level n sits in half PARITY of the snapshot pair, level n+1 in the other,
-// so stage 1 (theta = 0) and stage 4 (theta = 1) read one half without
-// blending.  All (x, y) and (u, v) arithmetic is on float pairs (one paired
-// FP32 instruction per two lanes of work).
+// species by block_begin), between levels n and n+1 (rk4_particle).
 template <int SCHEME, int PARITY>
-__global__ void __launch_bounds__(kRK4Threads) k_rk4(const __grid_constant__ RK4Args a) {
+__global__ void __launch_bounds__(kRK4MaxThreads) k_rk4(const __grid_constant__ RK4Args a) {
     int s = 0;
 #pragma unroll
     for (int k = 1; k < kMaxSpecies; k++)
         if (k < a.nspecies && blockIdx.x >= a.block_begin[k]) s = k;
     const SpeciesDev& sd = a.table[s];
-    const int np = sd.np;
-    const int p = (int)(blockIdx.x - a.block_begin[s]) * kRK4Threads + (int)threadIdx.x;
-    if (p >= np) return;
-    const int cur = sd.cur;
-    uint32_t* __restrict__ cellp = sd.cell[cur];
-    float2* __restrict__ offp = sd.off[cur];
-    const int n = a.n;
-    const uint32_t c = cellp[p];
-    const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
-    const float2 o = offp[p];
-    Stencil<SCHEME, PARITY> st;
-    st.load(a.snap, n, ci, cj);
-    const float h = a.h, dt = a.dt;
-    const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
-    const float2 two = make_float2(2.0f, 2.0f);
-    float2 np2;
-    float2 vnew = make_float2(0.f, 0.f);
-    const bool inertial = sd.inertial;
-    if (!inertial) {
-        // Eq. 12, stages at t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
-        float2 k1 = st.template first_stage<0>(o);
-        float2 k2 = st.template at<1>(a.snap, n, ci, cj, __ffma2_rn(h2, k1, o));
-        float2 k3 = st.template at<1>(a.snap, n, ci, cj, __ffma2_rn(h2, k2, o));
-        float2 k4 = st.template at<2>(a.snap, n, ci, cj, __ffma2_rn(h1, k3, o));
-        float2 sum = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(k2, k3), k1), k4);
-        const float h6 = h * (1.0f / 6.0f);
-        np2 = __ffma2_rn(make_float2(h6, h6), sum, o);
-    } else {
-        // Eq. 14: x and v jointly; stage s has x_s = x + c_s dt v_{s-1},
-        // v_s = v + c_s dt a_{s-1}, a_s = (u(x_s, t_s) - v_s) / St (Eq. 13).
-        const float2 ist = make_float2(sd.inv_st, sd.inv_st);
-        const float2 d2 = make_float2(0.5f * dt, 0.5f * dt), d1 = make_float2(dt, dt);
-        float2* __restrict__ velp = sd.vel[cur];
-        const float2 v = velp[p];
-        float2 u1 = st.template first_stage<0>(o);
-        float2 a1 = __fmul2_rn(fsub2(u1, v), ist);
-        float2 v2 = __ffma2_rn(d2, a1, v);
-        float2 u2 = st.template at<1>(a.snap, n, ci, cj, __ffma2_rn(h2, v, o));
-        float2 a2 = __fmul2_rn(fsub2(u2, v2), ist);
-        float2 v3 = __ffma2_rn(d2, a2, v);
-        float2 u3 = st.template at<1>(a.snap, n, ci, cj, __ffma2_rn(h2, v2, o));
-        float2 a3 = __fmul2_rn(fsub2(u3, v3), ist);
-        float2 v4 = __ffma2_rn(d1, a3, v);
-        float2 u4 = st.template at<2>(a.snap, n, ci, cj, __ffma2_rn(h1, v3, o));
-        float2 a4 = __fmul2_rn(fsub2(u4, v4), ist);
-        const float h6 = h * (1.0f / 6.0f), d6 = dt * (1.0f / 6.0f);
-        float2 sx = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(v2, v3), v), v4);
-        float2 sa = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(a2, a3), a1), a4);
-        np2 = __ffma2_rn(make_float2(h6, h6), sx, o);
-        vnew = __ffma2_rn(make_float2(d6, d6), sa, v);
-        velp[p] = vnew;
-    }
-    float ox, oy;
-    int ni, nj, dix, diy;
-    carry_axis(np2.x, ci, a.log2n, ox, ni, dix);
-    carry_axis(np2.y, cj, a.log2n, oy, nj, diy);
-    cellp[p] = (uint32_t)ni | ((uint32_t)nj << 16);
-    offp[p] = make_float2(ox, oy);
-    if (dix | diy) {  // crossed the periodic boundary: rare read-modify-write
-        int2* imgp = sd.img[cur];
-        int2 m = imgp[p];
-        imgp[p] = make_int2(m.x + dix, m.y + diy);
-    }
+    const int p = (int)(blockIdx.x - a.block_begin[s]) * (int)blockDim.x + (int)threadIdx.x;
+    if (p >= sd.np) return;
+    rk4_particle<SCHEME, PARITY>(a.snap, a.n, a.log2n, a.dt, a.h, sd, p);
 }
 
 // FP64 position -> (cell, offset, image), Sec. 3.2: mapped periodically onto
@@ -359,7 +279,7 @@ el_status particles_step_all(el_flow* f, int parity) {
     for (int s = 0; s < f->d.max_species; s++) {
         // every slot up to the last non-empty one takes part (empty ones get no blocks)
         a.block_begin[s] = blocks;
-        blocks += f->sp[s].np > 0 ? blocks_for(f->sp[s].np, kRK4Threads) : 0;
+        blocks += f->sp[s].np > 0 ? blocks_for(f->sp[s].np, f->rk4_threads) : 0;
         if (f->sp[s].np > 0) ns = s + 1;
     }
     if (ns == 0) return EL_OK;
@@ -368,15 +288,15 @@ el_status particles_step_all(el_flow* f, int parity) {
     // a given block_begin (the non-empty one) wins the select in the kernel
     if (parity == 0) {
         switch (f->d.interp) {
-            case EL_BILINEAR: k_rk4<0, 0><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
-            case EL_CATMULL_ROM: k_rk4<1, 0><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
-            default: k_rk4<2, 0><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+            case EL_BILINEAR: k_rk4<0, 0><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
+            case EL_CATMULL_ROM: k_rk4<1, 0><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
+            default: k_rk4<2, 0><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
         }
     } else {
         switch (f->d.interp) {
-            case EL_BILINEAR: k_rk4<0, 1><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
-            case EL_CATMULL_ROM: k_rk4<1, 1><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
-            default: k_rk4<2, 1><<<blocks, kRK4Threads, 0, f->stream>>>(a); break;
+            case EL_BILINEAR: k_rk4<0, 1><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
+            case EL_CATMULL_ROM: k_rk4<1, 1><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
+            default: k_rk4<2, 1><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
         }
     }
     EL_LAUNCHED(f);

@@ -6,7 +6,8 @@
 // depends on it (each particle's step is independent of the others, and
 // the statistics are reduced in original-index order).
 //
-//   k_sort_count   : rank[p] = atomicAdd(&bins[key], 1)
+//   k_sort_count   : rank[p] = atomicAdd(&bins[key], 1), key = the particle's
+//                    tile of 2^shift x 2^shift cells (shift tunable)
 //   scan (3 kernels): bins -> exclusive prefix sums (offsets)
 //   k_sort_scatter : buffer cur^1 at bins[key] + rank[p] <- buffer cur at p;
 //                    then cur flips (in the device species table too, so a
@@ -20,13 +21,18 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;
 constexpr int kScanTile = kScanThreads * kScanPer;  // 4096 bins per block
 
-__global__ void k_sort_count(const uint32_t* __restrict__ cell, int64_t np, int log2n,
+// Re-binning key of a cell: row-major index of its tile of 2^shift x 2^shift
+// cells (shift = 0: the cell itself).
+__device__ __forceinline__ uint32_t bin_key(uint32_t c, int log2n, int shift) {
+    uint32_t i = (c & 0xffffu) >> shift, j = (c >> 16) >> shift;
+    return (j << (log2n - shift)) | i;
+}
+
+__global__ void k_sort_count(const uint32_t* __restrict__ cell, int64_t np, int log2n, int shift,
                              uint32_t* __restrict__ bins, uint32_t* __restrict__ rank) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
-    uint32_t c = cell[p];
-    uint32_t key = ((c >> 16) << log2n) | (c & 0xffffu);
-    rank[p] = atomicAdd(bins + key, 1u);
+    rank[p] = atomicAdd(bins + bin_key(cell[p], log2n, shift), 1u);
 }
 
 // Exclusive scan of one tile of kScanTile values in place; the tile total
@@ -85,7 +91,7 @@ __global__ void k_sort_scatter(const uint32_t* __restrict__ cell0, const float2*
                                const float2* __restrict__ vel0, const int2* __restrict__ img0,
                                const uint32_t* __restrict__ id0, const uint32_t* __restrict__ rank,
                                const uint32_t* __restrict__ offsets, int64_t np, int log2n,
-                               int inertial, uint32_t* __restrict__ cell1, float2* __restrict__ off1,
+                               int shift, int inertial, uint32_t* __restrict__ cell1, float2* __restrict__ off1,
                                float2* __restrict__ vel1, int2* __restrict__ img1,
                                uint32_t* __restrict__ id1, SpeciesDev* __restrict__ table,
                                int new_cur) {
@@ -93,8 +99,7 @@ __global__ void k_sort_scatter(const uint32_t* __restrict__ cell0, const float2*
     if (p == 0) table->cur = new_cur;  // read only by later launches
     if (p >= np) return;
     uint32_t c = cell0[p];
-    uint32_t key = ((c >> 16) << log2n) | (c & 0xffffu);
-    uint32_t d = offsets[key] + rank[p];
+    uint32_t d = offsets[bin_key(c, log2n, shift)] + rank[p];
     cell1[d] = c;
     off1[d] = off0[p];
     if (inertial) vel1[d] = vel0[p];
@@ -125,14 +130,16 @@ el_status particles_sort(el_flow* f, int s) {
     const int T = 256;
     const int a = sp.cur, b = sp.cur ^ 1;
     int inertial = sp.st > 0.0 ? 1 : 0;
-    EL_CUDA_OK(f, cudaMemsetAsync(f->bins, 0, f->n2 * sizeof(uint32_t), f->stream));
-    k_sort_count<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[a], sp.np, f->log2n, f->bins,
-                                                            sp.rank);
+    const int shift = f->sort_shift;
+    const int64_t nbins = (int64_t)f->n2 >> (2 * shift);
+    EL_CUDA_OK(f, cudaMemsetAsync(f->bins, 0, (size_t)nbins * sizeof(uint32_t), f->stream));
+    k_sort_count<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[a], sp.np, f->log2n, shift,
+                                                            f->bins, sp.rank);
     EL_LAUNCHED(f);
-    EL_TRY(exclusive_scan(f, f->bins, (int64_t)f->n2));
+    EL_TRY(exclusive_scan(f, f->bins, nbins));
     k_sort_scatter<<<blocks_for(sp.np, T), T, 0, f->stream>>>(
         sp.cell[a], sp.off[a], sp.vel[a], sp.img[a], sp.id[a], sp.rank, f->bins, sp.np, f->log2n,
-        inertial, sp.cell[b], sp.off[b], sp.vel[b], sp.img[b], sp.id[b], f->table + s, b);
+        shift, inertial, sp.cell[b], sp.off[b], sp.vel[b], sp.img[b], sp.id[b], f->table + s, b);
     EL_LAUNCHED(f);
     sp.cur = b;
     f->h_table[s].cur = b;

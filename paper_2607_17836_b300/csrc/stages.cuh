@@ -1,0 +1,237 @@
+// Per-element bodies of the step kernels, shared by the single-flow kernels
+// (fluid.cu, particles.cu) and the batched kernels (batch.cu), so that a
+// simulation advanced alone or inside a batch does the same arithmetic.
+#pragma once
+
+#include "common.cuh"
+#include "interp.cuh"
+
+namespace el {
+
+__device__ __forceinline__ int wavenumber_row(int j, int n) { return j < n / 2 ? j : j - n; }
+
+// 2/3 rule: keep iff 3|kx| < n and 3|ky| < n.
+__device__ __forceinline__ bool kept(int kx, int ky, int n) {
+    return 3 * abs(kx) < n && 3 * abs(ky) < n;
+}
+
+// Error-free FP32 sum (double-float arithmetic).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+struct SpecArgs {
+    float2* what;       // omega-hat, high part
+    float2* what_lo;    // omega-hat, low part
+    float2* hist;       // AB2 history
+    const float2* nhat; // N-hat of the current level
+    float2* spec;       // nplanes output half spectra
+    const float2* ex;   // exp(-nu kx^2 dt) as (hi, lo)
+    const float2* ey;   // exp(-nu ky^2 dt) as (hi, lo)
+    const float* pre_x;
+    const float* pre_y;
+    int n, nh, nplanes, mode, first;
+    size_t nmodes;
+    float scale, dt, nu;
+};
+
+// AB2 update (when ADVANCE) and the spectral velocity / gradient planes of
+// the resulting omega-hat.
+//
+// omega-hat is held as an unevaluated sum w_hi + w_lo of two floats: one
+// float would round the small per-step change (the viscous decay is only
+// nu k^2 dt of w) the same way step after step and drift by up to half an
+// ulp per step; the pair keeps about 44 bits.  Only w_hi feeds the planes.
+// mode 0 (integrating factor): E = exp(-nu k^2 dt) = ex[kx] * ey[ky] (the 1-D
+//   factors computed on the host in FP64, held as float pairs);
+//   w <- E w - dt (3/2 E N - 1/2 E^2 H), H <- N.
+// mode 1 (Eq. 10 as printed): R = -N - nu k^2 w; w <- w + dt (3/2 R - 1/2 H), H <- R.
+// The first step is forward Euler in either mode.
+template <bool ADVANCE>
+__device__ __forceinline__ void spectral_mode(const SpecArgs& a, int i, int j) {
+    const int n = a.n;
+    const size_t q = (size_t)j * a.nh + i;
+    const int kx = i, ky = wavenumber_row(j, n);
+    const bool keep = kept(kx, ky, n);
+    const float2* __restrict__ nhat = a.nhat;
+    const float2* __restrict__ hist_in = a.hist;
+    const float2* __restrict__ lo_in = a.what_lo;
+    // every load first, so they are all in flight together
+    float2 w = a.what[q];
+    float2 N = make_float2(0.f, 0.f), wl = N, H = N, ea = N, eb = N;
+    if (ADVANCE) {
+        N = nhat[q];
+        wl = lo_in[q];
+        if (!a.first) H = hist_in[q];
+        if (a.mode == 0) {
+            ea = a.ex[i];
+            eb = a.ey[j];
+        }
+        if (!keep) N = make_float2(0.f, 0.f);
+        const float dt = a.dt;
+        float2 inc, hi, lo, hist_out;
+        if (a.mode == 0) {
+            float Eh = ea.x * eb.x;  // E = Eh + El (two-product of the hi parts)
+            float El = fmaf(ea.x, eb.x, -Eh) + fmaf(ea.x, eb.y, ea.y * eb.x);
+            float E2 = Eh * Eh;
+            float c1 = a.first ? dt : 1.5f * dt, c2 = a.first ? 0.f : 0.5f * dt * E2;
+            float px = Eh * w.x, py = Eh * w.y;
+            hi = make_float2(px, py);
+            lo = make_float2(fmaf(Eh, w.x, -px) + fmaf(El, w.x, Eh * wl.x),
+                             fmaf(Eh, w.y, -py) + fmaf(El, w.y, Eh * wl.y));
+            inc = make_float2(fmaf(c2, H.x, -c1 * Eh * N.x), fmaf(c2, H.y, -c1 * Eh * N.y));
+            hist_out = N;
+        } else {
+            float nuk2 = a.nu * (float)(kx * kx + ky * ky);
+            float2 R = make_float2(-N.x - nuk2 * w.x, -N.y - nuk2 * w.y);
+            inc = a.first ? make_float2(dt * R.x, dt * R.y)
+                          : make_float2(dt * (1.5f * R.x - 0.5f * H.x), dt * (1.5f * R.y - 0.5f * H.y));
+            hi = w;
+            lo = wl;
+            hist_out = R;
+        }
+        float sx, exx, sy, eyy;
+        two_sum(hi.x, lo.x + inc.x, sx, exx);
+        two_sum(hi.y, lo.y + inc.y, sy, eyy);
+        w = make_float2(sx, sy);
+        a.hist[q] = hist_out;
+        a.what[q] = w;
+        a.what_lo[q] = make_float2(exx, eyy);
+    }
+    const float dkx = (i == n / 2) ? 0.f : (float)kx;  // Nyquist: zero derivative
+    const float dky = (j == n / 2) ? 0.f : (float)ky;
+    const float k2 = (float)(kx * kx + ky * ky);
+    w.x *= a.scale;
+    w.y *= a.scale;
+    const float ik2 = k2 > 0.f ? 1.f / k2 : 0.f;  // psi-hat(0) = 0 (Eq. 5)
+    const float2 psi = make_float2(w.x * ik2, w.y * ik2);
+    const float2 uh = make_float2(-dky * psi.y, dky * psi.x);  // u-hat = i ky psi-hat
+    const float2 vh = make_float2(dkx * psi.y, -dkx * psi.x);  // v-hat = -i kx psi-hat
+    const size_t m = a.nmodes;
+    float2* __restrict__ spec = a.spec;
+    spec[q] = uh;
+    spec[m + q] = vh;
+    spec[2 * m + q] = make_float2(-dkx * w.y, dkx * w.x);  // i kx omega-hat
+    spec[3 * m + q] = make_float2(-dky * w.y, dky * w.x);  // i ky omega-hat
+    if (a.nplanes == 6) {
+        // Interpolating cubic-spline coefficients: (c_{i-1} + 4 c_i + c_{i+1})/6 = f_i
+        // is diagonal in Fourier space with factor (2 + cos k dx)/3 per axis.
+        const float p = a.pre_x[i] * a.pre_y[j];
+        spec[4 * m + q] = make_float2(uh.x * p, uh.y * p);
+        spec[5 * m + q] = make_float2(vh.x * p, vh.y * p);
+    }
+}
+
+// N = u wx + v wy at four consecutive nodes 4q..4q+3 (Eq. 7); the stencil
+// field of the new level goes to half `h` of the snapshot pair (h = 2: both).
+__device__ __forceinline__ void nonlinear_quad(const float4* __restrict__ phys4,
+                                               float4* __restrict__ nl4, float4* __restrict__ snap,
+                                               size_t n4, size_t q, int stencil_plane, int h) {
+    float4 u = phys4[q], v = phys4[n4 + q], wx = phys4[2 * n4 + q], wy = phys4[3 * n4 + q];
+    nl4[q] = make_float4(fmaf(u.x, wx.x, v.x * wy.x), fmaf(u.y, wx.y, v.y * wy.y),
+                         fmaf(u.z, wx.z, v.z * wy.z), fmaf(u.w, wx.w, v.w * wy.w));
+    if (stencil_plane != 0) {
+        u = phys4[4 * n4 + q];
+        v = phys4[5 * n4 + q];
+    }
+    float2* s2 = reinterpret_cast<float2*>(snap + 4 * q);
+    const float2 s[4] = {make_float2(u.x, v.x), make_float2(u.y, v.y), make_float2(u.z, v.z),
+                         make_float2(u.w, v.w)};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (h == 2) {
+            snap[4 * q + k] = make_float4(s[k].x, s[k].y, s[k].x, s[k].y);
+        } else {
+            s2[2 * k + h] = s[k];
+        }
+    }
+}
+
+// Carry an offset that left [0, 1) into the cell index and the image count.
+__device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off, int& cell,
+                                           int& dimg) {
+    float fl = floorf(x);
+    float o = x - fl;
+    int k = (int)fl;
+    if (o >= 1.0f) {  // x - floor(x) rounded up to 1 for x just below an integer
+        o = 0.0f;
+        k += 1;
+    }
+    int c2 = c + k;
+    dimg = c2 >> log2n;              // floor division by n
+    cell = c2 - (dimg << log2n);
+    off = o;
+}
+
+// One RK4 step of particle p of species sd (Eq. 12 tracers, Eq. 14 inertial)
+// between levels n and n+1.  PARITY = step & 1: level n sits in half PARITY
+// of the snapshot pair, level n+1 in the other, so stage 1 (theta = 0) and
+// stage 4 (theta = 1) read one half without blending.  All (x, y) and
+// (u, v) arithmetic is on float pairs (one paired FP32 instruction per two
+// lanes of work).  h = dt * n / (2 pi): grid units per unit velocity.
+template <int SCHEME, int PARITY>
+__device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap, int n, int log2n,
+                                             float dt, float h, const SpeciesDev& sd, int p) {
+    const int cur = sd.cur;
+    uint32_t* __restrict__ cellp = sd.cell[cur];
+    float2* __restrict__ offp = sd.off[cur];
+    const uint32_t c = cellp[p];
+    const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
+    const float2 o = offp[p];
+    Stencil<SCHEME, PARITY> st;
+    st.load(snap, n, ci, cj);
+    const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
+    const float2 two = make_float2(2.0f, 2.0f);
+    float2 np2;
+    float2 vnew = make_float2(0.f, 0.f);
+    const bool inertial = sd.inertial;
+    if (!inertial) {
+        // Eq. 12, stages at t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
+        float2 k1 = st.template first_stage<0>(o);
+        float2 k2 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, k1, o));
+        float2 k3 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, k2, o));
+        float2 k4 = st.template at<2>(snap, n, ci, cj, __ffma2_rn(h1, k3, o));
+        float2 sum = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(k2, k3), k1), k4);
+        const float h6 = h * (1.0f / 6.0f);
+        np2 = __ffma2_rn(make_float2(h6, h6), sum, o);
+    } else {
+        // Eq. 14: x and v jointly; stage s has x_s = x + c_s dt v_{s-1},
+        // v_s = v + c_s dt a_{s-1}, a_s = (u(x_s, t_s) - v_s) / St (Eq. 13).
+        const float2 ist = make_float2(sd.inv_st, sd.inv_st);
+        const float2 d2 = make_float2(0.5f * dt, 0.5f * dt), d1 = make_float2(dt, dt);
+        float2* __restrict__ velp = sd.vel[cur];
+        const float2 v = velp[p];
+        float2 u1 = st.template first_stage<0>(o);
+        float2 a1 = __fmul2_rn(fsub2(u1, v), ist);
+        float2 v2 = __ffma2_rn(d2, a1, v);
+        float2 u2 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, v, o));
+        float2 a2 = __fmul2_rn(fsub2(u2, v2), ist);
+        float2 v3 = __ffma2_rn(d2, a2, v);
+        float2 u3 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, v2, o));
+        float2 a3 = __fmul2_rn(fsub2(u3, v3), ist);
+        float2 v4 = __ffma2_rn(d1, a3, v);
+        float2 u4 = st.template at<2>(snap, n, ci, cj, __ffma2_rn(h1, v3, o));
+        float2 a4 = __fmul2_rn(fsub2(u4, v4), ist);
+        const float h6 = h * (1.0f / 6.0f), d6 = dt * (1.0f / 6.0f);
+        float2 sx = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(v2, v3), v), v4);
+        float2 sa = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(a2, a3), a1), a4);
+        np2 = __ffma2_rn(make_float2(h6, h6), sx, o);
+        vnew = __ffma2_rn(make_float2(d6, d6), sa, v);
+        velp[p] = vnew;
+    }
+    float ox, oy;
+    int ni, nj, dix, diy;
+    carry_axis(np2.x, ci, log2n, ox, ni, dix);
+    carry_axis(np2.y, cj, log2n, oy, nj, diy);
+    cellp[p] = (uint32_t)ni | ((uint32_t)nj << 16);
+    offp[p] = make_float2(ox, oy);
+    if (dix | diy) {  // crossed the periodic boundary: rare read-modify-write
+        int2* imgp = sd.img[cur];
+        int2 m = imgp[p];
+        imgp[p] = make_int2(m.x + dix, m.y + diy);
+    }
+}
+
+}  // namespace el

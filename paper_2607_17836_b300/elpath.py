@@ -23,8 +23,11 @@ STATUS = {0: "EL_OK", 1: "EL_EINVAL", 2: "EL_ENOMEM", 3: "EL_ECUDA", 4: "EL_ECUF
 # Public C symbols, in include/elpath.h order.
 SYMBOLS = ("el_workspace_bytes", "el_create_flow", "el_set_particles", "el_step_coupled",
            "el_get_stats", "el_get_particles", "el_get_field", "el_sample_velocity",
-           "el_profile_step", "el_kernel_launches", "el_dispersion_noalloc", "el_destroy_flow",
-           "el_last_error")
+           "el_profile_step", "el_get_tuning", "el_set_tuning", "el_autotune",
+           "el_kernel_launches", "el_batch_workspace_bytes", "el_batch_create", "el_batch_add",
+           "el_batch_remove", "el_batch_step", "el_batch_autotune", "el_batch_size",
+           "el_batch_kernel_launches", "el_batch_last_error", "el_batch_destroy",
+           "el_dispersion_noalloc", "el_destroy_flow", "el_last_error")
 NOALLOC_MAX_PARTICLES = 262144
 
 
@@ -39,6 +42,11 @@ class el_flow_desc(ctypes.Structure):
                 ("dt", ctypes.c_double), ("ab2_mode", ctypes.c_int32),
                 ("bspline_prefilter", ctypes.c_int32), ("max_species", ctypes.c_int32),
                 ("sort_every", ctypes.c_int32), ("max_particles", ctypes.c_int64)]
+
+
+class el_tuning(ctypes.Structure):
+    _fields_ = [("rk4_threads", ctypes.c_int32), ("sort_every", ctypes.c_int32),
+                ("sort_shift", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
 
 
 class el_stats(ctypes.Structure):
@@ -76,6 +84,28 @@ def load(path: str = LIB_PATH):
     lib.el_profile_step.argtypes = [P, D, I32]
     lib.el_kernel_launches.argtypes = [P]
     lib.el_kernel_launches.restype = I64
+    T = ctypes.POINTER(el_tuning)
+    lib.el_get_tuning.argtypes = [P, T]
+    lib.el_set_tuning.argtypes = [P, T]
+    lib.el_autotune.argtypes = [P, I32, T]
+    lib.el_batch_workspace_bytes.argtypes = [I32]
+    lib.el_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.el_batch_create.argtypes = [I32, V, ctypes.c_size_t, V, ctypes.POINTER(P)]
+    lib.el_batch_add.argtypes = [P, P]
+    lib.el_batch_remove.argtypes = [P, P]
+    lib.el_batch_step.argtypes = [P, I32]
+    lib.el_batch_autotune.argtypes = [P, I32, T]
+    lib.el_batch_size.argtypes = [P]
+    lib.el_batch_size.restype = I32
+    lib.el_batch_kernel_launches.argtypes = [P]
+    lib.el_batch_kernel_launches.restype = I64
+    lib.el_batch_last_error.argtypes = [P]
+    lib.el_batch_last_error.restype = ctypes.c_char_p
+    lib.el_batch_destroy.argtypes = [P]
+    for name in ("el_get_tuning", "el_set_tuning", "el_autotune", "el_batch_create",
+                 "el_batch_add", "el_batch_remove", "el_batch_step", "el_batch_autotune",
+                 "el_batch_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.el_dispersion_noalloc.argtypes = [V, V, I64, V, V]
     lib.el_dispersion_noalloc.restype = ctypes.c_int
     lib.el_destroy_flow.argtypes = [P]
@@ -246,5 +276,89 @@ class Flow:
     def kernel_launches(self) -> int:
         return int(self._lib.el_kernel_launches(self._h))
 
+    def tuning(self) -> dict:
+        t = el_tuning()
+        self._check(self._lib.el_get_tuning(self._h, ctypes.byref(t)))
+        return {"rk4_threads": t.rk4_threads, "sort_every": t.sort_every,
+                "sort_shift": t.sort_shift}
+
+    def set_tuning(self, rk4_threads=256, sort_every=20, sort_shift=0):
+        t = el_tuning(int(rk4_threads), int(sort_every), int(sort_shift), 0.0)
+        self._check(self._lib.el_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, trial_steps=10) -> dict:
+        """el_autotune: the trial steps are real steps of this simulation."""
+        t = el_tuning()
+        self._check(self._lib.el_autotune(self._h, int(trial_steps), ctypes.byref(t)))
+        return {"rk4_threads": t.rk4_threads, "sort_every": t.sort_every,
+                "sort_shift": t.sort_shift, "ms_per_step": t.ms_per_step}
+
     def synchronize(self):
         self.stream.synchronize()
+
+
+class Batch:
+    """el_batch: flows advanced together by one persistent kernel per stage."""
+
+    def __init__(self, max_members, stream=None, device=None):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = int(lib.el_batch_workspace_bytes(int(max_members)))
+        if nbytes == 0:
+            raise ElpathError(1, "max_members out of range")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = lib.el_batch_create(int(max_members), ctypes.c_void_p(self.workspace.data_ptr()),
+                                     ctypes.c_size_t(nbytes),
+                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise ElpathError(st, lib.el_last_error(None).decode())
+        self._h = h
+        self.members = []
+
+    def _check(self, st):
+        if st != 0:
+            raise ElpathError(st, self._lib.el_batch_last_error(self._h).decode())
+
+    def add(self, flow):
+        self._check(self._lib.el_batch_add(self._h, flow._h))
+        self.members.append(flow)
+
+    def remove(self, flow):
+        self._check(self._lib.el_batch_remove(self._h, flow._h))
+        self.members.remove(flow)
+
+    def step(self, nsteps=1):
+        self._check(self._lib.el_batch_step(self._h, int(nsteps)))
+
+    def autotune(self, trial_steps=10) -> dict:
+        t = el_tuning()
+        self._check(self._lib.el_batch_autotune(self._h, int(trial_steps), ctypes.byref(t)))
+        return {"rk4_threads": t.rk4_threads, "sort_every": t.sort_every,
+                "sort_shift": t.sort_shift, "ms_per_step": t.ms_per_step}
+
+    def size(self) -> int:
+        return int(self._lib.el_batch_size(self._h))
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.el_batch_kernel_launches(self._h))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.el_batch_destroy(h)
+            self._h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,114 @@
+"""Batched engine and autotuner (through the C ABI).
+
+A member of a batch does the same arithmetic as the same simulation stepped
+alone, whatever else is in the batch and whenever it joined; the tuning
+knobs change no result.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_17836_b300 import elpath, inputs
+from parity import OMEGA_RTOL, POS_ATOL, rel_linf
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SPECS = [  # (n, scheme, [(count, St)], nu, dt)
+    (32, 0, [(777, 0.0), (300, 1.0)], 1e-3, 2e-3),
+    (64, 1, [(5000, 0.1)], 5e-4, 1e-3),
+    (128, 2, [(2049, 0.0), (1000, 10.0), (257, 1.0)], 1e-4, 5e-4),
+    (256, 0, [(20000, 1.0)], 1e-4, 5e-4),
+]
+
+
+def make(spec, seed, sort_every=7):
+    n, scheme, species, nu, dt = spec
+    g = elpath.Flow(n, nu, dt, inputs.decaying_turbulence(n, seed), interp=scheme,
+                    max_species=len(species), max_particles=sum(c for c, _ in species),
+                    sort_every=sort_every)
+    for k, (c, st) in enumerate(species):
+        g.set_particles(k, inputs.uniform_positions(c, seed * 10 + k), st)
+    return g
+
+
+def state(g, spec):
+    out = [g.field(0)]
+    for k, (c, _) in enumerate(spec[2]):
+        out.extend(g.particles(k, c))
+    return out
+
+
+def assert_same(a, b):
+    assert rel_linf(a[0], b[0]) < OMEGA_RTOL
+    for x, y in zip(a[1:], b[1:]):
+        assert np.max(np.abs(x - y)) <= POS_ATOL
+
+
+def test_members_match_their_solo_runs():
+    steps = 40
+    solo = []
+    for m, spec in enumerate(SPECS):
+        g = make(spec, 100 + m)
+        g.step(steps)
+        solo.append(state(g, spec))
+        g.close()
+    batch = elpath.Batch(8)
+    flows = [make(spec, 100 + m) for m, spec in enumerate(SPECS)]
+    for g in flows:
+        batch.add(g)
+    batch.step(steps)
+    for g, spec, ref in zip(flows, SPECS, solo):
+        assert g.stats()["step"] == steps
+        assert_same(state(g, spec), ref)
+    # one launch per stage for the whole batch: 4 of our kernels per step
+    l0 = batch.kernel_launches()
+    batch.step(3)
+    assert batch.kernel_launches() - l0 == 3 * 4
+    batch.close()
+
+
+def test_members_joining_and_leaving_at_different_steps():
+    # member A runs 15 steps alone, then joins B (fresh) for 25; then A leaves
+    # and B continues 10 more in the batch.
+    a_spec, b_spec = SPECS[1], SPECS[2]
+    ref_a = make(a_spec, 7)
+    ref_a.step(40)
+    ref_b = make(b_spec, 8)
+    ref_b.step(35)
+    a = make(a_spec, 7)
+    a.step(15)
+    b = make(b_spec, 8)
+    batch = elpath.Batch(4)
+    batch.add(a)
+    batch.add(b)
+    batch.step(25)
+    batch.remove(a)
+    a.step(0)
+    batch.step(10)
+    assert a.stats()["step"] == 40 and b.stats()["step"] == 35
+    assert_same(state(a, a_spec), state(ref_a, a_spec))
+    assert_same(state(b, b_spec), state(ref_b, b_spec))
+    with pytest.raises(elpath.ElpathError) as e:
+        b.step(1)                                  # members step only with their batch
+    assert e.value.status == 5
+    batch.close()
+
+
+def test_autotune_changes_no_result():
+    spec = (128, 1, [(30000, 1.0), (10000, 0.0)], 1e-4, 5e-4)
+    ref = make(spec, 3, sort_every=20)
+    tuned = make(spec, 3, sort_every=20)
+    best = tuned.autotune(trial_steps=6)
+    assert best["rk4_threads"] in (128, 256, 512) and best["ms_per_step"] > 0
+    steps_done = tuned.stats()["step"]
+    ref.step(steps_done)
+    a, b = state(tuned, spec), state(ref, spec)
+    np.testing.assert_array_equal(a[1], b[1])      # bitwise: block size and sort order
+    np.testing.assert_array_equal(a[3], b[3])      # do not enter the arithmetic
+    batch = elpath.Batch(4)
+    flows = [make(s, 50 + m) for m, s in enumerate(SPECS[:3])]
+    for g in flows:
+        batch.add(g)
+    bbest = batch.autotune(trial_steps=4)
+    assert bbest["ms_per_step"] > 0
+    batch.close()
