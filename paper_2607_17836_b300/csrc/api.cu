@@ -125,7 +125,9 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* spec = take((size_t)planes * nm * 8);
     char* phys = take((size_t)planes * n2 * 4);
     char* nl = take(n2 * 4);
-    char* snap = take(n2 * 16);
+    char* snap0 = take(n2 * 16);
+    char* snap1 = take(n2 * 16);
+    char* snap2 = take(n2 * 16);
     char* aux_spec = take(nm * 8);
     char* aux_phys = take(n2 * 4);
     char* stage64 = take(n2 * 8);
@@ -151,7 +153,9 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->spec = (float2*)spec;
         f->phys = (float*)phys;
         f->nl = (float*)nl;
-        f->snap = (float4*)snap;
+        f->snap[0] = (float4*)snap0;
+        f->snap[1] = (float4*)snap1;
+        f->snap[2] = (float4*)snap2;
         f->aux_spec = (float2*)aux_spec;
         f->aux_phys = (float*)aux_phys;
         f->stage64 = (double*)stage64;
@@ -201,50 +205,104 @@ bool carve_species(el_flow* f, Species& sp, int64_t np) {
     return true;
 }
 
-// One coupled step (Algorithm 1): fluid n -> n+1, then every species by
-// RK4 between levels n and n+1.
-el_status step_body(el_flow* f, int64_t step) {
-    EL_TRY(fluid_step(f, step));
-    EL_TRY(particles_step_all(f, (int)(step & 1)));
+enum { kFluidStep = 0, kParticleStep = 1, kOverlapStep = 2 };
+
+// Enqueue one piece of Algorithm 1 on the flow's stream: the fluid step n ->
+// n+1, the particle step between levels n and n+1, or the particle step of n
+// on a forked branch alongside the fluid step of n+1.  The two are
+// independent: particles of step n read the level pair (n, n+1), the fluid
+// step of n+1 writes level n+2 into the pairs (n+1, n+2) and (n+2, n+3).
+el_status enqueue_step(el_flow* f, int kind, int64_t step) {
+    if (kind == kFluidStep) return fluid_step(f, step);
+    if (kind == kParticleStep) return particles_step_all(f, step);
+    EL_CUDA_OK(f, cudaEventRecord(f->ev_fork, f->stream));
+    EL_CUDA_OK(f, cudaStreamWaitEvent(f->side, f->ev_fork, 0));
+    cudaStream_t main = f->stream;
+    f->stream = f->side;
+    el_status s = particles_step_all(f, step);
+    f->stream = main;
+    EL_TRY(s);
+    EL_TRY(fluid_step(f, step + 1));
+    EL_CUDA_OK(f, cudaEventRecord(f->ev_join, f->side));
+    EL_CUDA_OK(f, cudaStreamWaitEvent(f->stream, f->ev_join, 0));
     return EL_OK;
 }
 
-void drop_graphs(el_flow* f) {
-    for (int k = 0; k < 2; k++) {
-        if (f->graph[k]) cudaGraphExecDestroy(f->graph[k]);
-        f->graph[k] = nullptr;
-        f->graph_valid[k] = false;
+cudaGraphExec_t* graph_slot(el_flow* f, int kind, int phase, int64_t** count) {
+    if (kind == kFluidStep) {
+        *count = &f->k_fluid[phase];
+        return &f->g_fluid[phase];
     }
+    if (kind == kParticleStep) {
+        *count = &f->k_part[phase];
+        return &f->g_part[phase];
+    }
+    *count = &f->k_both[phase];
+    return &f->g_both[phase];
 }
 
-// Capture the step of a given parity (steps >= 1 only: step 0 is the Euler
-// start and runs by direct launches).
-el_status build_graph(el_flow* f, int parity) {
-    if (f->graph[parity]) {
-        cudaGraphExecDestroy(f->graph[parity]);
-        f->graph[parity] = nullptr;
+// Capture `kind` for ring phase `phase` (a step >= 1 with that phase: the
+// first, forward-Euler fluid step always runs by direct launches).
+el_status build_graph(el_flow* f, int kind, int phase) {
+    int64_t* count = nullptr;
+    cudaGraphExec_t* slot = graph_slot(f, kind, phase, &count);
+    if (*slot) {
+        cudaGraphExecDestroy(*slot);
+        *slot = nullptr;
     }
-    f->graph_valid[parity] = false;
     int64_t before = f->launches;
     cudaGraph_t g = nullptr;
     EL_CUDA_OK(f, cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal));
-    el_status s = step_body(f, 2 + parity);
+    el_status s = enqueue_step(f, kind, 3 + phase);
     cudaError_t e = cudaStreamEndCapture(f->stream, &g);
     if (s != EL_OK) {
         if (g) cudaGraphDestroy(g);
         return s;
     }
     if (e != cudaSuccess) return fail(f, EL_ECUDA, "stream capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&f->graph[parity], g, 0);
+    e = cudaGraphInstantiate(slot, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(f, EL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    f->graph_kernels[parity] = f->launches - before;
-    f->launches = before;  // nothing ran yet; replays add graph_kernels each
-    f->graph_valid[parity] = true;
+    *count = f->launches - before;
+    f->launches = before;  // nothing ran yet; replays add the count each
+    return EL_OK;
+}
+
+bool graphs_enabled(const el_flow* f) {
+    static const bool no_graph = std::getenv("ELPATH_NO_GRAPH") != nullptr;
+    return f->stream != nullptr && !no_graph;
+}
+
+el_status run_step(el_flow* f, int kind, int64_t step) {
+    if (!graphs_enabled(f) || (kind == kFluidStep && step == 0)) return enqueue_step(f, kind, step);
+    int phase = (int)(step % 3);
+    int64_t* count = nullptr;
+    cudaGraphExec_t* slot = graph_slot(f, kind, phase, &count);
+    if (!*slot) EL_TRY(build_graph(f, kind, phase));
+    EL_CUDA_OK(f, cudaGraphLaunch(*slot, f->stream));
+    f->launches += *count;
+    return EL_OK;
+}
+
+el_status maybe_sort(el_flow* f) {
+    if (f->d.sort_every > 0 && f->since_sort >= f->d.sort_every) {
+        for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_sort(f, s));
+        f->since_sort = 0;
+    }
     return EL_OK;
 }
 
 }  // namespace
+
+void drop_graphs(el_flow* f) {
+    for (int k = 0; k < 3; k++) {
+        cudaGraphExec_t* gs[3] = {&f->g_fluid[k], &f->g_part[k], &f->g_both[k]};
+        for (cudaGraphExec_t* g : gs) {
+            if (*g) cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+    }
+}
 
 el_status fail(el_flow* f, el_status s, const char* fmt, ...) {
     char buf[512];
@@ -310,9 +368,21 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     auto bail = [&](el_status s) {
         g_create_error = f->err;
         destroy_plans(f->plan_c2r, f->plan_r2c, f->plan_c2r1);
+        if (f->side) cudaStreamDestroy(f->side);
+        if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+        if (f->ev_join) cudaEventDestroy(f->ev_join);
         delete f;
         return s;
     };
+    if (f->stream) {
+        cudaError_t es = cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking);
+        if (es == cudaSuccess) es = cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming);
+        if (es == cudaSuccess) es = cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming);
+        if (es != cudaSuccess) {
+            fail(f, EL_ECUDA, "side stream: %s", cudaGetErrorString(es));
+            return bail(EL_ECUDA);
+        }
+    }
     size_t w = 0;
     cufftResult r = make_plans(f->n, f->nplanes, &f->plan_c2r, &f->plan_r2c, &f->plan_c2r1, &w);
     if (r != CUFFT_SUCCESS || w > fft) {
@@ -376,27 +446,32 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
     return EL_OK;
 }
 
+// Algorithm 1 for nsteps steps.  The fluid runs one step ahead inside the
+// call: particles of step n and the fluid step of n+1 go on two branches of
+// one graph and overlap on the device; the call ends with both at the same
+// level, so every other call sees a consistent state.
 el_status el_step_coupled(el_flow* f, int32_t nsteps) {
     if (!f) return EL_EINVAL;
     if (f->batch) return fail(f, EL_ESTATE, "flow belongs to a batch: step it with el_batch_step");
     if (nsteps < 0) return fail(f, EL_EINVAL, "nsteps < 0");
-    static const bool no_graph = std::getenv("ELPATH_NO_GRAPH") != nullptr;
-    bool use_graph = f->stream != nullptr && !no_graph;
-    for (int32_t k = 0; k < nsteps; k++) {
-        if (f->d.sort_every > 0 && f->since_sort >= f->d.sort_every) {
-            for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_sort(f, s));
-            f->since_sort = 0;
-        }
-        int parity = (int)(f->step & 1);
-        if (use_graph && f->step > 0) {
-            if (!f->graph_valid[parity]) EL_TRY(build_graph(f, parity));
-            EL_CUDA_OK(f, cudaGraphLaunch(f->graph[parity], f->stream));
-            f->launches += f->graph_kernels[parity];
+    if (nsteps == 0) return EL_OK;
+    const bool overlap = graphs_enabled(f) && f->side;
+    const int64_t n0 = f->step;
+    EL_TRY(maybe_sort(f));
+    EL_TRY(run_step(f, kFluidStep, n0));
+    for (int64_t s = n0; s < n0 + nsteps; s++) {
+        const bool last = s == n0 + nsteps - 1;
+        if (last) {
+            EL_TRY(run_step(f, kParticleStep, s));
+        } else if (overlap) {
+            EL_TRY(run_step(f, kOverlapStep, s));
         } else {
-            EL_TRY(step_body(f, f->step));
+            EL_TRY(run_step(f, kParticleStep, s));
+            EL_TRY(run_step(f, kFluidStep, s + 1));
         }
-        f->step++;
+        f->step = s + 1;
         f->since_sort++;
+        if (!last) EL_TRY(maybe_sort(f));
     }
     return EL_OK;
 }
@@ -468,7 +543,7 @@ el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
     cudaEventRecord(ev[1], f->stream);
     if (st == EL_OK) st = fluid_step(f, f->step);
     cudaEventRecord(ev[2], f->stream);
-    if (st == EL_OK) st = particles_step_all(f, (int)(f->step & 1));
+    if (st == EL_OK) st = particles_step_all(f, f->step);
     cudaEventRecord(ev[3], f->stream);
     cudaError_t e = cudaStreamSynchronize(f->stream);
     if (st == EL_OK && e != cudaSuccess) st = fail(f, EL_ECUDA, "profile: %s", cudaGetErrorString(e));
@@ -611,6 +686,9 @@ el_status el_destroy_flow(el_flow* f) {
     cudaStreamSynchronize(f->stream);
     drop_graphs(f);
     destroy_plans(f->plan_c2r, f->plan_r2c, f->plan_c2r1);
+    if (f->side) cudaStreamDestroy(f->side);
+    if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+    if (f->ev_join) cudaEventDestroy(f->ev_join);
     delete f;
     return EL_OK;
 }

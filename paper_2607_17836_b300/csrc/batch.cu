@@ -29,7 +29,7 @@ struct MemberDev {
     SpecArgs spec;          // arrays and constants of k_spectral (first from `step`)
     const float4* phys4;
     float4* nl4;
-    float4* snap;
+    float4* snap[3];        // ring of level pairs: snap[k % 3] = levels (k, k+1)
     unsigned long long n4;  // n^2 / 4
     int stencil_plane, n, log2n, scheme;
     float dt, h;
@@ -89,9 +89,10 @@ __global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_co
         const int m = owner_of(b.nl_begin, b.nmembers, t);
         const MemberDev& md = b.members[m];
         const size_t q = (size_t)(t - b.nl_begin[m]) * kBNlThreads + threadIdx.x;
+        const long long lv = md.step + 1;  // the level this step produces
         if (q < md.n4)
-            nonlinear_quad(md.phys4, md.nl4, md.snap, md.n4, q, md.stencil_plane,
-                           (int)((md.step + 1) & 1));
+            nonlinear_quad(md.phys4, md.nl4, md.snap[(lv + 2) % 3], md.snap[lv % 3], nullptr, md.n4,
+                           q, md.stencil_plane);
     }
 }
 
@@ -102,14 +103,11 @@ __global__ void __launch_bounds__(512) k_batch_rk4(const __grid_constant__ Batch
         const MemberDev& md = b.members[b.rk_member[e]];
         const int p = (t - b.rk_begin[e]) * (int)blockDim.x + (int)threadIdx.x;
         if (p >= sd.np) continue;
-        const int sel = md.scheme * 2 + (int)(md.step & 1);
-        switch (sel) {
-            case 0: rk4_particle<0, 0>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
-            case 1: rk4_particle<0, 1>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
-            case 2: rk4_particle<1, 0>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
-            case 3: rk4_particle<1, 1>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
-            case 4: rk4_particle<2, 0>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
-            default: rk4_particle<2, 1>(md.snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+        const float4* snap = md.snap[md.step % 3];
+        switch (md.scheme) {
+            case 0: rk4_particle<0>(snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+            case 1: rk4_particle<1>(snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
+            default: rk4_particle<2>(snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
         }
     }
 }
@@ -201,7 +199,7 @@ MemberDev member_of(el_flow* f) {
     a.nu = (float)f->d.nu;
     md.phys4 = reinterpret_cast<const float4*>(f->phys);
     md.nl4 = reinterpret_cast<float4*>(f->nl);
-    md.snap = f->snap;
+    for (int k = 0; k < 3; k++) md.snap[k] = f->snap[k];
     md.n4 = f->n2 / 4;
     md.stencil_plane = f->stencil_plane;
     md.n = f->n;
@@ -444,11 +442,7 @@ el_status el_batch_remove(el_batch* b, el_flow* f) {
     cufftSetStream(f->plan_r2c, f->stream);
     cufftSetStream(f->plan_c2r1, f->stream);
     f->batch = nullptr;
-    for (int k = 0; k < 2; k++) {  // its own graphs were captured before it joined
-        if (f->graph[k]) cudaGraphExecDestroy(f->graph[k]);
-        f->graph[k] = nullptr;
-        f->graph_valid[k] = false;
-    }
+    drop_graphs(f);  // its own graphs were captured before it joined
     invalidate(b);
     return EL_OK;
 }

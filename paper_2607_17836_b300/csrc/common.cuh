@@ -76,7 +76,7 @@ struct el_flow {
     float2* spec = nullptr;   // nplanes half spectra (C2R input)
     float* phys = nullptr;    // nplanes physical planes (C2R output)
     float* nl = nullptr;      // physical nonlinear term (R2C input)
-    float4* snap = nullptr;   // (u_a, v_a, u_b, v_b) per node: two time levels
+    float4* snap[3] = {nullptr, nullptr, nullptr};  // ring: snap[k % 3] = levels (k, k+1) per node
     float2* aux_spec = nullptr;
     float* aux_phys = nullptr;
     double* stage64 = nullptr;  // n^2 doubles: host <-> device field staging
@@ -108,10 +108,12 @@ struct el_flow {
     int64_t since_sort = 0;
     int64_t launches = 0;
 
-    // captured step graphs, one per step parity
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int64_t graph_kernels[2] = {0, 0};
-    bool graph_valid[2] = {false, false};
+    // captured graphs, one per ring phase (step % 3): the fluid step alone,
+    // the particle step alone, and particles(n) alongside fluid(n + 1)
+    cudaGraphExec_t g_fluid[3] = {}, g_part[3] = {}, g_both[3] = {};
+    int64_t k_fluid[3] = {}, k_part[3] = {}, k_both[3] = {};
+    cudaStream_t side = nullptr;       // second branch of the overlapped step
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     std::string err;
 };
@@ -158,10 +160,12 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn);
 // ---- particles (particles.cu) ---------------------------------------------------
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
                         const double* vxy);
-el_status particles_step_all(el_flow* f, int parity);  // K6, every species in one launch
+el_status particles_step_all(el_flow* f, int64_t step);  // K6, every species in one launch
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
 el_status particles_stats_into(el_flow* f, int s, double* out3);  // msd x, msd y, cluster
 el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv);
+
+void drop_graphs(el_flow* f);                     // api.cu
 
 // ---- sort (sort.cu) -------------------------------------------------------------
 el_status particles_sort(el_flow* f, int s);      // K7

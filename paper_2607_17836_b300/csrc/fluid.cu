@@ -10,7 +10,7 @@
 //                            scheme the prefiltered spline coefficients
 //   cuFFT C2R (batched)    : the planes to physical space
 //   K3 k_nonlinear         : N = u d(omega)/dx + v d(omega)/dy (Eq. 7), and the
-//                            new time level of the particle snapshot pair
+//                            new time level into the ring of level pairs
 //   cuFFT R2C              : N-hat (Eq. 8)
 //
 // Modes are addressed by a 2-D grid (blockIdx.y = row j), so no thread
@@ -37,14 +37,14 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectral(const __grid_constant
     if (i == 0) spectral_mode<ADVANCE>(a, a.n / 2, j);
 }
 
-// N = u wx + v wy at every node; the stencil field of the new level goes to
-// half `h` of the snapshot pair (h = 2 writes both halves, at set-up).
-// Four nodes per thread: 16-byte loads of the planes.
+// N = u wx + v wy at every node and the new level into its two level pairs
+// (nonlinear_quad).  Four nodes per thread: 16-byte loads of the planes.
 __global__ void k_nonlinear(const float4* __restrict__ phys4, float4* __restrict__ nl4,
-                            float4* __restrict__ snap, size_t n4, int stencil_plane, int h) {
+                            float4* __restrict__ pair_prev, float4* __restrict__ pair_next,
+                            float4* __restrict__ init, size_t n4, int stencil_plane) {
     size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n4) return;
-    nonlinear_quad(phys4, nl4, snap, n4, q, stencil_plane, h);
+    nonlinear_quad(phys4, nl4, pair_prev, pair_next, init, n4, q, stencil_plane);
 }
 
 // Initial projection: mean removed, 2/3 rule (Sec. 3.1).
@@ -166,14 +166,18 @@ static SpecArgs spec_args(el_flow* f, int first) {
     return a;
 }
 
-// Planes -> physical fields, nonlinear term into the stencil half `h`, N-hat.
-static el_status finish_rhs(el_flow* f, int h) {
+// Planes -> physical fields, nonlinear term, level m into pairs (m-1, m) and
+// (m, m+1) of the ring (pair (k, k+1) is snap[k % 3]), N-hat.
+static el_status finish_rhs(el_flow* f, int64_t m, bool setup) {
     const int T = 256;
     EL_TRY(fft_exec_c2r(f, f->plan_c2r, f->spec, f->phys));
     size_t n4 = f->n2 / 4;
+    float4* prev = f->snap[(m + 2) % 3];
+    float4* next = f->snap[m % 3];
+    float4* third = f->snap[(m + 1) % 3];
     k_nonlinear<<<blocks_for((int64_t)n4, T), T, 0, f->stream>>>(
-        reinterpret_cast<const float4*>(f->phys), reinterpret_cast<float4*>(f->nl), f->snap, n4,
-        f->stencil_plane, h);
+        reinterpret_cast<const float4*>(f->phys), reinterpret_cast<float4*>(f->nl), prev, next,
+        setup ? third : nullptr, n4, f->stencil_plane);
     EL_LAUNCHED(f);
     EL_TRY(fft_exec_r2c(f, f->nl, f->nhat));
     return EL_OK;
@@ -198,14 +202,14 @@ el_status fluid_init(el_flow* f, const double* omega0_host) {
     EL_CUDA_OK(f, cudaMemsetAsync(f->what_lo, 0, f->nmodes * sizeof(float2), f->stream));
     k_spectral<false><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, 0));
     EL_LAUNCHED(f);
-    return finish_rhs(f, 2);
+    return finish_rhs(f, 0, true);
 }
 
-// Fluid n -> n+1 for step number `step`: level n+1 goes to half (step+1)&1.
+// Fluid n -> n+1 for step number n = `step`.
 el_status fluid_step(el_flow* f, int64_t step) {
     k_spectral<true><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, step == 0));
     EL_LAUNCHED(f);
-    return finish_rhs(f, (int)((step + 1) & 1));
+    return finish_rhs(f, step + 1, false);
 }
 
 el_status fluid_diagnostics(el_flow* f) {
@@ -232,10 +236,9 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn) {
         k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(f->phys + (which - 1) * f->n2,
                                                                    out, f->n2, 1, 0);
     } else {
-        // stencil field of the current level: half (step & 1) of the snapshot pair
-        int h = (int)(f->step & 1);
+        // stencil field of the current level n: first half of pair (n, n+1)
         k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(
-            reinterpret_cast<const float*>(f->snap), out, f->n2, 4, 2 * h + (which - 3));
+            reinterpret_cast<const float*>(f->snap[f->step % 3]), out, f->n2, 4, which - 3);
     }
     EL_LAUNCHED(f);
     EL_CUDA_OK(f, cudaMemcpyAsync(host_nn, out, f->n2 * sizeof(double), cudaMemcpyDeviceToHost,

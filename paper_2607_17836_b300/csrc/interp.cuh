@@ -1,12 +1,11 @@
 // Device-side spatial + temporal interpolation of the fluid velocity
 // (Sec. 3.4, Eqs. 15-24), shared by the particle step and the sampling hook.
 //
-// The field is the snapshot pair: per node a float4 (u_a, v_a, u_b, v_b)
-// holding two time levels, so one 16-byte load fetches both.  A node's value
-// at a stage is wa * (u_a, v_a) + wb * (u_b, v_b) (Eq. 23); the caller picks
-// (wa, wb) from theta and from which half holds level n.  Blending the nodes
-// before the spatial weights is the same linear map as Eq. 23 applied to the
-// two spatially interpolated values.
+// The field is a level pair: per node a float4 (u_n, v_n, u_n+1, v_n+1)
+// holding two consecutive time levels, so one 16-byte load fetches both.  A
+// node's value at a stage is wa * (u_n, v_n) + wb * (u_n+1, v_n+1) (Eq. 23).
+// Blending the nodes before the spatial weights is the same linear map as
+// Eq. 23 applied to the two spatially interpolated values.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -119,9 +118,8 @@ __device__ __forceinline__ void cubic_weights2(float2 s, float2 w[4]) {
 // stages nearly always fall in the cell of the previous stage: the stencil is
 // loaded once and re-used, and only a stage that crosses into another cell
 // fetches again.  (ci, cj) are the cell's unwrapped indices; addresses wrap.
-// PARITY: which half of each node holds level n (the other holds n+1).
 // THETA: 0 = level n, 1 = mid-way (theta = 1/2), 2 = level n+1 (Eq. 23).
-template <int SCHEME, int PARITY>
+template <int SCHEME>
 struct Stencil {
     static constexpr int W = SCHEME == 0 ? 2 : 4;
     static constexpr int O = SCHEME == 0 ? 0 : -1;  // first node relative to the cell
@@ -147,7 +145,7 @@ struct Stencil {
         const float4& t = v[k];
         const float2 lo = make_float2(t.x, t.y), hi = make_float2(t.z, t.w);
         if (THETA == 1) return __fadd2_rn(lo, hi);
-        return ((THETA == 0) == (PARITY == 0)) ? lo : hi;
+        return THETA == 0 ? lo : hi;
     }
 
     template <int THETA>

@@ -33,7 +33,7 @@ struct RK4Args {
 
 // K6: one RK4 step of every species in one launch (blocks are split between
 // species by block_begin), between levels n and n+1 (rk4_particle).
-template <int SCHEME, int PARITY>
+template <int SCHEME>
 __global__ void __launch_bounds__(kRK4MaxThreads) k_rk4(const __grid_constant__ RK4Args a) {
     int s = 0;
 #pragma unroll
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kRK4MaxThreads) k_rk4(const __grid_constant__ 
     const SpeciesDev& sd = a.table[s];
     const int p = (int)(blockIdx.x - a.block_begin[s]) * (int)blockDim.x + (int)threadIdx.x;
     if (p >= sd.np) return;
-    rk4_particle<SCHEME, PARITY>(a.snap, a.n, a.log2n, a.dt, a.h, sd, p);
+    rk4_particle<SCHEME>(a.snap, a.n, a.log2n, a.dt, a.h, sd, p);
 }
 
 // FP64 position -> (cell, offset, image), Sec. 3.2: mapped periodically onto
@@ -86,9 +86,10 @@ __device__ float2 fluid_at_scheme(int scheme, const float4* snap, int n, int ci,
 }
 
 // K9: split-precision state from FP64 positions; velocity from vxy, or zero
-// slip (the interpolated fluid velocity of the current level, half `cur`).
+// slip (the interpolated fluid velocity of the current level: the first half
+// of the pair `snap`).
 __global__ void k_init(const double* __restrict__ xy, const double* __restrict__ vxy, int64_t np,
-                       int n, int scheme, int inertial, int cur, const float4* __restrict__ snap,
+                       int n, int scheme, int inertial, const float4* __restrict__ snap,
                        uint32_t* __restrict__ cell, float2* __restrict__ off,
                        float2* __restrict__ vel, int2* __restrict__ img, uint32_t* __restrict__ id,
                        double2* __restrict__ x0) {
@@ -108,8 +109,7 @@ __global__ void k_init(const double* __restrict__ xy, const double* __restrict__
         if (vxy) {
             vel[p] = make_float2((float)vxy[2 * p], (float)vxy[2 * p + 1]);
         } else {
-            float wa = cur ? 0.0f : 1.0f;
-            vel[p] = fluid_at_scheme(scheme, snap, n, ci, cj, ox, oy, wa, 1.0f - wa);
+            vel[p] = fluid_at_scheme(scheme, snap, n, ci, cj, ox, oy, 1.0f, 0.0f);
         }
     }
 }
@@ -243,7 +243,7 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
     }
     if (np > 0) {
         k_init<<<blocks_for(np, T), T, 0, f->stream>>>(
-            stage, d_vxy, np, f->n, f->d.interp, st > 0.0 ? 1 : 0, (int)(f->step & 1), f->snap,
+            stage, d_vxy, np, f->n, f->d.interp, st > 0.0 ? 1 : 0, f->snap[f->step % 3],
             sp.cell[cur], sp.off[cur], sp.vel[cur], sp.img[cur], sp.id[cur], sp.x0);
         EL_LAUNCHED(f);
     }
@@ -265,10 +265,11 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
     return EL_OK;
 }
 
-// K6 for every species of the flow in one launch; parity = step & 1.
-el_status particles_step_all(el_flow* f, int parity) {
+// K6 for every species of the flow in one launch, step number `step`
+// (levels step and step + 1: pair snap[step % 3]).
+el_status particles_step_all(el_flow* f, int64_t step) {
     RK4Args a{};
-    a.snap = f->snap;
+    a.snap = f->snap[step % 3];
     a.table = f->table;
     a.n = f->n;
     a.log2n = f->log2n;
@@ -286,18 +287,10 @@ el_status particles_step_all(el_flow* f, int parity) {
     a.nspecies = ns;
     // empty slots share block_begin with the next slot, so the last slot with
     // a given block_begin (the non-empty one) wins the select in the kernel
-    if (parity == 0) {
-        switch (f->d.interp) {
-            case EL_BILINEAR: k_rk4<0, 0><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
-            case EL_CATMULL_ROM: k_rk4<1, 0><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
-            default: k_rk4<2, 0><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
-        }
-    } else {
-        switch (f->d.interp) {
-            case EL_BILINEAR: k_rk4<0, 1><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
-            case EL_CATMULL_ROM: k_rk4<1, 1><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
-            default: k_rk4<2, 1><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
-        }
+    switch (f->d.interp) {
+        case EL_BILINEAR: k_rk4<0><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
+        case EL_CATMULL_ROM: k_rk4<1><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
+        default: k_rk4<2><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
     }
     EL_LAUNCHED(f);
     return EL_OK;
@@ -349,13 +342,10 @@ el_status particles_stats_into(el_flow* f, int s, double* out3) {
 el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv) {
     if (np == 0) return EL_OK;
     const int T = 256;
-    // previous level in half (step + 1) & 1, current level in half step & 1
-    int cur = (int)(f->step & 1);
+    // pair (n-1, n) of the ring: previous level first, current level second
     float th = (float)theta;
-    float w_cur = th, w_prev = 1.0f - th;
-    float wa = cur == 0 ? w_cur : w_prev, wb = cur == 0 ? w_prev : w_cur;
-    k_sample<<<blocks_for(np, T), T, 0, f->stream>>>(d_xy, np, f->n, f->d.interp, wa, wb, f->snap,
-                                                      d_uv);
+    k_sample<<<blocks_for(np, T), T, 0, f->stream>>>(d_xy, np, f->n, f->d.interp, 1.0f - th, th,
+                                                      f->snap[(f->step + 2) % 3], d_uv);
     EL_LAUNCHED(f);
     return EL_OK;
 }

@@ -124,11 +124,17 @@ __device__ __forceinline__ void spectral_mode(const SpecArgs& a, int i, int j) {
     }
 }
 
-// N = u wx + v wy at four consecutive nodes 4q..4q+3 (Eq. 7); the stencil
-// field of the new level goes to half `h` of the snapshot pair (h = 2: both).
+// N = u wx + v wy at four consecutive nodes 4q..4q+3 (Eq. 7).  The stencil
+// field of the new level m goes to the second half of pair (m-1, m) and the
+// first half of pair (m, m+1).  At set-up (`init` = the third pair) level 0
+// fills both halves of all three pairs, so no pair ever holds uninitialised
+// values (a blend weight of 0 times a NaN left in reused memory is NaN).
 __device__ __forceinline__ void nonlinear_quad(const float4* __restrict__ phys4,
-                                               float4* __restrict__ nl4, float4* __restrict__ snap,
-                                               size_t n4, size_t q, int stencil_plane, int h) {
+                                               float4* __restrict__ nl4,
+                                               float4* __restrict__ pair_prev,
+                                               float4* __restrict__ pair_next,
+                                               float4* __restrict__ init, size_t n4, size_t q,
+                                               int stencil_plane) {
     float4 u = phys4[q], v = phys4[n4 + q], wx = phys4[2 * n4 + q], wy = phys4[3 * n4 + q];
     nl4[q] = make_float4(fmaf(u.x, wx.x, v.x * wy.x), fmaf(u.y, wx.y, v.y * wy.y),
                          fmaf(u.z, wx.z, v.z * wy.z), fmaf(u.w, wx.w, v.w * wy.w));
@@ -136,15 +142,19 @@ __device__ __forceinline__ void nonlinear_quad(const float4* __restrict__ phys4,
         u = phys4[4 * n4 + q];
         v = phys4[5 * n4 + q];
     }
-    float2* s2 = reinterpret_cast<float2*>(snap + 4 * q);
+    float2* prev2 = reinterpret_cast<float2*>(pair_prev + 4 * q);
+    float2* next2 = reinterpret_cast<float2*>(pair_next + 4 * q);
     const float2 s[4] = {make_float2(u.x, v.x), make_float2(u.y, v.y), make_float2(u.z, v.z),
                          make_float2(u.w, v.w)};
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        if (h == 2) {
-            snap[4 * q + k] = make_float4(s[k].x, s[k].y, s[k].x, s[k].y);
-        } else {
-            s2[2 * k + h] = s[k];
+        prev2[2 * k + 1] = s[k];
+        next2[2 * k] = s[k];
+        if (init) {
+            const float4 both = make_float4(s[k].x, s[k].y, s[k].x, s[k].y);
+            pair_prev[4 * q + k] = both;
+            pair_next[4 * q + k] = both;
+            init[4 * q + k] = both;
         }
     }
 }
@@ -166,12 +176,12 @@ __device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off
 }
 
 // One RK4 step of particle p of species sd (Eq. 12 tracers, Eq. 14 inertial)
-// between levels n and n+1.  PARITY = step & 1: level n sits in half PARITY
-// of the snapshot pair, level n+1 in the other, so stage 1 (theta = 0) and
-// stage 4 (theta = 1) read one half without blending.  All (x, y) and
-// (u, v) arithmetic is on float pairs (one paired FP32 instruction per two
-// lanes of work).  h = dt * n / (2 pi): grid units per unit velocity.
-template <int SCHEME, int PARITY>
+// between levels n and n+1, read from their level pair `snap`: stage 1
+// (theta = 0) and stage 4 (theta = 1) read one half of each node without
+// blending.  All (x, y) and (u, v) arithmetic is on float pairs (one paired
+// FP32 instruction per two lanes of work).  h = dt * n / (2 pi): grid units
+// per unit velocity.
+template <int SCHEME>
 __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap, int n, int log2n,
                                              float dt, float h, const SpeciesDev& sd, int p) {
     const int cur = sd.cur;
@@ -180,7 +190,7 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap, in
     const uint32_t c = cellp[p];
     const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
     const float2 o = offp[p];
-    Stencil<SCHEME, PARITY> st;
+    Stencil<SCHEME> st;
     st.load(snap, n, ci, cj);
     const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
     const float2 two = make_float2(2.0f, 2.0f);

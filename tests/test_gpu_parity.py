@@ -247,3 +247,31 @@ def test_argument_errors():
     with pytest.raises(elpath.ElpathError) as e:
         elpath.Flow(n, 1e-3, 1e-3, w0, workspace=small)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_no_uninitialised_reads(scheme):
+    # A workspace full of NaN bytes (0xFF) must give the same bits as a zeroed
+    # one: every value the path reads is written first.
+    n = 64
+    w0 = decaying(n, seed=16, k0=6.0)
+    xy = inputs.uniform_positions(3000, seed=17)
+    outs = []
+    for fill in (0, 255):
+        desc = elpath.make_desc(n, 1e-3, 1e-3, interp=scheme, max_species=2, max_particles=6000,
+                                sort_every=4)
+        ws = torch.full((elpath.workspace_bytes(desc),), fill, dtype=torch.uint8, device="cuda")
+        g = elpath.Flow(n, 1e-3, 1e-3, w0, interp=scheme, max_species=2, max_particles=6000,
+                        sort_every=4, workspace=ws)
+        g.set_particles(0, xy, 1.0)
+        g.set_particles(1, xy, 0.0)
+        g.step(9)
+        st = g.stats()
+        outs.append((g.particles(0, 3000), g.particles(1, 3000)[0], g.field(0), st["msd"][:2]))
+        g.close()
+    a, b = outs
+    np.testing.assert_array_equal(a[0][0], b[0][0])
+    np.testing.assert_array_equal(a[0][1], b[0][1])
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[2], b[2])
+    assert a[3] == b[3]
