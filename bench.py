@@ -85,7 +85,7 @@ def recorded_traffic(scheme_name):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -100,7 +100,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -318,6 +318,9 @@ def run_ours(args, wl, scheme, world, rank, local):
     stream = flow.stream
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    # Warm-up: the autotuner's trial windows (real steps; no result depends on
+    # the settings it picks), then W plain steps.
+    tuning = flow.autotune(trial_steps=5) if not args.no_autotune else flow.tuning()
     for _ in range(args.warmup):
         flow.step(1)
     stream.synchronize()
@@ -372,6 +375,7 @@ def run_ours(args, wl, scheme, world, rank, local):
         g16 = elpath.Flow(wl.n, wl.nu, wl.dt, w0, interp=scheme, max_species=1,
                           max_particles=big, sort_every=SORT_EVERY, device=dev)
         g16.set_particles(0, inputs.uniform_positions(big, 99 + rank), 1.0)
+        g16.autotune(trial_steps=4)
         for _ in range(3):
             g16.step(1)
         pr = [g16.profile_step() for _ in range(10)]
@@ -432,7 +436,7 @@ def run_ours(args, wl, scheme, world, rank, local):
             "e2e": {"value": e2e_value, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "what": "set_particles from pinned host + K steps + stats + particles back"},
-            "roofline_16M": roof16,
+            "roofline_16M": roof16, "tuning": tuning,
             "gpu_launches": launches, "wall_s": t_wall,
             "clocks": clocks.summary(), "energy": st["energy"]}
     if not args.no_ensemble:
@@ -449,13 +453,14 @@ def run_ours(args, wl, scheme, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--scheme", default="bilinear", choices=sorted(SCHEMES))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-roofline16", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -160,11 +160,15 @@ typedef struct {
 el_status el_get_tuning(const el_flow* flow, el_tuning* out);
 el_status el_set_tuning(el_flow* flow, const el_tuning* tuning);
 
-/* Autotuner: times trial windows of real steps (at least trial_steps, and two
- * re-binning periods) for block sizes {128, 256, 512}, then cadences
- * {0, 5, 10, 20, 40}, then tiles {1, 2, 4} cells, keeps the fastest and
- * applies it.  The trial steps advance the simulation like any others.
- * Synchronises the stream. */
+/* Autotuner.  Picks the particle step's block size (fastest of {128, 256,
+ * 512} over trial_steps steps, each right after a re-binning), the
+ * re-binning tile (fastest of 1, 2, 4 cells per side, counting its cost)
+ * and the cadence from a measured model: the step time grows about linearly
+ * as particles drift out of cell order, t(k) = t0 + a k, so with re-binning
+ * cost c every S steps the mean is t0 + a S / 2 + c / S, least at
+ * S = sqrt(2 c / a) (t0, t(W) and c are timed; 0 = never when a is nil).
+ * The trial steps advance the simulation like any others; no result depends
+ * on the settings.  Synchronises the stream. */
 el_status el_autotune(el_flow* flow, int32_t trial_steps, el_tuning* best);
 
 /* Number of kernel launches of the library (not cuFFT) issued so far by

@@ -1,6 +1,7 @@
 // The C ABI of include/elpath.h: argument checks, the workspace layout,
 // cuFFT plans, the captured step graph and the coupled step of Algorithm 1.
 #include "common.cuh"
+#include "tune.cuh"
 
 #include <cmath>
 #include <cstdarg>
@@ -127,7 +128,6 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* nl = take(n2 * 4);
     char* snap0 = take(n2 * 16);
     char* snap1 = take(n2 * 16);
-    char* snap2 = take(n2 * 16);
     char* aux_spec = take(nm * 8);
     char* aux_phys = take(n2 * 4);
     char* stage64 = take(n2 * 8);
@@ -155,7 +155,6 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->nl = (float*)nl;
         f->snap[0] = (float4*)snap0;
         f->snap[1] = (float4*)snap1;
-        f->snap[2] = (float4*)snap2;
         f->aux_spec = (float2*)aux_spec;
         f->aux_phys = (float*)aux_phys;
         f->stage64 = (double*)stage64;
@@ -210,8 +209,8 @@ enum { kFluidStep = 0, kParticleStep = 1, kOverlapStep = 2 };
 // Enqueue one piece of Algorithm 1 on the flow's stream: the fluid step n ->
 // n+1, the particle step between levels n and n+1, or the particle step of n
 // on a forked branch alongside the fluid step of n+1.  The two are
-// independent: particles of step n read the level pair (n, n+1), the fluid
-// step of n+1 writes level n+2 into the pairs (n+1, n+2) and (n+2, n+3).
+// independent: particles of step n read the level pair (n, n+1); the fluid
+// step of n+1 only reads that pair's second half and writes pair (n+1, n+2).
 el_status enqueue_step(el_flow* f, int kind, int64_t step) {
     if (kind == kFluidStep) return fluid_step(f, step);
     if (kind == kParticleStep) return particles_step_all(f, step);
@@ -241,7 +240,7 @@ cudaGraphExec_t* graph_slot(el_flow* f, int kind, int phase, int64_t** count) {
     return &f->g_both[phase];
 }
 
-// Capture `kind` for ring phase `phase` (a step >= 1 with that phase: the
+// Capture `kind` for step parity `phase` (a step >= 1 with that parity: the
 // first, forward-Euler fluid step always runs by direct launches).
 el_status build_graph(el_flow* f, int kind, int phase) {
     int64_t* count = nullptr;
@@ -253,7 +252,7 @@ el_status build_graph(el_flow* f, int kind, int phase) {
     int64_t before = f->launches;
     cudaGraph_t g = nullptr;
     EL_CUDA_OK(f, cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal));
-    el_status s = enqueue_step(f, kind, 3 + phase);
+    el_status s = enqueue_step(f, kind, 2 + phase);
     cudaError_t e = cudaStreamEndCapture(f->stream, &g);
     if (s != EL_OK) {
         if (g) cudaGraphDestroy(g);
@@ -275,7 +274,7 @@ bool graphs_enabled(const el_flow* f) {
 
 el_status run_step(el_flow* f, int kind, int64_t step) {
     if (!graphs_enabled(f) || (kind == kFluidStep && step == 0)) return enqueue_step(f, kind, step);
-    int phase = (int)(step % 3);
+    int phase = (int)(step % 2);
     int64_t* count = nullptr;
     cudaGraphExec_t* slot = graph_slot(f, kind, phase, &count);
     if (!*slot) EL_TRY(build_graph(f, kind, phase));
@@ -295,7 +294,7 @@ el_status maybe_sort(el_flow* f) {
 }  // namespace
 
 void drop_graphs(el_flow* f) {
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < 2; k++) {
         cudaGraphExec_t* gs[3] = {&f->g_fluid[k], &f->g_part[k], &f->g_both[k]};
         for (cudaGraphExec_t* g : gs) {
             if (*g) cudaGraphExecDestroy(*g);
@@ -588,87 +587,6 @@ el_status el_set_tuning(el_flow* f, const el_tuning* t) {
     return EL_OK;
 }
 
-}  // extern "C"
-
-namespace {
-
-// Milliseconds per step of `window` steps after two untimed ones, with
-// CUDA events on `stream` (re-binning included where it falls due).
-template <class StepFn>
-el_status time_steps(StepFn step, cudaStream_t stream, int window, double* ms, char* why) {
-    cudaEvent_t a, b;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return EL_ECUDA;
-    el_status s = step(2);
-    if (s == EL_OK) {
-        cudaEventRecord(a, stream);
-        s = step(window);
-        cudaEventRecord(b, stream);
-    }
-    if (s == EL_OK && cudaEventSynchronize(b) == cudaSuccess) {
-        float t = 0.f;
-        cudaEventElapsedTime(&t, a, b);
-        *ms = t / window;
-    } else if (s == EL_OK) {
-        s = EL_ECUDA;
-        snprintf(why, 128, "event synchronize failed");
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return s;
-}
-
-// Coordinate search over the particle step's block size, then the
-// re-binning cadence, then the re-binning tile.  None of them changes any
-// result (every particle's arithmetic is independent of order and launch
-// shape), so the trial steps are ordinary steps of the simulation.
-template <class StepFn, class ApplyFn>
-el_status autotune(StepFn step, ApplyFn apply, cudaStream_t stream, el_tuning start, int trial,
-                   el_tuning* best_out, int n) {
-    char why[128] = {0};
-    el_tuning best = start;
-    double best_ms = 1e30;
-    auto trial_of = [&](el_tuning t) -> el_status {
-        EL_TRY(apply(t));
-        int window = std::max(trial, 2 * t.sort_every);
-        double ms = 0.0;
-        EL_TRY(time_steps(step, stream, window, &ms, why));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = t;
-        }
-        return EL_OK;
-    };
-    const int threads[] = {128, 256, 512};
-    const int cadence[] = {0, 5, 10, 20, 40};
-    const int shifts[] = {0, 1, 2};
-    for (int th : threads) {
-        el_tuning t = best;
-        t.rk4_threads = th;
-        EL_TRY(trial_of(t));
-    }
-    for (int c : cadence) {
-        el_tuning t = best;
-        t.sort_every = c;
-        if (c == best.sort_every && best_ms < 1e30) continue;
-        EL_TRY(trial_of(t));
-    }
-    if (best.sort_every > 0)
-        for (int sh : shifts) {
-            if ((1 << sh) > n / 4 || sh == best.sort_shift) continue;
-            el_tuning t = best;
-            t.sort_shift = sh;
-            EL_TRY(trial_of(t));
-        }
-    EL_TRY(apply(best));
-    best.ms_per_step = best_ms;
-    *best_out = best;
-    return EL_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
 el_status el_autotune(el_flow* f, int32_t trial_steps, el_tuning* best) {
     if (!f || !best) return EL_EINVAL;
     if (f->batch) return fail(f, EL_ESTATE, "flow belongs to a batch: use el_batch_autotune");
@@ -677,7 +595,12 @@ el_status el_autotune(el_flow* f, int32_t trial_steps, el_tuning* best) {
     el_get_tuning(f, &start);
     auto step = [f](int n) { return el_step_coupled(f, n); };
     auto apply = [f](el_tuning t) { return el_set_tuning(f, &t); };
-    return autotune(step, apply, f->stream, start, trial_steps, best, f->n);
+    auto sort_all = [f]() -> el_status {
+        for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_sort(f, s));
+        f->since_sort = 0;
+        return EL_OK;
+    };
+    return autotune_model(step, apply, sort_all, f->stream, start, trial_steps, best, f->n);
 }
 
 el_status el_destroy_flow(el_flow* f) {

@@ -6,7 +6,8 @@
 //   cuFFT C2R per member, on forked branches (they run concurrently)
 //   k_batch_nonlinear (persistent, every member's nodes)   nonlinear term + snapshot
 //   cuFFT R2C per member, on forked branches
-//   k_batch_rk4       (persistent, every member's species) RK4 particle step
+//   k_batch_rk4<S>    (persistent, every member's species) RK4 particle step,
+//                     one launch per interpolation scheme present
 //   k_batch_advance                                        per-member step counters
 //
 // The per-element arithmetic is the single-flow kernels' (stages.cuh), so a
@@ -16,6 +17,7 @@
 // Re-binning runs per member, outside the graph, when it is due.
 #include "common.cuh"
 #include "stages.cuh"
+#include "tune.cuh"
 
 #include <algorithm>
 #include <cstdarg>
@@ -29,7 +31,7 @@ struct MemberDev {
     SpecArgs spec;          // arrays and constants of k_spectral (first from `step`)
     const float4* phys4;
     float4* nl4;
-    float4* snap[3];        // ring of level pairs: snap[k % 3] = levels (k, k+1)
+    float4* snap[2];        // level pairs: snap[k % 2] = levels (k, k+1)
     unsigned long long n4;  // n^2 / 4
     int stencil_plane, n, log2n, scheme;
     float dt, h;
@@ -91,24 +93,23 @@ __global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_co
         const size_t q = (size_t)(t - b.nl_begin[m]) * kBNlThreads + threadIdx.x;
         const long long lv = md.step + 1;  // the level this step produces
         if (q < md.n4)
-            nonlinear_quad(md.phys4, md.nl4, md.snap[(lv + 2) % 3], md.snap[lv % 3], nullptr, md.n4,
-                           q, md.stencil_plane);
+            nonlinear_quad(md.phys4, md.nl4, md.snap[lv % 2], md.snap[(lv + 1) % 2], nullptr,
+                           md.n4, q, md.stencil_plane);
     }
 }
 
-__global__ void __launch_bounds__(512) k_batch_rk4(const __grid_constant__ BatchArgs b) {
+// One kernel per interpolation scheme (each with its own register budget);
+// the entries of the other schemes are skipped.
+template <int SCHEME>
+__global__ void __launch_bounds__(512, SCHEME == 0 ? 3 : 1) k_batch_rk4(const __grid_constant__ BatchArgs b) {
     for (int t = blockIdx.x; t < b.rk_tasks; t += gridDim.x) {
         const int e = owner_of(b.rk_begin, b.nentries, t);
-        const SpeciesDev& sd = *b.rk_sp[e];
         const MemberDev& md = b.members[b.rk_member[e]];
+        if (md.scheme != SCHEME) continue;
+        const SpeciesDev& sd = *b.rk_sp[e];
         const int p = (t - b.rk_begin[e]) * (int)blockDim.x + (int)threadIdx.x;
         if (p >= sd.np) continue;
-        const float4* snap = md.snap[md.step % 3];
-        switch (md.scheme) {
-            case 0: rk4_particle<0>(snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
-            case 1: rk4_particle<1>(snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
-            default: rk4_particle<2>(snap, md.n, md.log2n, md.dt, md.h, sd, p); break;
-        }
+        rk4_particle<SCHEME>(md.snap[md.step % 2], md.n, md.log2n, md.dt, md.h, sd, p);
     }
 }
 
@@ -140,7 +141,8 @@ struct el_batch {
     std::vector<int> h_spec_begin, h_nl_begin, h_rk_begin, h_rk_member;
     std::vector<const SpeciesDev*> h_rk_sp;
     BatchArgs args{};
-    int grid_spec = 0, grid_nl = 0, grid_rk = 0;
+    int grid_spec = 0, grid_nl = 0, grid_rk[3] = {0, 0, 0};
+    bool scheme_used[3] = {false, false, false};
     bool tables_valid = false;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_kernels = 0;
@@ -199,7 +201,7 @@ MemberDev member_of(el_flow* f) {
     a.nu = (float)f->d.nu;
     md.phys4 = reinterpret_cast<const float4*>(f->phys);
     md.nl4 = reinterpret_cast<float4*>(f->nl);
-    for (int k = 0; k < 3; k++) md.snap[k] = f->snap[k];
+    for (int k = 0; k < 2; k++) md.snap[k] = f->snap[k];
     md.n4 = f->n2 / 4;
     md.stencil_plane = f->stencil_plane;
     md.n = f->n;
@@ -275,8 +277,13 @@ el_status rebuild_tables(el_batch* b) {
     b->grid_spec = std::max(1, std::min(a.spec_tasks, occ * b->sms));
     BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_nonlinear, kBNlThreads, 0));
     b->grid_nl = std::max(1, std::min(a.nl_tasks, occ * b->sms));
-    BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_rk4, rk_threads, 0));
-    b->grid_rk = std::max(1, std::min(a.rk_tasks, std::max(1, occ) * b->sms));
+    void (*rk_kernels[3])(BatchArgs) = {k_batch_rk4<0>, k_batch_rk4<1>, k_batch_rk4<2>};
+    for (int sc = 0; sc < 3; sc++) {
+        b->scheme_used[sc] = false;
+        for (el_flow* f : b->members) b->scheme_used[sc] = b->scheme_used[sc] || f->d.interp == sc;
+        BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rk_kernels[sc], rk_threads, 0));
+        b->grid_rk[sc] = std::max(1, std::min(a.rk_tasks, std::max(1, occ) * b->sms));
+    }
     b->tables_valid = true;
     return EL_OK;
 }
@@ -311,8 +318,10 @@ el_status capture_body(el_batch* b) {
     EL_TRY(fork_ffts(b, false));
     if (a.rk_tasks > 0) {
         int threads = b->members.empty() ? 256 : b->members[0]->rk4_threads;
-        k_batch_rk4<<<b->grid_rk, threads, 0, b->stream>>>(a);
-        b->launches++;
+        if (b->scheme_used[0]) k_batch_rk4<0><<<b->grid_rk[0], threads, 0, b->stream>>>(a);
+        if (b->scheme_used[1]) k_batch_rk4<1><<<b->grid_rk[1], threads, 0, b->stream>>>(a);
+        if (b->scheme_used[2]) k_batch_rk4<2><<<b->grid_rk[2], threads, 0, b->stream>>>(a);
+        b->launches += (int)b->scheme_used[0] + (int)b->scheme_used[1] + (int)b->scheme_used[2];
     }
     k_batch_advance<<<1, 256, 0, b->stream>>>(b->d_members, a.nmembers);
     b->launches++;
@@ -499,27 +508,6 @@ el_status el_batch_destroy(el_batch* b) {
 
 namespace {
 
-template <class StepFn>
-el_status batch_time(StepFn step, cudaStream_t stream, int window, double* ms) {
-    cudaEvent_t a, b;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return EL_ECUDA;
-    el_status s = step(2);
-    if (s == EL_OK) {
-        cudaEventRecord(a, stream);
-        s = step(window);
-        cudaEventRecord(b, stream);
-    }
-    if (s == EL_OK) {
-        if (cudaEventSynchronize(b) != cudaSuccess) s = EL_ECUDA;
-        float t = 0.f;
-        cudaEventElapsedTime(&t, a, b);
-        *ms = t / window;
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return s;
-}
-
 el_status batch_apply(el_batch* b, const el_tuning& t) {
     for (el_flow* f : b->members) {
         f->rk4_threads = t.rk4_threads;
@@ -538,39 +526,17 @@ extern "C" el_status el_batch_autotune(el_batch* b, int32_t trial_steps, el_tuni
     if (trial_steps < 1) return bfail(b, EL_EINVAL, "trial_steps must be >= 1");
     if (b->members.empty()) return bfail(b, EL_ESTATE, "empty batch");
     el_flow* f0 = b->members[0];
-    el_tuning best{f0->rk4_threads, f0->d.sort_every, f0->sort_shift, 0.0};
-    double best_ms = 1e30;
+    el_tuning start{f0->rk4_threads, f0->d.sort_every, f0->sort_shift, 0.0};
+    int nmin = f0->n;
+    for (el_flow* f : b->members) nmin = std::min(nmin, f->n);
     auto step = [b](int n) { return el_batch_step(b, n); };
-    auto trial = [&](el_tuning t) -> el_status {
-        EL_TRY(batch_apply(b, t));
-        double ms = 0.0;
-        EL_TRY(batch_time(step, b->stream, std::max(trial_steps, 2 * t.sort_every), &ms));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = t;
+    auto apply = [b](el_tuning t) { return batch_apply(b, t); };
+    auto sort_all = [b]() -> el_status {
+        for (el_flow* f : b->members) {
+            for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_sort(f, s));
+            f->since_sort = 0;
         }
         return EL_OK;
     };
-    for (int th : {128, 256, 512}) {
-        el_tuning t = best;
-        t.rk4_threads = th;
-        EL_TRY(trial(t));
-    }
-    for (int c : {0, 5, 10, 20, 40}) {
-        if (c == best.sort_every) continue;
-        el_tuning t = best;
-        t.sort_every = c;
-        EL_TRY(trial(t));
-    }
-    if (best.sort_every > 0)
-        for (int sh : {0, 1, 2}) {
-            if (sh == best.sort_shift) continue;
-            el_tuning t = best;
-            t.sort_shift = sh;
-            EL_TRY(trial(t));
-        }
-    EL_TRY(batch_apply(b, best));
-    best.ms_per_step = best_ms;
-    *best_out = best;
-    return EL_OK;
+    return autotune_model(step, apply, sort_all, b->stream, start, trial_steps, best_out, nmin);
 }

@@ -76,7 +76,7 @@ struct el_flow {
     float2* spec = nullptr;   // nplanes half spectra (C2R input)
     float* phys = nullptr;    // nplanes physical planes (C2R output)
     float* nl = nullptr;      // physical nonlinear term (R2C input)
-    float4* snap[3] = {nullptr, nullptr, nullptr};  // ring: snap[k % 3] = levels (k, k+1) per node
+    float4* snap[2] = {nullptr, nullptr};  // level pairs: snap[k % 2] = levels (k, k+1) per node
     float2* aux_spec = nullptr;
     float* aux_phys = nullptr;
     double* stage64 = nullptr;  // n^2 doubles: host <-> device field staging
@@ -108,10 +108,10 @@ struct el_flow {
     int64_t since_sort = 0;
     int64_t launches = 0;
 
-    // captured graphs, one per ring phase (step % 3): the fluid step alone,
-    // the particle step alone, and particles(n) alongside fluid(n + 1)
-    cudaGraphExec_t g_fluid[3] = {}, g_part[3] = {}, g_both[3] = {};
-    int64_t k_fluid[3] = {}, k_part[3] = {}, k_both[3] = {};
+    // captured graphs, one per step parity: the fluid step alone, the
+    // particle step alone, and particles(n) alongside fluid(n + 1)
+    cudaGraphExec_t g_fluid[2] = {}, g_part[2] = {}, g_both[2] = {};
+    int64_t k_fluid[2] = {}, k_part[2] = {}, k_both[2] = {};
     cudaStream_t side = nullptr;       // second branch of the overlapped step
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
@@ -166,6 +166,7 @@ el_status particles_stats_into(el_flow* f, int s, double* out3);  // msd x, msd 
 el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv);
 
 void drop_graphs(el_flow* f);                     // api.cu
+
 
 // ---- sort (sort.cu) -------------------------------------------------------------
 el_status particles_sort(el_flow* f, int s);      // K7

@@ -10,7 +10,7 @@
 //                            scheme the prefiltered spline coefficients
 //   cuFFT C2R (batched)    : the planes to physical space
 //   K3 k_nonlinear         : N = u d(omega)/dx + v d(omega)/dy (Eq. 7), and the
-//                            new time level into the ring of level pairs
+//                            level pair (n, n+1) the particle step reads
 //   cuFFT R2C              : N-hat (Eq. 8)
 //
 // Modes are addressed by a 2-D grid (blockIdx.y = row j), so no thread
@@ -37,14 +37,14 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectral(const __grid_constant
     if (i == 0) spectral_mode<ADVANCE>(a, a.n / 2, j);
 }
 
-// N = u wx + v wy at every node and the new level into its two level pairs
+// N = u wx + v wy at every node and the level pair of the new level
 // (nonlinear_quad).  Four nodes per thread: 16-byte loads of the planes.
 __global__ void k_nonlinear(const float4* __restrict__ phys4, float4* __restrict__ nl4,
-                            float4* __restrict__ pair_prev, float4* __restrict__ pair_next,
-                            float4* __restrict__ init, size_t n4, int stencil_plane) {
+                            const float4* __restrict__ src, float4* __restrict__ dst,
+                            float4* __restrict__ other, size_t n4, int stencil_plane) {
     size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n4) return;
-    nonlinear_quad(phys4, nl4, pair_prev, pair_next, init, n4, q, stencil_plane);
+    nonlinear_quad(phys4, nl4, src, dst, other, n4, q, stencil_plane);
 }
 
 // Initial projection: mean removed, 2/3 rule (Sec. 3.1).
@@ -166,18 +166,17 @@ static SpecArgs spec_args(el_flow* f, int first) {
     return a;
 }
 
-// Planes -> physical fields, nonlinear term, level m into pairs (m-1, m) and
-// (m, m+1) of the ring (pair (k, k+1) is snap[k % 3]), N-hat.
+// Planes -> physical fields, nonlinear term, the pair (m-1, m) of the new
+// level m (pair (k, k+1) is snap[k % 2]), N-hat.
 static el_status finish_rhs(el_flow* f, int64_t m, bool setup) {
     const int T = 256;
     EL_TRY(fft_exec_c2r(f, f->plan_c2r, f->spec, f->phys));
     size_t n4 = f->n2 / 4;
-    float4* prev = f->snap[(m + 2) % 3];
-    float4* next = f->snap[m % 3];
-    float4* third = f->snap[(m + 1) % 3];
+    float4* dst = f->snap[(m + 1) % 2];        // pair (m-1, m)
+    const float4* src = f->snap[m % 2];        // pair (m-2, m-1): level m-1 in its second half
     k_nonlinear<<<blocks_for((int64_t)n4, T), T, 0, f->stream>>>(
-        reinterpret_cast<const float4*>(f->phys), reinterpret_cast<float4*>(f->nl), prev, next,
-        setup ? third : nullptr, n4, f->stencil_plane);
+        reinterpret_cast<const float4*>(f->phys), reinterpret_cast<float4*>(f->nl),
+        setup ? nullptr : src, dst, setup ? f->snap[m % 2] : nullptr, n4, f->stencil_plane);
     EL_LAUNCHED(f);
     EL_TRY(fft_exec_r2c(f, f->nl, f->nhat));
     return EL_OK;
@@ -236,9 +235,10 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn) {
         k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(f->phys + (which - 1) * f->n2,
                                                                    out, f->n2, 1, 0);
     } else {
-        // stencil field of the current level n: first half of pair (n, n+1)
+        // stencil field of the current level n: second half of pair (n-1, n)
         k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(
-            reinterpret_cast<const float*>(f->snap[f->step % 3]), out, f->n2, 4, which - 3);
+            reinterpret_cast<const float*>(f->snap[(f->step + 1) % 2]), out, f->n2, 4,
+            2 + (which - 3));
     }
     EL_LAUNCHED(f);
     EL_CUDA_OK(f, cudaMemcpyAsync(host_nn, out, f->n2 * sizeof(double), cudaMemcpyDeviceToHost,

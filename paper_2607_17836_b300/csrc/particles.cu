@@ -22,6 +22,15 @@ namespace el {
 namespace {
 
 constexpr int kRK4MaxThreads = 512;
+// Blocks of kRK4MaxThreads per SM the kernels are compiled for, which caps
+// their registers (2 -> 64, 3 -> 40): occupancy hides the two dependent
+// memory round trips of a particle (state, then stencil).
+#ifndef EL_RK4_BILINEAR_MIN_BLOCKS
+#define EL_RK4_BILINEAR_MIN_BLOCKS 3
+#endif
+#ifndef EL_RK4_CUBIC_MIN_BLOCKS
+#define EL_RK4_CUBIC_MIN_BLOCKS 1
+#endif
 
 struct RK4Args {
     const float4* snap;
@@ -34,7 +43,7 @@ struct RK4Args {
 // K6: one RK4 step of every species in one launch (blocks are split between
 // species by block_begin), between levels n and n+1 (rk4_particle).
 template <int SCHEME>
-__global__ void __launch_bounds__(kRK4MaxThreads) k_rk4(const __grid_constant__ RK4Args a) {
+__global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_MIN_BLOCKS : EL_RK4_CUBIC_MIN_BLOCKS) k_rk4(const __grid_constant__ RK4Args a) {
     int s = 0;
 #pragma unroll
     for (int k = 1; k < kMaxSpecies; k++)
@@ -86,8 +95,8 @@ __device__ float2 fluid_at_scheme(int scheme, const float4* snap, int n, int ci,
 }
 
 // K9: split-precision state from FP64 positions; velocity from vxy, or zero
-// slip (the interpolated fluid velocity of the current level: the first half
-// of the pair `snap`).
+// slip (the interpolated fluid velocity of the current level: the second
+// half of the pair `snap`).
 __global__ void k_init(const double* __restrict__ xy, const double* __restrict__ vxy, int64_t np,
                        int n, int scheme, int inertial, const float4* __restrict__ snap,
                        uint32_t* __restrict__ cell, float2* __restrict__ off,
@@ -109,7 +118,7 @@ __global__ void k_init(const double* __restrict__ xy, const double* __restrict__
         if (vxy) {
             vel[p] = make_float2((float)vxy[2 * p], (float)vxy[2 * p + 1]);
         } else {
-            vel[p] = fluid_at_scheme(scheme, snap, n, ci, cj, ox, oy, 1.0f, 0.0f);
+            vel[p] = fluid_at_scheme(scheme, snap, n, ci, cj, ox, oy, 0.0f, 1.0f);
         }
     }
 }
@@ -243,7 +252,7 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
     }
     if (np > 0) {
         k_init<<<blocks_for(np, T), T, 0, f->stream>>>(
-            stage, d_vxy, np, f->n, f->d.interp, st > 0.0 ? 1 : 0, f->snap[f->step % 3],
+            stage, d_vxy, np, f->n, f->d.interp, st > 0.0 ? 1 : 0, f->snap[(f->step + 1) % 2],
             sp.cell[cur], sp.off[cur], sp.vel[cur], sp.img[cur], sp.id[cur], sp.x0);
         EL_LAUNCHED(f);
     }
@@ -266,10 +275,10 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
 }
 
 // K6 for every species of the flow in one launch, step number `step`
-// (levels step and step + 1: pair snap[step % 3]).
+// (levels step and step + 1: pair snap[step % 2]).
 el_status particles_step_all(el_flow* f, int64_t step) {
     RK4Args a{};
-    a.snap = f->snap[step % 3];
+    a.snap = f->snap[step % 2];
     a.table = f->table;
     a.n = f->n;
     a.log2n = f->log2n;
@@ -342,10 +351,10 @@ el_status particles_stats_into(el_flow* f, int s, double* out3) {
 el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv) {
     if (np == 0) return EL_OK;
     const int T = 256;
-    // pair (n-1, n) of the ring: previous level first, current level second
+    // pair (n-1, n): previous level first, current level second
     float th = (float)theta;
     k_sample<<<blocks_for(np, T), T, 0, f->stream>>>(d_xy, np, f->n, f->d.interp, 1.0f - th, th,
-                                                      f->snap[(f->step + 2) % 3], d_uv);
+                                                      f->snap[(f->step + 1) % 2], d_uv);
     EL_LAUNCHED(f);
     return EL_OK;
 }

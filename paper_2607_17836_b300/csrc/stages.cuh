@@ -124,16 +124,17 @@ __device__ __forceinline__ void spectral_mode(const SpecArgs& a, int i, int j) {
     }
 }
 
-// N = u wx + v wy at four consecutive nodes 4q..4q+3 (Eq. 7).  The stencil
-// field of the new level m goes to the second half of pair (m-1, m) and the
-// first half of pair (m, m+1).  At set-up (`init` = the third pair) level 0
-// fills both halves of all three pairs, so no pair ever holds uninitialised
-// values (a blend weight of 0 times a NaN left in reused memory is NaN).
+// N = u wx + v wy at four consecutive nodes 4q..4q+3 (Eq. 7), and the
+// level pair (m-1, m) of the new level m: `dst` = (level m-1 read from the
+// second half of `src`, level m), one full 16-byte store per node.  At set-up
+// (src == nullptr) level 0 fills both halves of `dst` and of `other`, so no
+// pair ever holds uninitialised values (a blend weight of 0 times a NaN left
+// in reused memory is NaN).
 __device__ __forceinline__ void nonlinear_quad(const float4* __restrict__ phys4,
                                                float4* __restrict__ nl4,
-                                               float4* __restrict__ pair_prev,
-                                               float4* __restrict__ pair_next,
-                                               float4* __restrict__ init, size_t n4, size_t q,
+                                               const float4* __restrict__ src,
+                                               float4* __restrict__ dst,
+                                               float4* __restrict__ other, size_t n4, size_t q,
                                                int stencil_plane) {
     float4 u = phys4[q], v = phys4[n4 + q], wx = phys4[2 * n4 + q], wy = phys4[3 * n4 + q];
     nl4[q] = make_float4(fmaf(u.x, wx.x, v.x * wy.x), fmaf(u.y, wx.y, v.y * wy.y),
@@ -142,19 +143,18 @@ __device__ __forceinline__ void nonlinear_quad(const float4* __restrict__ phys4,
         u = phys4[4 * n4 + q];
         v = phys4[5 * n4 + q];
     }
-    float2* prev2 = reinterpret_cast<float2*>(pair_prev + 4 * q);
-    float2* next2 = reinterpret_cast<float2*>(pair_next + 4 * q);
     const float2 s[4] = {make_float2(u.x, v.x), make_float2(u.y, v.y), make_float2(u.z, v.z),
                          make_float2(u.w, v.w)};
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        prev2[2 * k + 1] = s[k];
-        next2[2 * k] = s[k];
-        if (init) {
+        const size_t i = 4 * q + k;
+        if (src) {
+            const float4 old = src[i];
+            dst[i] = make_float4(old.z, old.w, s[k].x, s[k].y);
+        } else {
             const float4 both = make_float4(s[k].x, s[k].y, s[k].x, s[k].y);
-            pair_prev[4 * q + k] = both;
-            pair_next[4 * q + k] = both;
-            init[4 * q + k] = both;
+            dst[i] = both;
+            other[i] = both;
         }
     }
 }
