@@ -75,6 +75,11 @@ typedef struct {
     int32_t max_species;        /* 0..EL_MAX_SPECIES                                     */
     int32_t sort_every;         /* re-bin particles by cell every k steps; 0 = never     */
     int64_t max_particles;      /* capacity summed over all species                      */
+    int32_t tracer_velocity;    /* tracers (St = 0) take the fluid velocity from
+                                   0: the interpolated velocity field (default);
+                                   1: the interpolated streamfunction at (x +- dx, y)
+                                      and (x, y +- dy) and centred differences
+                                      (Sec. 3.2, Eq. 11), the paper's production path */
 } el_flow_desc;
 
 /* Bytes of device workspace a flow with this description needs (0 if the

@@ -78,6 +78,10 @@ def _load():
         lib.orc_bspline_prefilter.argtypes = [ctypes.c_int, D]
         lib.orc_particles_rk4.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           D, D, D, D, I64, D, D, D, D]
+        lib.orc_flow_psi.argtypes = [ctypes.c_void_p, D]
+        lib.orc_psi_velocity_many.argtypes = [ctypes.c_int, ctypes.c_int, D, I64, D, D, D, D]
+        lib.orc_tracers_rk4_psi.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, D, D, I64,
+                                            D, D]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -148,6 +152,24 @@ def particles_rk4(scheme, dt, st, un, vn, un1, vn1, x, y, vx=None, vy=None):
                               _p(vy) if st > 0 else None)
 
 
+def psi_velocity(psi, scheme, x, y):
+    """Tracer velocity from the streamfunction grid function by Eq. 11."""
+    psi = _f64(psi)
+    x, y = _f64(np.atleast_1d(x)), _f64(np.atleast_1d(y))
+    u, v = np.empty_like(x), np.empty_like(x)
+    _load().orc_psi_velocity_many(int(psi.shape[0]), int(scheme), _p(psi), int(x.size), _p(x),
+                                  _p(y), _p(u), _p(v))
+    return u, v
+
+
+def tracers_rk4_psi(scheme, dt, psin, psin1, x, y):
+    """One RK4 step in place of tracers driven by the streamfunction (Eq. 11)."""
+    a, b = _f64(psin), _f64(psin1)
+    assert x.dtype == np.float64 and y.dtype == np.float64
+    _load().orc_tracers_rk4_psi(int(a.shape[0]), int(scheme), float(dt), _p(a), _p(b), int(x.size),
+                                _p(x), _p(y))
+
+
 # --- fluid --------------------------------------------------------------------
 class Flow:
     """Pseudospectral AB2 vorticity solver on the periodic [0, 2 pi)^2 grid."""
@@ -179,6 +201,11 @@ class Flow:
         out = {k: np.empty((n, n)) for k in which}
         ptrs = [_p(out.get(k)) for k in ("u", "v", "w", "wx", "wy")]
         self._lib.orc_flow_fields(self._h, *ptrs)
+        return out
+
+    def psi(self):
+        out = np.empty((self.n, self.n))
+        self._lib.orc_flow_psi(self._h, _p(out))
         return out
 
     def spectrum(self):
@@ -236,12 +263,21 @@ class Coupled:
     """One-way coupled step of Algorithm 1: advance the fluid n -> n+1, then
     every particle species by one RK4 step between the two field levels."""
 
-    def __init__(self, n, nu, dt, omega0, scheme=BILINEAR, ab2_mode=0, bspline_prefilter=True):
+    def __init__(self, n, nu, dt, omega0, scheme=BILINEAR, ab2_mode=0, bspline_prefilter=True,
+                 tracer_velocity=0):
         self.flow = Flow(n, nu, dt, omega0, ab2_mode)
         self.n, self.dt, self.scheme = int(n), float(dt), int(scheme)
         self.prefilter = bool(bspline_prefilter)
+        self.tracer_psi = bool(tracer_velocity)
         self.species: list[Species] = []
         self._level = self._stencil_fields()
+        self._psi = self._psi_field()
+
+    def _psi_field(self):
+        if not self.tracer_psi:
+            return None
+        p = self.flow.psi()
+        return bspline_prefilter(p) if self.scheme == BSPLINE and self.prefilter else p
 
     def _stencil_fields(self):
         f = self.flow.fields(("u", "v"))
@@ -271,11 +307,17 @@ class Coupled:
     def step(self, nsteps=1):
         for _ in range(int(nsteps)):
             un, vn = self._level
+            pn = self._psi
             self.flow.step(1)
             un1, vn1 = self._stencil_fields()
+            pn1 = self._psi_field()
             for s in self.species:
-                particles_rk4(self.scheme, self.dt, s.st, un, vn, un1, vn1, s.x, s.y, s.vx, s.vy)
+                if s.st == 0 and self.tracer_psi:
+                    tracers_rk4_psi(self.scheme, self.dt, pn, pn1, s.x, s.y)
+                else:
+                    particles_rk4(self.scheme, self.dt, s.st, un, vn, un1, vn1, s.x, s.y, s.vx, s.vy)
             self._level = (un1, vn1)
+            self._psi = pn1
 
     def stats(self):
         e, z, p = self.flow.diagnostics()

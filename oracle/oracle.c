@@ -234,6 +234,19 @@ void orc_flow_fields(orc_flow *f, double *u, double *v, double *w, double *wx, d
     (void)nn;
 }
 
+/* Physical streamfunction psi of the current spectrum (Eq. 5). */
+void orc_flow_psi(orc_flow *f, double *psi) {
+    int n = f->n;
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+            size_t q = (size_t)j * n + i;
+            double kx = wavenum(i, n), ky = wavenum(j, n), k2 = kx * kx + ky * ky;
+            f->t0r[q] = k2 > 0.0 ? f->wr[q] / k2 : 0.0;
+            f->t0i[q] = k2 > 0.0 ? f->wi[q] / k2 : 0.0;
+        }
+    to_physical(n, f->t0r, f->t0i, psi);
+}
+
 /* Dealiased spectral nonlinear term N-hat = FFT(u d(omega)/dx + v d(omega)/dy)
  * (Eqs. 7, 8), with the 2/3 rule applied, into (nr, ni). */
 static void nonlinear_hat(orc_flow *f, double *nr, double *ni) {
@@ -479,6 +492,51 @@ static void stage_velocity(const orc_vel *c, double x, double y, double theta, d
     double b1 = orc_interp(c->n, c->vn1, c->scheme, x, y);
     *u = (1.0 - theta) * a0 + theta * a1;
     *v = (1.0 - theta) * b0 + theta * b1;
+}
+
+/* Tracer velocity from the streamfunction, Sec. 3.2 and Eq. 11: psi at the
+ * four points (x +- dx, y), (x, y +- dy) (mapped periodically inside
+ * orc_interp), each interpolated in space by the scheme and blended linearly
+ * in time; u = (psi_N - psi_S) / 2dy, v = -(psi_E - psi_W) / 2dx. */
+static void psi_velocity(int n, int scheme, const double *pn, const double *pn1, double x,
+                         double y, double theta, double *u, double *v) {
+    double d = TWO_PI / (double)n;
+    double px[4] = {x, x, x + d, x - d}, py[4] = {y + d, y - d, y, y};
+    double val[4];
+    for (int k = 0; k < 4; k++) {
+        double a = orc_interp(n, pn, scheme, px[k], py[k]);
+        double b = orc_interp(n, pn1, scheme, px[k], py[k]);
+        val[k] = (1.0 - theta) * a + theta * b;
+    }
+    *u = (val[0] - val[1]) / (2.0 * d);
+    *v = -(val[2] - val[3]) / (2.0 * d);
+}
+
+void orc_psi_velocity_many(int n, int scheme, const double *psi, int64_t np, const double *x,
+                           const double *y, double *u, double *v) {
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < np; p++) psi_velocity(n, scheme, psi, psi, x[p], y[p], 0.0, &u[p], &v[p]);
+}
+
+/* One RK4 step (Eq. 12) of np tracers whose velocity comes from the
+ * streamfunction (levels psin, psin1; coefficients for the B-spline scheme). */
+void orc_tracers_rk4_psi(int n, int scheme, double dt, const double *psin, const double *psin1,
+                         int64_t np, double *x, double *y) {
+    const double theta[4] = {0.0, 0.5, 0.5, 1.0};
+    const double frac[4] = {0.0, 0.5, 0.5, 1.0};
+    const double wgt[4] = {1.0, 2.0, 2.0, 1.0};
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < np; p++) {
+        double x0 = x[p], y0 = y[p], kx = 0.0, ky = 0.0, sx = 0.0, sy = 0.0;
+        for (int s = 0; s < 4; s++) {
+            psi_velocity(n, scheme, psin, psin1, x0 + frac[s] * dt * kx, y0 + frac[s] * dt * ky,
+                         theta[s], &kx, &ky);
+            sx += wgt[s] * kx;
+            sy += wgt[s] * ky;
+        }
+        x[p] = x0 + dt / 6.0 * sx;
+        y[p] = y0 + dt / 6.0 * sy;
+    }
 }
 
 /* One RK4 step of length dt for np particles, from time level n (fields

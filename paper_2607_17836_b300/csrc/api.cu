@@ -40,11 +40,12 @@ const char* check_desc(const el_flow_desc* d) {
     if (d->max_particles < 0 || d->max_particles > ((int64_t)1 << 31)) return "max_particles out of range";
     if (d->max_particles > 0 && d->max_species == 0) return "max_particles > 0 needs max_species > 0";
     if (d->sort_every < 0) return "sort_every must be >= 0";
+    if (d->tracer_velocity != 0 && d->tracer_velocity != 1) return "tracer_velocity must be 0 or 1";
     return nullptr;
 }
 
 int planes_of(const el_flow_desc& d) {
-    return (d.interp == EL_BSPLINE && d.bspline_prefilter) ? 6 : 4;
+    return 4 + ((d.interp == EL_BSPLINE && d.bspline_prefilter) ? 2 : 0) + (d.tracer_velocity ? 1 : 0);
 }
 
 // Bytes one species of np particles takes from the pool: 12 arrays, each
@@ -128,6 +129,8 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* nl = take(n2 * 4);
     char* snap0 = take(n2 * 16);
     char* snap1 = take(n2 * 16);
+    char* psi0 = d.tracer_velocity ? take(n2 * 8) : nullptr;
+    char* psi1 = d.tracer_velocity ? take(n2 * 8) : nullptr;
     char* aux_spec = take(nm * 8);
     char* aux_phys = take(n2 * 4);
     char* stage64 = take(n2 * 8);
@@ -155,6 +158,8 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->nl = (float*)nl;
         f->snap[0] = (float4*)snap0;
         f->snap[1] = (float4*)snap1;
+        f->psi[0] = (float2*)psi0;
+        f->psi[1] = (float2*)psi1;
         f->aux_spec = (float2*)aux_spec;
         f->aux_phys = (float*)aux_phys;
         f->stage64 = (double*)stage64;
@@ -359,7 +364,8 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     f->n2 = (size_t)f->n * f->n;
     f->nmodes = (size_t)f->n * f->nh;
     f->nplanes = planes_of(*desc);
-    f->stencil_plane = f->nplanes == 6 ? 4 : 0;
+    f->stencil_plane = (desc->interp == EL_BSPLINE && desc->bspline_prefilter) ? 4 : 0;
+    f->psi_plane = desc->tracer_velocity ? f->nplanes - 1 : -1;
     f->ws = (char*)dev_workspace;
     f->ws_bytes = workspace_bytes;
     carve(*desc, fft, f, f->ws);

@@ -32,8 +32,9 @@ struct MemberDev {
     const float4* phys4;
     float4* nl4;
     float4* snap[2];        // level pairs: snap[k % 2] = levels (k, k+1)
+    float2* psi[2];         // streamfunction level pairs, or nullptr
     unsigned long long n4;  // n^2 / 4
-    int stencil_plane, n, log2n, scheme;
+    int stencil_plane, psi_plane, n, log2n, scheme;
     float dt, h;
     long long step;
 };
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_co
         const long long lv = md.step + 1;  // the level this step produces
         if (q < md.n4)
             nonlinear_quad(md.phys4, md.nl4, md.snap[lv % 2], md.snap[(lv + 1) % 2], nullptr,
-                           md.n4, q, md.stencil_plane);
+                           md.n4, q, md.stencil_plane, md.psi_plane, md.psi[lv % 2],
+                           md.psi[(lv + 1) % 2], nullptr);
     }
 }
 
@@ -109,7 +111,12 @@ __global__ void __launch_bounds__(512, SCHEME == 0 ? 3 : 1) k_batch_rk4(const __
         const SpeciesDev& sd = *b.rk_sp[e];
         const int p = (t - b.rk_begin[e]) * (int)blockDim.x + (int)threadIdx.x;
         if (p >= sd.np) continue;
-        rk4_particle<SCHEME>(md.snap[md.step % 2], md.n, md.log2n, md.dt, md.h, sd, p);
+        if (md.psi_plane >= 0)
+            rk4_particle<SCHEME, true>(md.snap[md.step % 2], md.psi[md.step % 2], md.n, md.log2n,
+                                       md.dt, md.h, sd, p);
+        else
+            rk4_particle<SCHEME, false>(md.snap[md.step % 2], nullptr, md.n, md.log2n, md.dt, md.h,
+                                        sd, p);
     }
 }
 
@@ -193,6 +200,8 @@ MemberDev member_of(el_flow* f) {
     a.n = f->n;
     a.nh = f->nh;
     a.nplanes = f->nplanes;
+    a.spline = f->stencil_plane != 0;
+    a.psi_plane = f->psi_plane;
     a.mode = f->d.ab2_mode;
     a.first = 0;
     a.nmodes = f->nmodes;
@@ -201,7 +210,11 @@ MemberDev member_of(el_flow* f) {
     a.nu = (float)f->d.nu;
     md.phys4 = reinterpret_cast<const float4*>(f->phys);
     md.nl4 = reinterpret_cast<float4*>(f->nl);
-    for (int k = 0; k < 2; k++) md.snap[k] = f->snap[k];
+    for (int k = 0; k < 2; k++) {
+        md.snap[k] = f->snap[k];
+        md.psi[k] = f->psi[k];
+    }
+    md.psi_plane = f->psi_plane;
     md.n4 = f->n2 / 4;
     md.stencil_plane = f->stencil_plane;
     md.n = f->n;

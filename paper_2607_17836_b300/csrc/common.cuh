@@ -61,8 +61,9 @@ struct el_flow {
     // geometry
     int n = 0, nh = 0, log2n = 0;
     size_t n2 = 0, nmodes = 0;
-    int nplanes = 4;         // 4: u, v, wx, wy; 6: + prefiltered cu, cv
+    int nplanes = 4;         // u, v, wx, wy [, prefiltered cu, cv] [, psi stencil]
     int stencil_plane = 0;   // plane holding the u the particle stencil weights
+    int psi_plane = -1;      // plane of the streamfunction stencil field, or -1
 
     // workspace carve-out
     char* ws = nullptr;
@@ -77,6 +78,7 @@ struct el_flow {
     float* phys = nullptr;    // nplanes physical planes (C2R output)
     float* nl = nullptr;      // physical nonlinear term (R2C input)
     float4* snap[2] = {nullptr, nullptr};  // level pairs: snap[k % 2] = levels (k, k+1) per node
+    float2* psi[2] = {nullptr, nullptr};   // streamfunction level pairs (tracer_velocity = 1)
     float2* aux_spec = nullptr;
     float* aux_phys = nullptr;
     double* stage64 = nullptr;  // n^2 doubles: host <-> device field staging

@@ -41,10 +41,13 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectral(const __grid_constant
 // (nonlinear_quad).  Four nodes per thread: 16-byte loads of the planes.
 __global__ void k_nonlinear(const float4* __restrict__ phys4, float4* __restrict__ nl4,
                             const float4* __restrict__ src, float4* __restrict__ dst,
-                            float4* __restrict__ other, size_t n4, int stencil_plane) {
+                            float4* __restrict__ other, size_t n4, int stencil_plane,
+                            int psi_plane, const float2* __restrict__ psi_src,
+                            float2* __restrict__ psi_dst, float2* __restrict__ psi_other) {
     size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n4) return;
-    nonlinear_quad(phys4, nl4, src, dst, other, n4, q, stencil_plane);
+    nonlinear_quad(phys4, nl4, src, dst, other, n4, q, stencil_plane, psi_plane, psi_src, psi_dst,
+                   psi_other);
 }
 
 // Initial projection: mean removed, 2/3 rule (Sec. 3.1).
@@ -157,6 +160,8 @@ static SpecArgs spec_args(el_flow* f, int first) {
     a.n = f->n;
     a.nh = f->nh;
     a.nplanes = f->nplanes;
+    a.spline = f->stencil_plane != 0;
+    a.psi_plane = f->psi_plane;
     a.mode = f->d.ab2_mode;
     a.first = first;
     a.nmodes = f->nmodes;
@@ -176,7 +181,9 @@ static el_status finish_rhs(el_flow* f, int64_t m, bool setup) {
     const float4* src = f->snap[m % 2];        // pair (m-2, m-1): level m-1 in its second half
     k_nonlinear<<<blocks_for((int64_t)n4, T), T, 0, f->stream>>>(
         reinterpret_cast<const float4*>(f->phys), reinterpret_cast<float4*>(f->nl),
-        setup ? nullptr : src, dst, setup ? f->snap[m % 2] : nullptr, n4, f->stencil_plane);
+        setup ? nullptr : src, dst, setup ? f->snap[m % 2] : nullptr, n4, f->stencil_plane,
+        f->psi_plane, setup ? nullptr : f->psi[m % 2], f->psi[(m + 1) % 2],
+        setup ? f->psi[m % 2] : nullptr);
     EL_LAUNCHED(f);
     EL_TRY(fft_exec_r2c(f, f->nl, f->nhat));
     return EL_OK;

@@ -192,4 +192,58 @@ struct Stencil {
     }
 };
 
+// Scalar field (the streamfunction) stored as level pairs (f_n, f_n+1) per
+// node: its value in cell (i, j) (unwrapped) at offsets (sx, sy), at the
+// stage time THETA (0: level n, 1: mid-way, 2: level n+1).
+template <int SCHEME, int THETA>
+__device__ __forceinline__ float scalar_at(const float2* __restrict__ f, int n, int i, int j,
+                                           float sx, float sy) {
+    const int m = n - 1;
+    auto lv = [&](int idx) {
+        const float2 t = __ldg(f + idx);
+        return THETA == 0 ? t.x : (THETA == 2 ? t.y : 0.5f * (t.x + t.y));
+    };
+    if (SCHEME == 0) {
+        const int i0 = i & m, i1 = (i + 1) & m, r0 = (j & m) * n, r1 = ((j + 1) & m) * n;
+        const float a = lv(r0 + i0), b = lv(r0 + i1), c = lv(r1 + i0), d = lv(r1 + i1);
+        const float lo = fmaf(sx, b - a, a), hi = fmaf(sx, d - c, c);
+        return fmaf(sy, hi - lo, lo);
+    } else {
+        float wx[4], wy[4];
+        if (SCHEME == 1) {
+            weights_catmull_rom(sx, wx);
+            weights_catmull_rom(sy, wy);
+        } else {
+            weights_bspline(sx, wx);
+            weights_bspline(sy, wy);
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const int row = ((j + b - 1) & m) * n;
+            float r = 0.f;
+#pragma unroll
+            for (int a = 0; a < 4; a++) r = fmaf(wx[a], lv(row + ((i + a - 1) & m)), r);
+            acc = fmaf(wy[b], r, acc);
+        }
+        return acc;
+    }
+}
+
+// Tracer velocity from the streamfunction (Eq. 11) at grid-unit position
+// (ci + l.x, cj + l.y): u = (psi(x, y+dy) - psi(x, y-dy)) / 2dy,
+// v = -(psi(x+dx, y) - psi(x-dx, y)) / 2dx, inv2d = 1 / (2 dx).
+template <int SCHEME, int THETA>
+__device__ __forceinline__ float2 psi_velocity(const float2* __restrict__ psi, int n, int ci, int cj,
+                                               float2 l, float inv2d) {
+    const float flx = floorf(l.x), fly = floorf(l.y);
+    const int i = ci + (int)flx, j = cj + (int)fly;
+    const float sx = l.x - flx, sy = l.y - fly;
+    const float pe = scalar_at<SCHEME, THETA>(psi, n, i + 1, j, sx, sy);
+    const float pw = scalar_at<SCHEME, THETA>(psi, n, i - 1, j, sx, sy);
+    const float pn = scalar_at<SCHEME, THETA>(psi, n, i, j + 1, sx, sy);
+    const float ps = scalar_at<SCHEME, THETA>(psi, n, i, j - 1, sx, sy);
+    return make_float2((pn - ps) * inv2d, (pw - pe) * inv2d);
+}
+
 }  // namespace el

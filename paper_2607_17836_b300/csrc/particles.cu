@@ -34,6 +34,7 @@ constexpr int kRK4MaxThreads = 512;
 
 struct RK4Args {
     const float4* snap;
+    const float2* psi;        // streamfunction pair (tracer_velocity = 1), else nullptr
     const SpeciesDev* table;  // device-resident: the sort flips `cur` there
     int n, log2n, nspecies;
     float dt, h;              // h = dt * n / (2 pi): grid units per unit velocity
@@ -42,7 +43,7 @@ struct RK4Args {
 
 // K6: one RK4 step of every species in one launch (blocks are split between
 // species by block_begin), between levels n and n+1 (rk4_particle).
-template <int SCHEME>
+template <int SCHEME, bool PSI>
 __global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_MIN_BLOCKS : EL_RK4_CUBIC_MIN_BLOCKS) k_rk4(const __grid_constant__ RK4Args a) {
     int s = 0;
 #pragma unroll
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_
     const SpeciesDev& sd = a.table[s];
     const int p = (int)(blockIdx.x - a.block_begin[s]) * (int)blockDim.x + (int)threadIdx.x;
     if (p >= sd.np) return;
-    rk4_particle<SCHEME>(a.snap, a.n, a.log2n, a.dt, a.h, sd, p);
+    rk4_particle<SCHEME, PSI>(a.snap, a.psi, a.n, a.log2n, a.dt, a.h, sd, p);
 }
 
 // FP64 position -> (cell, offset, image), Sec. 3.2: mapped periodically onto
@@ -279,6 +280,7 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
 el_status particles_step_all(el_flow* f, int64_t step) {
     RK4Args a{};
     a.snap = f->snap[step % 2];
+    a.psi = f->psi_plane >= 0 ? f->psi[step % 2] : nullptr;
     a.table = f->table;
     a.n = f->n;
     a.log2n = f->log2n;
@@ -296,10 +298,19 @@ el_status particles_step_all(el_flow* f, int64_t step) {
     a.nspecies = ns;
     // empty slots share block_begin with the next slot, so the last slot with
     // a given block_begin (the non-empty one) wins the select in the kernel
-    switch (f->d.interp) {
-        case EL_BILINEAR: k_rk4<0><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
-        case EL_CATMULL_ROM: k_rk4<1><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
-        default: k_rk4<2><<<blocks, f->rk4_threads, 0, f->stream>>>(a); break;
+    const int T = f->rk4_threads;
+    if (f->psi_plane < 0) {
+        switch (f->d.interp) {
+            case EL_BILINEAR: k_rk4<0, false><<<blocks, T, 0, f->stream>>>(a); break;
+            case EL_CATMULL_ROM: k_rk4<1, false><<<blocks, T, 0, f->stream>>>(a); break;
+            default: k_rk4<2, false><<<blocks, T, 0, f->stream>>>(a); break;
+        }
+    } else {
+        switch (f->d.interp) {
+            case EL_BILINEAR: k_rk4<0, true><<<blocks, T, 0, f->stream>>>(a); break;
+            case EL_CATMULL_ROM: k_rk4<1, true><<<blocks, T, 0, f->stream>>>(a); break;
+            default: k_rk4<2, true><<<blocks, T, 0, f->stream>>>(a); break;
+        }
     }
     EL_LAUNCHED(f);
     return EL_OK;

@@ -33,6 +33,8 @@ struct SpecArgs {
     const float* pre_x;
     const float* pre_y;
     int n, nh, nplanes, mode, first;
+    int spline;         // 1: write prefiltered cu, cv to planes 4, 5
+    int psi_plane;      // plane of the streamfunction stencil field, or -1
     size_t nmodes;
     float scale, dt, nu;
 };
@@ -115,13 +117,14 @@ __device__ __forceinline__ void spectral_mode(const SpecArgs& a, int i, int j) {
     spec[m + q] = vh;
     spec[2 * m + q] = make_float2(-dkx * w.y, dkx * w.x);  // i kx omega-hat
     spec[3 * m + q] = make_float2(-dky * w.y, dky * w.x);  // i ky omega-hat
-    if (a.nplanes == 6) {
-        // Interpolating cubic-spline coefficients: (c_{i-1} + 4 c_i + c_{i+1})/6 = f_i
-        // is diagonal in Fourier space with factor (2 + cos k dx)/3 per axis.
-        const float p = a.pre_x[i] * a.pre_y[j];
-        spec[4 * m + q] = make_float2(uh.x * p, uh.y * p);
-        spec[5 * m + q] = make_float2(vh.x * p, vh.y * p);
+    // Interpolating cubic-spline coefficients: (c_{i-1} + 4 c_i + c_{i+1})/6 = f_i
+    // is diagonal in Fourier space with factor (2 + cos k dx)/3 per axis.
+    const float pf = a.spline ? a.pre_x[i] * a.pre_y[j] : 1.0f;
+    if (a.spline) {
+        spec[4 * m + q] = make_float2(uh.x * pf, uh.y * pf);
+        spec[5 * m + q] = make_float2(vh.x * pf, vh.y * pf);
     }
+    if (a.psi_plane >= 0) spec[(size_t)a.psi_plane * m + q] = make_float2(psi.x * pf, psi.y * pf);
 }
 
 // N = u wx + v wy at four consecutive nodes 4q..4q+3 (Eq. 7), and the
@@ -135,7 +138,10 @@ __device__ __forceinline__ void nonlinear_quad(const float4* __restrict__ phys4,
                                                const float4* __restrict__ src,
                                                float4* __restrict__ dst,
                                                float4* __restrict__ other, size_t n4, size_t q,
-                                               int stencil_plane) {
+                                               int stencil_plane, int psi_plane,
+                                               const float2* __restrict__ psi_src,
+                                               float2* __restrict__ psi_dst,
+                                               float2* __restrict__ psi_other) {
     float4 u = phys4[q], v = phys4[n4 + q], wx = phys4[2 * n4 + q], wy = phys4[3 * n4 + q];
     nl4[q] = make_float4(fmaf(u.x, wx.x, v.x * wy.x), fmaf(u.y, wx.y, v.y * wy.y),
                          fmaf(u.z, wx.z, v.z * wy.z), fmaf(u.w, wx.w, v.w * wy.w));
@@ -155,6 +161,20 @@ __device__ __forceinline__ void nonlinear_quad(const float4* __restrict__ phys4,
             const float4 both = make_float4(s[k].x, s[k].y, s[k].x, s[k].y);
             dst[i] = both;
             other[i] = both;
+        }
+    }
+    if (psi_plane >= 0) {  // the streamfunction stencil field, same pair layout (scalar)
+        const float4 ps = phys4[(size_t)psi_plane * n4 + q];
+        const float pk[4] = {ps.x, ps.y, ps.z, ps.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const size_t i = 4 * q + k;
+            if (src) {
+                psi_dst[i] = make_float2(psi_src[i].y, pk[k]);
+            } else {
+                psi_dst[i] = make_float2(pk[k], pk[k]);
+                psi_other[i] = make_float2(pk[k], pk[k]);
+            }
         }
     }
 }
@@ -181,8 +201,9 @@ __device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off
 // blending.  All (x, y) and (u, v) arithmetic is on float pairs (one paired
 // FP32 instruction per two lanes of work).  h = dt * n / (2 pi): grid units
 // per unit velocity.
-template <int SCHEME>
-__device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap, int n, int log2n,
+template <int SCHEME, bool PSI>
+__device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
+                                             const float2* __restrict__ psi, int n, int log2n,
                                              float dt, float h, const SpeciesDev& sd, int p) {
     const int cur = sd.cur;
     uint32_t* __restrict__ cellp = sd.cell[cur];
@@ -197,7 +218,19 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap, in
     float2 np2;
     float2 vnew = make_float2(0.f, 0.f);
     const bool inertial = sd.inertial;
-    if (!inertial) {
+    if (PSI && !inertial) {
+        // Eq. 11: the streamfunction at (x +- dx, y) and (x, y +- dy), each
+        // interpolated in space and time, and centred differences; the
+        // neighbours sit one grid unit away, so they share the offsets.
+        const float inv2d = (float)n * (float)(1.0 / (4.0 * 3.14159265358979323846));
+        float2 k1 = psi_velocity<SCHEME, 0>(psi, n, ci, cj, o, inv2d);
+        float2 k2 = psi_velocity<SCHEME, 1>(psi, n, ci, cj, __ffma2_rn(h2, k1, o), inv2d);
+        float2 k3 = psi_velocity<SCHEME, 1>(psi, n, ci, cj, __ffma2_rn(h2, k2, o), inv2d);
+        float2 k4 = psi_velocity<SCHEME, 2>(psi, n, ci, cj, __ffma2_rn(h1, k3, o), inv2d);
+        float2 sum = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(k2, k3), k1), k4);
+        const float h6 = h * (1.0f / 6.0f);
+        np2 = __ffma2_rn(make_float2(h6, h6), sum, o);
+    } else if (!inertial) {
         // Eq. 12, stages at t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
         float2 k1 = st.template first_stage<0>(o);
         float2 k2 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, k1, o));

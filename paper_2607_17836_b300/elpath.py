@@ -41,7 +41,8 @@ class el_flow_desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("interp", ctypes.c_int32), ("nu", ctypes.c_double),
                 ("dt", ctypes.c_double), ("ab2_mode", ctypes.c_int32),
                 ("bspline_prefilter", ctypes.c_int32), ("max_species", ctypes.c_int32),
-                ("sort_every", ctypes.c_int32), ("max_particles", ctypes.c_int64)]
+                ("sort_every", ctypes.c_int32), ("max_particles", ctypes.c_int64),
+                ("tracer_velocity", ctypes.c_int32)]
 
 
 class el_tuning(ctypes.Structure):
@@ -131,10 +132,10 @@ def _host_f64(a, shape=None):
 
 
 def make_desc(n, nu, dt, interp=BILINEAR, ab2_mode=0, bspline_prefilter=True, max_species=0,
-              max_particles=0, sort_every=0) -> el_flow_desc:
+              max_particles=0, sort_every=0, tracer_velocity=0) -> el_flow_desc:
     return el_flow_desc(int(n), int(interp), float(nu), float(dt), int(ab2_mode),
                         1 if bspline_prefilter else 0, int(max_species), int(sort_every),
-                        int(max_particles))
+                        int(max_particles), int(tracer_velocity))
 
 
 def workspace_bytes(desc: el_flow_desc) -> int:
@@ -166,12 +167,12 @@ class Flow:
 
     def __init__(self, n, nu, dt, omega0, interp=BILINEAR, ab2_mode=0, bspline_prefilter=True,
                  max_species=0, max_particles=0, sort_every=0, stream=None, device=None,
-                 workspace=None):
+                 workspace=None, tracer_velocity=0):
         import torch
         lib = load()
         self._lib = lib
         self.desc = make_desc(n, nu, dt, interp, ab2_mode, bspline_prefilter, max_species,
-                              max_particles, sort_every)
+                              max_particles, sort_every, tracer_velocity)
         self.n = int(n)
         self.device = torch.device(device if device is not None else "cuda")
         nbytes = workspace_bytes(self.desc)

@@ -36,8 +36,9 @@ class OracleRun:
         self.sets = []
         f = self.flow.fields(("u", "v"))
         self.level = (f["u"], f["v"])
+        self.psi_level = self.flow.psi()
 
-    def add(self, scheme, st, xy, vxy=None):
+    def add(self, scheme, st, xy, vxy=None, psi=False):
         xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
         x, y = xy[:, 0].copy(), xy[:, 1].copy()
         if st > 0:
@@ -50,18 +51,29 @@ class OracleRun:
         else:
             vx = vy = None
         self.sets.append({"scheme": scheme, "st": float(st), "x": x, "y": y, "vx": vx, "vy": vy,
-                          "x0": x.copy(), "y0": y.copy()})
+                          "x0": x.copy(), "y0": y.copy(), "psi": bool(psi) and st == 0})
         return len(self.sets) - 1
 
     def step(self, nsteps):
         for _ in range(nsteps):
             un, vn = self.level
+            pn = self.psi_level
             self.flow.step(1)
             f = self.flow.fields(("u", "v"))
             un1, vn1 = f["u"], f["v"]
+            pn1 = self.flow.psi()
             cache = {}
             for s in self.sets:
                 sc = s["scheme"]
+                if s["psi"]:
+                    key = ("psi", sc)
+                    if key not in cache:
+                        pre = sc == oracle.BSPLINE and self.prefilter
+                        cache[key] = ((oracle.bspline_prefilter(pn) if pre else pn),
+                                      (oracle.bspline_prefilter(pn1) if pre else pn1))
+                    a, b = cache[key]
+                    oracle.tracers_rk4_psi(sc, self.flow.dt, a, b, s["x"], s["y"])
+                    continue
                 if sc not in cache:
                     cache[sc] = (oracle_stencil(un, vn, sc, self.prefilter),
                                  oracle_stencil(un1, vn1, sc, self.prefilter))
@@ -69,6 +81,7 @@ class OracleRun:
                 oracle.particles_rk4(sc, self.flow.dt, s["st"], a, b, c, d, s["x"], s["y"],
                                      s["vx"], s["vy"])
             self.level = (un1, vn1)
+            self.psi_level = pn1
 
     def positions(self, k):
         s = self.sets[k]
@@ -80,10 +93,11 @@ class OracleRun:
 
 
 def gpu_flow(n, nu, dt, omega0, interp=0, max_species=1, max_particles=0, sort_every=0,
-             ab2_mode=0, prefilter=True):
+             ab2_mode=0, prefilter=True, tracer_velocity=0):
     return elpath.Flow(n, nu, dt, omega0, interp=interp, ab2_mode=ab2_mode,
                        bspline_prefilter=prefilter, max_species=max_species,
-                       max_particles=max_particles, sort_every=sort_every)
+                       max_particles=max_particles, sort_every=sort_every,
+                       tracer_velocity=tracer_velocity)
 
 
 def decaying(n, seed=2, k0=10.0):

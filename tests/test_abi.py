@@ -48,9 +48,9 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(el_flow_desc), offsetof(el_flow_desc, nu),
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(el_flow_desc), offsetof(el_flow_desc, nu),
          offsetof(el_flow_desc, dt), offsetof(el_flow_desc, max_particles),
-         offsetof(el_flow_desc, sort_every));
+         offsetof(el_flow_desc, sort_every), offsetof(el_flow_desc, tracer_velocity));
   printf("%zu %zu %zu %zu %zu\\n", sizeof(el_stats), offsetof(el_stats, msd),
          offsetof(el_stats, cluster), offsetof(el_stats, np), offsetof(el_stats, finite));
   return 0;
@@ -63,7 +63,7 @@ int main(void) {{
     s = [int(x) for x in lines[1].split()]
     D, S = elpath.el_flow_desc, elpath.el_stats
     assert d == [ctypes.sizeof(D), D.nu.offset, D.dt.offset, D.max_particles.offset,
-                 D.sort_every.offset]
+                 D.sort_every.offset, D.tracer_velocity.offset]
     assert s == [ctypes.sizeof(S), S.msd.offset, S.cluster.offset, S.np.offset, S.finite.offset]
 
 

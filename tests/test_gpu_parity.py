@@ -275,3 +275,24 @@ def test_no_uninitialised_reads(scheme):
     np.testing.assert_array_equal(a[1], b[1])
     np.testing.assert_array_equal(a[2], b[2])
     assert a[3] == b[3]
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_streamfunction_tracers_parity(scheme):
+    # tracer_velocity = 1: tracers use Eq. 11 (streamfunction + centred
+    # differences), inertial particles the interpolated velocity.
+    n, nu, dt = 128, 1e-4, 5e-4
+    w0 = decaying(n, seed=18)
+    g = gpu_flow(n, nu, dt, w0, interp=scheme, max_species=2, max_particles=8000, sort_every=9,
+                 tracer_velocity=1)
+    o = OracleRun(n, nu, dt, w0)
+    xy = inputs.uniform_positions(4000, seed=19)
+    g.set_particles(0, xy, 0.0)
+    g.set_particles(1, xy, 1.0)
+    o.add(scheme, 0.0, xy, psi=True)
+    o.add(scheme, 1.0, xy)
+    g.step(200)
+    o.step(200)
+    for s in range(2):
+        pos, _ = g.particles(s, 4000)
+        assert np.max(np.abs(pos - o.positions(s))) < POS_ATOL, s

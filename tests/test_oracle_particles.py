@@ -145,3 +145,38 @@ def test_cluster_index_of_uniform_points_is_near_zero():
     # so Var/mean - 1 = P (B-1)/B - 1
     x = np.full(1000, 0.01)
     assert abs(oracle.cluster_index(x, x) - (1000 * 4095 / 4096 - 1)) < 1e-9
+
+
+@pytest.mark.parametrize("scheme,tol", [(oracle.CATMULL_ROM, 5e-5), (oracle.BSPLINE, 2e-6)])
+def test_streamfunction_velocity_is_the_centred_difference(scheme, tol):
+    # Eq. 11 on psi = sin x sin y: centred differences of width 2 dx give
+    # u = sin x cos y * sin(dx)/dx and v = -cos x sin y * sin(dx)/dx exactly,
+    # so the oracle must reproduce the sinc factor (1 - dx^2/6), not the
+    # analytic velocity: this pins the formula's axes, sign and width.
+    n = 64
+    X, Y = inputs.grid(n)
+    psi = np.sin(X) * np.sin(Y)
+    if scheme == oracle.BSPLINE:
+        psi = oracle.bspline_prefilter(psi)
+    xy = inputs.uniform_positions(500, seed=31)
+    u, v = oracle.psi_velocity(psi, scheme, xy[:, 0], xy[:, 1])
+    d = 2 * np.pi / n
+    sinc = np.sin(d) / d
+    np.testing.assert_allclose(u, np.sin(xy[:, 0]) * np.cos(xy[:, 1]) * sinc, atol=tol)
+    np.testing.assert_allclose(v, -np.cos(xy[:, 0]) * np.sin(xy[:, 1]) * sinc, atol=tol)
+    # ... and the sinc factor is resolved: the plain analytic velocity is off
+    assert np.max(np.abs(u - np.sin(xy[:, 0]) * np.cos(xy[:, 1]))) > 10 * tol
+
+
+def test_streamfunction_and_velocity_tracers_agree_short_time():
+    # Both tracer paths follow the same flow; they differ by O(dx^2).
+    wl = inputs.taylor_green_64()
+    a = oracle.Coupled(wl.n, wl.nu, wl.dt, wl.omega0(), scheme=oracle.BSPLINE)
+    b = oracle.Coupled(wl.n, wl.nu, wl.dt, wl.omega0(), scheme=oracle.BSPLINE, tracer_velocity=1)
+    xy = inputs.uniform_positions(256, seed=32)
+    a.add_species(xy, 0.0)
+    b.add_species(xy, 0.0)
+    a.step(100)
+    b.step(100)
+    d = np.hypot(a.species[0].x - b.species[0].x, a.species[0].y - b.species[0].y)
+    assert 1e-6 < d.max() < 1e-3   # paths differ, by O(dx^2) of the distance travelled
