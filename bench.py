@@ -134,6 +134,22 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over the ranks (x itself when world == 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -349,11 +365,8 @@ def run_ours(args, wl, scheme, world, rank, local):
     launches = flow.kernel_launches() - launches0
     chunk_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     step_ms = [t / c for t, c in zip(chunk_ms, chunks)]
-    total_ms = float(sum(chunk_ms))
+    total_ms = max_over_ranks(float(sum(chunk_ms)), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
 
     # Per-stage times (direct launches with events between the stages).
@@ -405,16 +418,11 @@ def run_ours(args, wl, scheme, world, rank, local):
     e2e_s = time.perf_counter() - t0
     h2d = sum(xy.nbytes for xy in xys)
     d2h = sum(s.count * 16 * (2 if s.st > 0 else 1) for s in wl.species)
-    e2e_value = wl.particles * args.steps / e2e_s
-
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_value = wl.particles * args.steps * world / float(t.item())
+    e2e_value = aggregate_rate(wl.particles * args.steps, world, max_over_ranks(e2e_s, world, dev))
 
     if rank != 0:
         return
-    value = wl.particles * args.steps * world / (total_ms * 1e-3)
+    value = aggregate_rate(wl.particles * args.steps, world, total_ms * 1e-3)
     srt = sorted(step_ms)
     p50 = srt[len(srt) // 2]
     p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
