@@ -6,6 +6,17 @@
 #include "common.cuh"
 #include "interp.cuh"
 
+#ifndef EL_STREAMING_STATE
+#define EL_STREAMING_STATE 1
+#endif
+#if EL_STREAMING_STATE
+#define EL_STATE_LD(ptr) __ldcs(ptr)
+#define EL_STATE_ST(ptr, v) __stcs(ptr, v)
+#else
+#define EL_STATE_LD(ptr) (*(ptr))
+#define EL_STATE_ST(ptr, v) (*(ptr) = (v))
+#endif
+
 namespace el {
 
 __device__ __forceinline__ int wavenumber_row(int j, int n) { return j < n / 2 ? j : j - n; }
@@ -208,9 +219,11 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
     const int cur = sd.cur;
     uint32_t* __restrict__ cellp = sd.cell[cur];
     float2* __restrict__ offp = sd.off[cur];
-    const uint32_t c = cellp[p];
+    // the particle state is streamed once per step: evict-first loads and
+    // stores keep the caches for the level pair the gathers re-read
+    const uint32_t c = EL_STATE_LD(cellp + p);
     const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
-    const float2 o = offp[p];
+    const float2 o = EL_STATE_LD(offp + p);
     Stencil<SCHEME> st;
     st.load(snap, n, ci, cj);
     const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
@@ -245,7 +258,7 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
         const float2 ist = make_float2(sd.inv_st, sd.inv_st);
         const float2 d2 = make_float2(0.5f * dt, 0.5f * dt), d1 = make_float2(dt, dt);
         float2* __restrict__ velp = sd.vel[cur];
-        const float2 v = velp[p];
+        const float2 v = EL_STATE_LD(velp + p);
         float2 u1 = st.template first_stage<0>(o);
         float2 a1 = __fmul2_rn(fsub2(u1, v), ist);
         float2 v2 = __ffma2_rn(d2, a1, v);
@@ -262,14 +275,14 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
         float2 sa = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(a2, a3), a1), a4);
         np2 = __ffma2_rn(make_float2(h6, h6), sx, o);
         vnew = __ffma2_rn(make_float2(d6, d6), sa, v);
-        velp[p] = vnew;
+        EL_STATE_ST(velp + p, vnew);
     }
     float ox, oy;
     int ni, nj, dix, diy;
     carry_axis(np2.x, ci, log2n, ox, ni, dix);
     carry_axis(np2.y, cj, log2n, oy, nj, diy);
-    cellp[p] = (uint32_t)ni | ((uint32_t)nj << 16);
-    offp[p] = make_float2(ox, oy);
+    EL_STATE_ST(cellp + p, (uint32_t)ni | ((uint32_t)nj << 16));
+    EL_STATE_ST(offp + p, make_float2(ox, oy));
     if (dix | diy) {  // crossed the periodic boundary: rare read-modify-write
         int2* imgp = sd.img[cur];
         int2 m = imgp[p];
