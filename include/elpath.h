@@ -231,6 +231,29 @@ el_status el_batch_destroy(el_batch* batch);
 el_status el_dispersion_noalloc(const double* d_xy, const double* d_xy0, int64_t np,
                                 double* d_out3, void* cuda_stream);
 
+/* Checkpoint and resume.  The coupled step (Algorithm 1) depends on a flow
+ * only through omega-hat, the AB2 history and N-hat of the current level
+ * (Sec. 3.1, Eqs. 9-10), the level pair holding the current velocity field
+ * (Sec. 3.2; with tracer_velocity = 1 also the streamfunction pair) and each
+ * particle's state and reference position; the state image is exactly that
+ * plus the step count, in host byte order, ending in a 64-bit FNV-1a
+ * checksum.  Loading an image into a flow created with the same n, interp,
+ * nu, dt, ab2_mode, bspline_prefilter and tracer_velocity and stepping on
+ * reproduces the uninterrupted run bit for bit.
+ *
+ * el_save_state: host_buf = NULL stores the image size in *bytes and returns
+ * EL_OK.  Otherwise *bytes is the buffer's size; a buffer that is too small
+ * gives EL_EINVAL with the needed size in *bytes; on success *bytes is the
+ * image size.  Synchronises the stream.
+ * el_load_state: replaces the flow's state by the image (bytes = its exact
+ * size).  EL_EINVAL, with the flow unchanged, for an image that is not one,
+ * is truncated or altered (checksum), was saved by a flow of another
+ * descriptor, or has more particles than the flow can hold; EL_ESTATE for a
+ * member of a batch.  The tuning settings stay the flow's own.  Synchronises
+ * the stream. */
+el_status el_save_state(el_flow* flow, void* host_buf, size_t* bytes);
+el_status el_load_state(el_flow* flow, const void* host_buf, size_t bytes);
+
 /* Destroy the flow (plans, graphs, host state).  The workspace is the
  * caller's to free afterwards. */
 el_status el_destroy_flow(el_flow* flow);

@@ -259,6 +259,13 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
     }
     sp.np = np;
     sp.st = st;
+    EL_TRY(particles_restore_table(f, s));
+    EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
+    return EL_OK;
+}
+
+el_status particles_restore_table(el_flow* f, int s) {
+    const Species& sp = f->sp[s];
     SpeciesDev& d = f->h_table[s];
     for (int k = 0; k < 2; k++) {
         d.cell[k] = sp.cell[k];
@@ -266,13 +273,11 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
         d.vel[k] = sp.vel[k];
         d.img[k] = sp.img[k];
     }
-    d.np = (int)np;
-    d.cur = cur;
-    d.inertial = st > 0.0 ? 1 : 0;
-    d.inv_st = st > 0.0 ? (float)(1.0 / st) : 0.0f;
-    EL_TRY(upload_table(f));
-    EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
-    return EL_OK;
+    d.np = (int)sp.np;
+    d.cur = sp.cur;
+    d.inertial = sp.st > 0.0 ? 1 : 0;
+    d.inv_st = sp.st > 0.0 ? (float)(1.0 / sp.st) : 0.0f;
+    return upload_table(f);
 }
 
 // K6 for every species of the flow in one launch, step number `step`

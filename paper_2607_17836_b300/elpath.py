@@ -27,7 +27,8 @@ SYMBOLS = ("el_workspace_bytes", "el_create_flow", "el_set_particles", "el_step_
            "el_kernel_launches", "el_batch_workspace_bytes", "el_batch_create", "el_batch_add",
            "el_batch_remove", "el_batch_step", "el_batch_autotune", "el_batch_size",
            "el_batch_kernel_launches", "el_batch_last_error", "el_batch_destroy",
-           "el_dispersion_noalloc", "el_destroy_flow", "el_last_error")
+           "el_dispersion_noalloc", "el_save_state", "el_load_state", "el_destroy_flow",
+           "el_last_error")
 NOALLOC_MAX_PARTICLES = 262144
 
 
@@ -109,12 +110,14 @@ def load(path: str = LIB_PATH):
         getattr(lib, name).restype = ctypes.c_int
     lib.el_dispersion_noalloc.argtypes = [V, V, I64, V, V]
     lib.el_dispersion_noalloc.restype = ctypes.c_int
+    lib.el_save_state.argtypes = [P, V, ctypes.POINTER(ctypes.c_size_t)]
+    lib.el_load_state.argtypes = [P, V, ctypes.c_size_t]
     lib.el_destroy_flow.argtypes = [P]
     lib.el_last_error.argtypes = [P]
     lib.el_last_error.restype = ctypes.c_char_p
     for name in ("el_create_flow", "el_set_particles", "el_step_coupled", "el_get_stats",
                  "el_get_particles", "el_get_field", "el_sample_velocity", "el_profile_step",
-                 "el_destroy_flow"):
+                 "el_save_state", "el_load_state", "el_destroy_flow"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -293,6 +296,19 @@ class Flow:
         self._check(self._lib.el_autotune(self._h, int(trial_steps), ctypes.byref(t)))
         return {"rk4_threads": t.rk4_threads, "sort_every": t.sort_every,
                 "sort_shift": t.sort_shift, "ms_per_step": t.ms_per_step}
+
+    def save_state(self) -> bytes:
+        """el_save_state: the flow's complete state at its current step."""
+        size = ctypes.c_size_t(0)
+        self._check(self._lib.el_save_state(self._h, None, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(size.value)
+        self._check(self._lib.el_save_state(self._h, buf, ctypes.byref(size)))
+        return buf.raw[:size.value]
+
+    def load_state(self, image: bytes):
+        """el_load_state: replace the flow's state by a saved image."""
+        image = bytes(image)
+        self._check(self._lib.el_load_state(self._h, ctypes.c_char_p(image), len(image)))
 
     def synchronize(self):
         self.stream.synchronize()
