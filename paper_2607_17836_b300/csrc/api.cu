@@ -1,7 +1,6 @@
 // The C ABI of include/elpath.h: argument checks, the workspace layout,
 // cuFFT plans, the captured step graph and the coupled step of Algorithm 1.
 #include "common.cuh"
-#include "fft.cuh"
 #include "tune.cuh"
 
 #include <cmath>
@@ -17,6 +16,8 @@ namespace el {
 
 void batch_member_changed(el_batch* b);
 
+void fluid_tables(const el_flow_desc& d, std::vector<float2>& ex, std::vector<float2>& ey,
+                  std::vector<float>& px, std::vector<float>& py);
 
 namespace {
 
@@ -58,52 +59,56 @@ size_t species_bytes(int64_t np) {
 
 // cuFFT work-area bytes for (n, planes), cached.
 std::mutex g_fft_mutex;
-std::map<int, size_t> g_fft_bytes;
+std::map<std::pair<int, int>, size_t> g_fft_bytes;
 
-// cuFFT plans of the set-up (R2C of the initial field) and of the field
-// readback (C2R of one plane); the time step does not use cuFFT.
-cufftResult make_plans(int n, cufftHandle* r2c, cufftHandle* c2r1, size_t* work) {
+cufftResult make_plans(int n, int planes, cufftHandle* c2r, cufftHandle* r2c, cufftHandle* c2r1,
+                       size_t* work) {
     int dims[2] = {n, n};
-    size_t w1 = 0, w2 = 0;
+    size_t w0 = 0, w1 = 0, w2 = 0;
     cufftResult r;
-    *r2c = *c2r1 = 0;
+    *c2r = *r2c = *c2r1 = 0;
+    if ((r = cufftCreate(c2r)) != CUFFT_SUCCESS) return r;
     if ((r = cufftCreate(r2c)) != CUFFT_SUCCESS) return r;
     if ((r = cufftCreate(c2r1)) != CUFFT_SUCCESS) return r;
+    cufftSetAutoAllocation(*c2r, 0);
     cufftSetAutoAllocation(*r2c, 0);
     cufftSetAutoAllocation(*c2r1, 0);
+    if ((r = cufftMakePlanMany(*c2r, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, planes, &w0)) !=
+        CUFFT_SUCCESS)
+        return r;
     if ((r = cufftMakePlanMany(*r2c, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, &w1)) !=
         CUFFT_SUCCESS)
         return r;
     if ((r = cufftMakePlanMany(*c2r1, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1, &w2)) !=
         CUFFT_SUCCESS)
         return r;
-    *work = std::max(w1, w2);
+    *work = std::max(w0, std::max(w1, w2));
     return CUFFT_SUCCESS;
 }
 
-void destroy_plans(cufftHandle a, cufftHandle b) {
+void destroy_plans(cufftHandle a, cufftHandle b, cufftHandle c) {
     if (a) cufftDestroy(a);
     if (b) cufftDestroy(b);
+    if (c) cufftDestroy(c);
 }
 
-bool fft_work_bytes(int n, size_t* out) {
+bool fft_work_bytes(int n, int planes, size_t* out) {
     std::lock_guard<std::mutex> g(g_fft_mutex);
-    auto it = g_fft_bytes.find(n);
+    auto key = std::make_pair(n, planes);
+    auto it = g_fft_bytes.find(key);
     if (it != g_fft_bytes.end()) {
         *out = it->second;
         return true;
     }
-    cufftHandle a, b;
+    cufftHandle a, b, c;
     size_t w = 0;
-    cufftResult r = make_plans(n, &a, &b, &w);
-    destroy_plans(a, b);
+    cufftResult r = make_plans(n, planes, &a, &b, &c, &w);
+    destroy_plans(a, b, c);
     if (r != CUFFT_SUCCESS) return false;
-    g_fft_bytes[n] = w;
+    g_fft_bytes[key] = w;
     *out = w;
     return true;
 }
-
-int pitch_of(int n) { return (n / 2 + 1 + 3) / 4 * 4; }
 
 // The workspace layout.  With base == nullptr only the size is computed.
 size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
@@ -114,13 +119,14 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         return base ? base + o : nullptr;
     };
     size_t n = (size_t)d.n, nh = n / 2 + 1, n2 = n * n, nm = n * nh;
-    size_t rows = n * (size_t)pitch_of(d.n);
     int planes = planes_of(d);
     char* what = take(nm * 8);
     char* what_lo = take(nm * 8);
     char* hist = take(nm * 8);
-    char* nrow = take(rows * 8);
-    char* planes_p = take((size_t)planes * rows * 8);
+    char* nhat = take(nm * 8);
+    char* spec = take((size_t)planes * nm * 8);
+    char* phys = take((size_t)planes * n2 * 4);
+    char* nl = take(n2 * 4);
     char* snap0 = take(n2 * 16);
     char* snap1 = take(n2 * 16);
     char* psi0 = d.tracer_velocity ? take(n2 * 8) : nullptr;
@@ -132,9 +138,6 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* ey = take(n * 8);
     char* px = take(nh * 4);
     char* py = take(n * 4);
-    char* tw_col = take(n * 8);
-    char* tw_row = take(n / 2 * 8);
-    char* wn = take(nh * 8);
     char* table = take(sizeof(SpeciesDev) * kMaxSpecies);
     char* red = take((size_t)kRedBlocks * 3 * 8);
     char* red_out = take(64 * 8);
@@ -149,8 +152,10 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->what = (float2*)what;
         f->what_lo = (float2*)what_lo;
         f->hist = (float2*)hist;
-        f->nrow = (float2*)nrow;
-        f->planes = (float2*)planes_p;
+        f->nhat = (float2*)nhat;
+        f->spec = (float2*)spec;
+        f->phys = (float*)phys;
+        f->nl = (float*)nl;
         f->snap[0] = (float4*)snap0;
         f->snap[1] = (float4*)snap1;
         f->psi[0] = (float2*)psi0;
@@ -162,9 +167,6 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->ey = (float2*)ey;
         f->pre_x = (float*)px;
         f->pre_y = (float*)py;
-        f->tw_col = (float2*)tw_col;
-        f->tw_row = (float2*)tw_row;
-        f->wn = (float2*)wn;
         f->table = (SpeciesDev*)table;
         f->red = (double*)red;
         f->red_out = (double*)red_out;
@@ -340,7 +342,7 @@ extern "C" {
 size_t el_workspace_bytes(const el_flow_desc* desc) {
     if (check_desc(desc)) return 0;
     size_t fft = 0;
-    if (!fft_work_bytes(desc->n, &fft)) return 0;
+    if (!fft_work_bytes(desc->n, planes_of(*desc), &fft)) return 0;
     return carve(*desc, fft, nullptr, nullptr);
 }
 
@@ -355,7 +357,7 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     for (size_t q = 0, nn = (size_t)desc->n * desc->n; q < nn; q++)
         if (!std::isfinite(omega0[q])) return fail(nullptr, EL_EINVAL, "omega0 has a non-finite value");
     size_t fft = 0;
-    if (!fft_work_bytes(desc->n, &fft))
+    if (!fft_work_bytes(desc->n, planes_of(*desc), &fft))
         return fail(nullptr, EL_ECUFFT, "cuFFT plan creation failed for n=%d", desc->n);
     size_t need = carve(*desc, fft, nullptr, nullptr);
     if (workspace_bytes < need)
@@ -374,8 +376,6 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     f->n2 = (size_t)f->n * f->n;
     f->nmodes = (size_t)f->n * f->nh;
     f->nplanes = planes_of(*desc);
-    f->pitch = pitch_of(desc->n);
-    f->log2tc = col_log2tc(desc->n);
     f->stencil_plane = (desc->interp == EL_BSPLINE && desc->bspline_prefilter) ? 4 : 0;
     f->psi_plane = desc->tracer_velocity ? f->nplanes - 1 : -1;
     f->ws = (char*)dev_workspace;
@@ -384,7 +384,7 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
 
     auto bail = [&](el_status s) {
         g_create_error = f->err;
-        destroy_plans(f->plan_r2c, f->plan_c2r1);
+        destroy_plans(f->plan_c2r, f->plan_r2c, f->plan_c2r1);
         if (f->side) cudaStreamDestroy(f->side);
         if (f->ev_fork) cudaEventDestroy(f->ev_fork);
         if (f->ev_join) cudaEventDestroy(f->ev_join);
@@ -401,12 +401,12 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
         }
     }
     size_t w = 0;
-    cufftResult r = make_plans(f->n, &f->plan_r2c, &f->plan_c2r1, &w);
+    cufftResult r = make_plans(f->n, f->nplanes, &f->plan_c2r, &f->plan_r2c, &f->plan_c2r1, &w);
     if (r != CUFFT_SUCCESS || w > fft) {
         fail(f, EL_ECUFFT, "cuFFT plan creation failed (%d)", (int)r);
         return bail(EL_ECUFFT);
     }
-    cufftHandle plans[2] = {f->plan_r2c, f->plan_c2r1};
+    cufftHandle plans[3] = {f->plan_c2r, f->plan_r2c, f->plan_c2r1};
     for (cufftHandle p : plans) {
         if (cufftSetWorkArea(p, f->fft_work) != CUFFT_SUCCESS || cufftSetStream(p, f->stream) != CUFFT_SUCCESS) {
             fail(f, EL_ECUFFT, "cuFFT work area / stream binding failed");
@@ -415,20 +415,14 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     }
     f->plans_made = true;
 
-    FluidTables tab;
-    fluid_tables(*desc, tab);
+    std::vector<float2> ex, ey;
+    std::vector<float> px, py;
+    fluid_tables(*desc, ex, ey, px, py);
     cudaError_t e = cudaSuccess;
-    auto up = [&](void* dst, const void* src, size_t bytes) {
-        if (e == cudaSuccess && bytes > 0)
-            e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, f->stream);
-    };
-    up(f->ex, tab.ex.data(), tab.ex.size() * 8);
-    up(f->ey, tab.ey.data(), tab.ey.size() * 8);
-    up(f->pre_x, tab.px.data(), tab.px.size() * 4);
-    up(f->pre_y, tab.py.data(), tab.py.size() * 4);
-    up(f->tw_col, tab.tw_col.data(), tab.tw_col.size() * 8);
-    up(f->tw_row, tab.tw_row.data(), tab.tw_row.size() * 8);
-    up(f->wn, tab.wn.data(), tab.wn.size() * 8);
+    e = e ? e : cudaMemcpyAsync(f->ex, ex.data(), ex.size() * 8, cudaMemcpyHostToDevice, f->stream);
+    e = e ? e : cudaMemcpyAsync(f->ey, ey.data(), ey.size() * 8, cudaMemcpyHostToDevice, f->stream);
+    e = e ? e : cudaMemcpyAsync(f->pre_x, px.data(), px.size() * 4, cudaMemcpyHostToDevice, f->stream);
+    e = e ? e : cudaMemcpyAsync(f->pre_y, py.data(), py.size() * 4, cudaMemcpyHostToDevice, f->stream);
     if (e != cudaSuccess) {
         fail(f, EL_ECUDA, "table upload: %s", cudaGetErrorString(e));
         return bail(EL_ECUDA);
@@ -632,7 +626,7 @@ el_status el_destroy_flow(el_flow* f) {
     if (f->batch) el_batch_remove(f->batch, f);
     cudaStreamSynchronize(f->stream);
     drop_graphs(f);
-    destroy_plans(f->plan_r2c, f->plan_c2r1);
+    destroy_plans(f->plan_c2r, f->plan_r2c, f->plan_c2r1);
     if (f->side) cudaStreamDestroy(f->side);
     if (f->ev_fork) cudaEventDestroy(f->ev_fork);
     if (f->ev_join) cudaEventDestroy(f->ev_join);

@@ -1,22 +1,22 @@
 // Batched engine: many independent simulations (flows of any grid size,
 // species mix, scheme and step count) advanced together.  One coupled step of
-// the batch is one captured CUDA graph of persistent kernels, each over the
-// work of every member:
+// the batch is one captured CUDA graph:
 //
-//   k_batch_column   column pass of every member's tiles   N-hat, AB2, planes
-//   k_batch_row      row pass of every member's rows       N, level pair, x-FFT of N
-//   k_batch_rk4<S>   RK4 particle step of every member's species, one launch
-//                    per interpolation scheme present
-//   k_batch_advance  per-member step counters
+//   k_batch_spectral  (persistent, every member's modes)   AB2 + velocity planes
+//   cuFFT C2R per member, on forked branches (they run concurrently)
+//   k_batch_nonlinear (persistent, every member's nodes)   nonlinear term + snapshot
+//   cuFFT R2C per member, on forked branches
+//   k_batch_rk4<S>    (persistent, every member's species) RK4 particle step,
+//                     one launch per interpolation scheme present
+//   k_batch_advance                                        per-member step counters
 //
-// The per-element arithmetic is the single-flow kernels' (fft.cuh,
-// stages.cuh), so a member's results do not depend on what else is in the
-// batch.  Each member keeps its own step counter on the device (members join
-// and leave at any step), so the same graph serves every step until the
-// membership changes.  Re-binning runs per member, outside the graph, when it
-// is due.
+// The per-element arithmetic is the single-flow kernels' (stages.cuh), so a
+// member's results do not depend on what else is in the batch.  Each member
+// keeps its own step counter on the device (members join and leave at any
+// step), so the same graph serves every step until the membership changes.
+// Re-binning runs per member, outside the graph, when it is due.
 #include "common.cuh"
-#include "fft.cuh"
+#include "stages.cuh"
 #include "tune.cuh"
 
 #include <algorithm>
@@ -28,30 +28,33 @@ namespace el {
 
 // Fluid and particle parameters of one member, device-resident.
 struct MemberDev {
-    ColArgs col;            // column pass
-    RowArgs row;            // row pass (level pairs chosen from `step`)
+    SpecArgs spec;          // arrays and constants of k_spectral (first from `step`)
+    const float4* phys4;
+    float4* nl4;
     float4* snap[2];        // level pairs: snap[k % 2] = levels (k, k+1)
     float2* psi[2];         // streamfunction level pairs, or nullptr
-    int psi_plane, n, log2n, scheme;
+    unsigned long long n4;  // n^2 / 4
+    int stencil_plane, psi_plane, n, log2n, scheme;
     float dt, h;
     long long step;
 };
 
-// The passes are compiled per remainder radix (log2 of the transform length
-// mod 4), so the fluid stage is one launch per pass and remainder present;
-// each launch's task list gives the other members zero tasks.
 struct BatchArgs {
     MemberDev* members;
-    const int* col_begin;             // task prefix sums, 4 x (nmembers + 1), one row per remainder
-    const int* row_begin;
+    const int* spec_begin;            // task prefix sums, nmembers + 1
+    const int* nl_begin;
     const int* rk_begin;              // nentries + 1
     const int* rk_member;             // member of each (member, species) entry
     const SpeciesDev* const* rk_sp;   // that member's device species descriptor
     int nmembers, nentries;
-    int col_tasks[4], row_tasks[4], rk_tasks;
+    int spec_tasks, nl_tasks, rk_tasks;
 };
 
 namespace {
+
+constexpr int kBSpecThreads = 128;
+constexpr int kBNlThreads = 256;
+constexpr int kSideStreams = 4;
 
 // Largest k in [0, count) with begin[k] <= t (begin ascending, begin[0] = 0).
 __device__ __forceinline__ int owner_of(const int* __restrict__ begin, int count, int t) {
@@ -63,33 +66,38 @@ __device__ __forceinline__ int owner_of(const int* __restrict__ begin, int count
     return lo;
 }
 
-// One block per task (a column tile or a row of one member).  Block size and
-// shared memory are the largest any member needs; the passes loop over their
-// elements, so a larger block only leaves threads idle.
-template <int REM>
-__global__ void __launch_bounds__(256) k_batch_column(const __grid_constant__ BatchArgs b) {
-    extern __shared__ float2 sm[];
-    const int* begin = b.col_begin + REM * (b.nmembers + 1);
-    const int t = blockIdx.x;
-    const int m = owner_of(begin, b.nmembers, t);
-    const MemberDev& md = b.members[m];
-    column_tile<REM>(md.col, md.step == 0, 1, t - begin[m], sm);
+__host__ __device__ __forceinline__ int spec_chunks(int n) {
+    int c = (n / 2) / kBSpecThreads;
+    return c < 1 ? 1 : c;
 }
 
-template <int REM>
-__global__ void __launch_bounds__(512) k_batch_row(const __grid_constant__ BatchArgs b) {
-    extern __shared__ float2 sm[];
-    const int* begin = b.row_begin + REM * (b.nmembers + 1);
-    const int t = blockIdx.x;
-    const int m = owner_of(begin, b.nmembers, t);
-    const MemberDev& md = b.members[m];
-    const long long m1 = md.step + 1;  // the level this step produces
-    RowLevel lv{};
-    lv.snap_dst = md.snap[(m1 + 1) % 2];
-    lv.snap_src = md.snap[m1 % 2];
-    lv.psi_dst = md.psi[(m1 + 1) % 2];
-    lv.psi_src = md.psi[m1 % 2];
-    row_pass<REM>(md.row, lv, t - begin[m], sm);
+__global__ void __launch_bounds__(kBSpecThreads) k_batch_spectral(const __grid_constant__ BatchArgs b) {
+    for (int t = blockIdx.x; t < b.spec_tasks; t += gridDim.x) {
+        const int m = owner_of(b.spec_begin, b.nmembers, t);
+        const MemberDev& md = b.members[m];
+        const int local = t - b.spec_begin[m];
+        const int chunks = spec_chunks(md.n);
+        const int j = local / chunks, i = (local - j * chunks) * kBSpecThreads + threadIdx.x;
+        SpecArgs a = md.spec;
+        a.first = md.step == 0;
+        if (i < md.n / 2) {
+            spectral_mode<true>(a, i, j);
+            if (i == 0) spectral_mode<true>(a, md.n / 2, j);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_constant__ BatchArgs b) {
+    for (int t = blockIdx.x; t < b.nl_tasks; t += gridDim.x) {
+        const int m = owner_of(b.nl_begin, b.nmembers, t);
+        const MemberDev& md = b.members[m];
+        const size_t q = (size_t)(t - b.nl_begin[m]) * kBNlThreads + threadIdx.x;
+        const long long lv = md.step + 1;  // the level this step produces
+        if (q < md.n4)
+            nonlinear_quad(md.phys4, md.nl4, md.snap[lv % 2], md.snap[(lv + 1) % 2], nullptr,
+                           md.n4, q, md.stencil_plane, md.psi_plane, md.psi[lv % 2],
+                           md.psi[(lv + 1) % 2], nullptr);
+    }
 }
 
 // One kernel per interpolation scheme (each with its own register budget);
@@ -116,11 +124,6 @@ __global__ void k_batch_advance(MemberDev* members, int nmembers) {
     for (int m = threadIdx.x; m < nmembers; m += blockDim.x) members[m].step += 1;
 }
 
-using BatchKernel = void (*)(BatchArgs);
-const BatchKernel kBatchColumn[4] = {k_batch_column<0>, k_batch_column<1>, k_batch_column<2>,
-                                     k_batch_column<3>};
-const BatchKernel kBatchRow[4] = {k_batch_row<0>, k_batch_row<1>, k_batch_row<2>, k_batch_row<3>};
-
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -135,23 +138,23 @@ struct el_batch {
     std::vector<el_flow*> members;
     // device tables (in the caller's workspace)
     MemberDev* d_members = nullptr;
-    int* d_col_begin = nullptr;
-    int* d_row_begin = nullptr;
+    int* d_spec_begin = nullptr;
+    int* d_nl_begin = nullptr;
     int* d_rk_begin = nullptr;
     int* d_rk_member = nullptr;
     const SpeciesDev** d_rk_sp = nullptr;
     // host copies (kept alive while their upload may be pending)
     std::vector<MemberDev> h_members;
-    std::vector<int> h_col_begin, h_row_begin, h_rk_begin, h_rk_member;  // 4 x (M + 1) for the passes
+    std::vector<int> h_spec_begin, h_nl_begin, h_rk_begin, h_rk_member;
     std::vector<const SpeciesDev*> h_rk_sp;
     BatchArgs args{};
-    int grid_col[4] = {}, grid_row[4] = {}, grid_rk[3] = {0, 0, 0};
-    int col_block = 32, row_block = 32;
-    size_t col_smem = 0, row_smem = 0;
+    int grid_spec = 0, grid_nl = 0, grid_rk[3] = {0, 0, 0};
     bool scheme_used[3] = {false, false, false};
     bool tables_valid = false;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_kernels = 0;
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
     int sms = 0;
     int64_t launches = 0;
     std::string err;
@@ -178,19 +181,42 @@ el_status bfail(el_batch* b, el_status s, const char* fmt, ...) {
 
 size_t table_bytes(int max_members) {
     size_t m = (size_t)max_members, e = m * kMaxSpecies;
-    return align_up(m * sizeof(MemberDev)) + 2 * align_up(4 * (m + 1) * sizeof(int)) +
+    return align_up(m * sizeof(MemberDev)) + 2 * align_up((m + 1) * sizeof(int)) +
            2 * align_up((e + 1) * sizeof(int)) + align_up(e * sizeof(void*));
 }
 
 MemberDev member_of(el_flow* f) {
     MemberDev md{};
-    md.col = column_args(f);
-    md.row = row_args(f);
+    SpecArgs& a = md.spec;
+    a.what = f->what;
+    a.what_lo = f->what_lo;
+    a.hist = f->hist;
+    a.nhat = f->nhat;
+    a.spec = f->spec;
+    a.ex = f->ex;
+    a.ey = f->ey;
+    a.pre_x = f->pre_x;
+    a.pre_y = f->pre_y;
+    a.n = f->n;
+    a.nh = f->nh;
+    a.nplanes = f->nplanes;
+    a.spline = f->stencil_plane != 0;
+    a.psi_plane = f->psi_plane;
+    a.mode = f->d.ab2_mode;
+    a.first = 0;
+    a.nmodes = f->nmodes;
+    a.scale = 1.0f / (float)f->n2;
+    a.dt = (float)f->d.dt;
+    a.nu = (float)f->d.nu;
+    md.phys4 = reinterpret_cast<const float4*>(f->phys);
+    md.nl4 = reinterpret_cast<float4*>(f->nl);
     for (int k = 0; k < 2; k++) {
         md.snap[k] = f->snap[k];
         md.psi[k] = f->psi[k];
     }
     md.psi_plane = f->psi_plane;
+    md.n4 = f->n2 / 4;
+    md.stencil_plane = f->stencil_plane;
     md.n = f->n;
     md.log2n = f->log2n;
     md.scheme = f->d.interp;
@@ -204,8 +230,8 @@ MemberDev member_of(el_flow* f) {
 el_status rebuild_tables(el_batch* b) {
     const int M = (int)b->members.size();
     b->h_members.clear();
-    b->h_col_begin.assign(4 * (size_t)(M + 1), 0);
-    b->h_row_begin.assign(4 * (size_t)(M + 1), 0);
+    b->h_spec_begin.assign(1, 0);
+    b->h_nl_begin.assign(1, 0);
     b->h_rk_begin.assign(1, 0);
     b->h_rk_member.clear();
     b->h_rk_sp.clear();
@@ -214,12 +240,9 @@ el_status rebuild_tables(el_batch* b) {
         el_flow* f = b->members[m];
         rk_threads = f->rk4_threads;  // one block size for the whole batch
         b->h_members.push_back(member_of(f));
-        for (int r = 0; r < 4; r++) {
-            int* cb = &b->h_col_begin[(size_t)r * (M + 1)];
-            int* rb = &b->h_row_begin[(size_t)r * (M + 1)];
-            cb[m + 1] = cb[m] + ((f->log2n & 3) == r ? col_tiles(f->n, f->log2tc) : 0);
-            rb[m + 1] = rb[m] + (((f->log2n - 1) & 3) == r ? f->n : 0);
-        }
+        b->h_spec_begin.push_back(b->h_spec_begin.back() + f->n * spec_chunks(f->n));
+        b->h_nl_begin.push_back(b->h_nl_begin.back() +
+                                (int)((f->n2 / 4 + kBNlThreads - 1) / kBNlThreads));
     }
     for (int m = 0; m < M; m++) {
         el_flow* f = b->members[m];
@@ -235,24 +258,22 @@ el_status rebuild_tables(el_batch* b) {
     }
     BatchArgs& a = b->args;
     a.members = b->d_members;
-    a.col_begin = b->d_col_begin;
-    a.row_begin = b->d_row_begin;
+    a.spec_begin = b->d_spec_begin;
+    a.nl_begin = b->d_nl_begin;
     a.rk_begin = b->d_rk_begin;
     a.rk_member = b->d_rk_member;
     a.rk_sp = b->d_rk_sp;
     a.nmembers = M;
     a.nentries = (int)b->h_rk_member.size();
-    for (int r = 0; r < 4; r++) {
-        a.col_tasks[r] = b->h_col_begin[(size_t)r * (M + 1) + M];
-        a.row_tasks[r] = b->h_row_begin[(size_t)r * (M + 1) + M];
-    }
+    a.spec_tasks = b->h_spec_begin.back();
+    a.nl_tasks = b->h_nl_begin.back();
     a.rk_tasks = b->h_rk_begin.back();
     if (M > 0) {
         BT_CUDA(b, cudaMemcpyAsync(b->d_members, b->h_members.data(), sizeof(MemberDev) * M,
                                    cudaMemcpyHostToDevice, b->stream));
-        BT_CUDA(b, cudaMemcpyAsync(b->d_col_begin, b->h_col_begin.data(), sizeof(int) * 4 * (M + 1),
+        BT_CUDA(b, cudaMemcpyAsync(b->d_spec_begin, b->h_spec_begin.data(), sizeof(int) * (M + 1),
                                    cudaMemcpyHostToDevice, b->stream));
-        BT_CUDA(b, cudaMemcpyAsync(b->d_row_begin, b->h_row_begin.data(), sizeof(int) * 4 * (M + 1),
+        BT_CUDA(b, cudaMemcpyAsync(b->d_nl_begin, b->h_nl_begin.data(), sizeof(int) * (M + 1),
                                    cudaMemcpyHostToDevice, b->stream));
     }
     if (a.nentries > 0) {
@@ -265,22 +286,10 @@ el_status rebuild_tables(el_batch* b) {
     }
     // persistent grids: as many blocks as fit on the GPU at once (capped by the work)
     int occ = 0;
-    b->col_block = b->row_block = 32;
-    b->col_smem = b->row_smem = 0;
-    for (el_flow* f : b->members) {
-        b->col_block = std::max(b->col_block, col_threads(f->n, f->log2tc));
-        b->row_block = std::max(b->row_block, row_threads(f->n, f->nplanes));
-        b->col_smem = std::max(b->col_smem, col_smem_bytes(f->log2n, f->log2tc));
-        b->row_smem = std::max(b->row_smem, row_smem_bytes(f->log2n, f->nplanes));
-    }
-    for (int r = 0; r < 4; r++) {
-        BT_CUDA(b, cudaFuncSetAttribute(kBatchColumn[r], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)max_col_smem_bytes()));
-        BT_CUDA(b, cudaFuncSetAttribute(kBatchRow[r], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)max_row_smem_bytes()));
-        b->grid_col[r] = a.col_tasks[r];
-        b->grid_row[r] = a.row_tasks[r];
-    }
+    BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_spectral, kBSpecThreads, 0));
+    b->grid_spec = std::max(1, std::min(a.spec_tasks, occ * b->sms));
+    BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_nonlinear, kBNlThreads, 0));
+    b->grid_nl = std::max(1, std::min(a.nl_tasks, occ * b->sms));
     void (*rk_kernels[3])(BatchArgs) = {k_batch_rk4<0>, k_batch_rk4<1>, k_batch_rk4<2>};
     for (int sc = 0; sc < 3; sc++) {
         b->scheme_used[sc] = false;
@@ -292,18 +301,34 @@ el_status rebuild_tables(el_batch* b) {
     return EL_OK;
 }
 
+// cuFFT of every member on forked branches of the capture.
+el_status fork_ffts(el_batch* b, bool c2r) {
+    BT_CUDA(b, cudaEventRecord(b->fork_ev, b->stream));
+    for (int k = 0; k < kSideStreams; k++) BT_CUDA(b, cudaStreamWaitEvent(b->side[k], b->fork_ev, 0));
+    for (size_t m = 0; m < b->members.size(); m++) {
+        el_flow* f = b->members[m];
+        cudaStream_t s = b->side[m % kSideStreams];
+        cufftHandle plan = c2r ? f->plan_c2r : f->plan_r2c;
+        if (cufftSetStream(plan, s) != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cufftSetStream");
+        cufftResult r = c2r ? cufftExecC2R(plan, reinterpret_cast<cufftComplex*>(f->spec), f->phys)
+                            : cufftExecR2C(plan, f->nl, reinterpret_cast<cufftComplex*>(f->nhat));
+        if (r != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cuFFT exec failed (%d)", (int)r);
+    }
+    for (int k = 0; k < kSideStreams; k++) {
+        BT_CUDA(b, cudaEventRecord(b->join_ev[k], b->side[k]));
+        BT_CUDA(b, cudaStreamWaitEvent(b->stream, b->join_ev[k], 0));
+    }
+    return EL_OK;
+}
+
 el_status capture_body(el_batch* b) {
     const BatchArgs& a = b->args;
-    for (int r = 0; r < 4; r++) {
-        if (a.col_tasks[r] == 0) continue;
-        kBatchColumn[r]<<<b->grid_col[r], b->col_block, b->col_smem, b->stream>>>(a);
-        b->launches++;
-    }
-    for (int r = 0; r < 4; r++) {
-        if (a.row_tasks[r] == 0) continue;
-        kBatchRow[r]<<<b->grid_row[r], b->row_block, b->row_smem, b->stream>>>(a);
-        b->launches++;
-    }
+    k_batch_spectral<<<b->grid_spec, kBSpecThreads, 0, b->stream>>>(a);
+    b->launches++;
+    EL_TRY(fork_ffts(b, true));
+    k_batch_nonlinear<<<b->grid_nl, kBNlThreads, 0, b->stream>>>(a);
+    b->launches++;
+    EL_TRY(fork_ffts(b, false));
     if (a.rk_tasks > 0) {
         int threads = b->members.empty() ? 256 : b->members[0]->rk4_threads;
         if (b->scheme_used[0]) k_batch_rk4<0><<<b->grid_rk[0], threads, 0, b->stream>>>(a);
@@ -327,6 +352,10 @@ el_status build_batch_graph(el_batch* b) {
     BT_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     el_status s = capture_body(b);
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    for (el_flow* f : b->members) {  // plans back on the batch stream
+        cufftSetStream(f->plan_c2r, b->stream);
+        cufftSetStream(f->plan_r2c, b->stream);
+    }
     if (s != EL_OK) {
         if (g) cudaGraphDestroy(g);
         return s;
@@ -382,14 +411,19 @@ el_status el_batch_create(int32_t max_members, void* dev_workspace, size_t bytes
     size_t m = (size_t)max_members, e = m * kMaxSpecies, off = 0;
     auto take = [&](size_t n) { char* r = p + off; off += align_up(n); return r; };
     b->d_members = (MemberDev*)take(m * sizeof(MemberDev));
-    b->d_col_begin = (int*)take(4 * (m + 1) * sizeof(int));
-    b->d_row_begin = (int*)take(4 * (m + 1) * sizeof(int));
+    b->d_spec_begin = (int*)take((m + 1) * sizeof(int));
+    b->d_nl_begin = (int*)take((m + 1) * sizeof(int));
     b->d_rk_begin = (int*)take((e + 1) * sizeof(int));
     b->d_rk_member = (int*)take((e + 1) * sizeof(int));
     b->d_rk_sp = (const SpeciesDev**)take(e * sizeof(void*));
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int k = 0; k < kSideStreams && err == cudaSuccess; k++)
+        err = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    for (int k = 0; k < kSideStreams && err == cudaSuccess; k++)
+        err = cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming);
     if (err != cudaSuccess) {
         el_batch_destroy(b);
         return fail(nullptr, EL_ECUDA, "batch create: %s", cudaGetErrorString(err));
@@ -410,6 +444,7 @@ el_status el_batch_add(el_batch* b, el_flow* f) {
         f->rk4_threads = b->members[0]->rk4_threads;
     f->own_stream = f->stream;
     f->stream = b->stream;
+    cufftSetStream(f->plan_c2r, b->stream);
     cufftSetStream(f->plan_r2c, b->stream);
     cufftSetStream(f->plan_c2r1, b->stream);
     f->batch = b;
@@ -425,6 +460,7 @@ el_status el_batch_remove(el_batch* b, el_flow* f) {
     BT_CUDA(b, cudaStreamSynchronize(b->stream));
     b->members.erase(it);
     f->stream = f->own_stream;
+    cufftSetStream(f->plan_c2r, f->stream);
     cufftSetStream(f->plan_r2c, f->stream);
     cufftSetStream(f->plan_c2r1, f->stream);
     f->batch = nullptr;
@@ -472,6 +508,11 @@ el_status el_batch_destroy(el_batch* b) {
     if (b->stream || !b->members.empty()) cudaStreamSynchronize(b->stream);
     while (!b->members.empty()) el_batch_remove(b, b->members.back());
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (int k = 0; k < kSideStreams; k++) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     delete b;
     return EL_OK;
 }

@@ -1,8 +1,8 @@
 // Checkpoint and resume of one flow: el_save_state / el_load_state.
 //
 // A coupled step (Algorithm 1) depends on the flow only through
-//   - omega-hat (high and low parts), the AB2 history and the nonlinear
-//     term of the current level n, transformed along x (Sec. 3.1, Eqs. 8-10),
+//   - omega-hat (high and low parts), the AB2 history and N-hat of the
+//     current level n (Sec. 3.1, Eqs. 8-10),
 //   - the level pair holding level n (the fluid step of n reads level n from
 //     it and writes the pair (n, n+1) the particle step blends, Sec. 3.2),
 //     and the streamfunction pair when tracers use Eq. 11,
@@ -14,7 +14,7 @@
 // enter no result).
 //
 // Image layout (host byte order, every section a multiple of 8 bytes):
-//   CkptHeader | omega-hat hi | lo | history | x-transformed N | level pair |
+//   CkptHeader | omega-hat hi | lo | history | N-hat | level pair |
 //   [streamfunction pair] | per non-empty species: cell, offset, [velocity],
 //   image, id, x0 | FNV-1a 64-bit checksum of everything before it.
 #include "common.cuh"
@@ -65,7 +65,7 @@ std::vector<Section> sections(el_flow* f, const int64_t* np, const double* st, i
     s.push_back({f->what, nm});
     s.push_back({f->what_lo, nm});
     s.push_back({f->hist, nm});
-    s.push_back({f->nrow, (size_t)f->n * f->pitch * sizeof(float2)});
+    s.push_back({f->nhat, nm});
     const int pair = (int)((step + 1) % 2);  // pair (n-1, n): level n in its second half
     s.push_back({f->snap[pair], f->n2 * sizeof(float4)});
     if (f->psi_plane >= 0) s.push_back({f->psi[pair], f->n2 * sizeof(float2)});
@@ -187,6 +187,7 @@ el_status el_load_state(el_flow* f, const void* host_buf, size_t bytes) {
         at += pad8(x.bytes);
     }
     for (int k = 0; k < f->d.max_species; k++) EL_TRY(particles_restore_table(f, k));
+    EL_TRY(fluid_refresh_planes(f));
     drop_graphs(f);
     EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
     return EL_OK;

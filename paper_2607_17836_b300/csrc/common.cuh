@@ -8,7 +8,6 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
-#include <vector>
 
 #include "../../include/elpath.h"
 
@@ -71,25 +70,22 @@ struct el_flow {
     size_t ws_bytes = 0;
 
     // fluid state (device)
-    int pitch = 0;            // row pitch of the row-space arrays (n/2 + 1 rounded up to 4)
-    int log2tc = 2;           // columns per column-pass tile: 4, 2 or 1
-    float2* what = nullptr;   // omega-hat, column-major [kx][j], (n/2+1) x n
+    float2* what = nullptr;   // omega-hat, half spectrum [ky][kx], n x (n/2+1)
     float2* what_lo = nullptr;  // low part of omega-hat (compensated storage)
     float2* hist = nullptr;   // AB2 history
-    float2* nrow = nullptr;   // nonlinear term of the latest level transformed along x, [y][pitch]
-    float2* planes = nullptr; // nplanes row-space planes [p][y][pitch] (column-pass output)
+    float2* nhat = nullptr;   // nonlinear term of the latest level
+    float2* spec = nullptr;   // nplanes half spectra (C2R input)
+    float* phys = nullptr;    // nplanes physical planes (C2R output)
+    float* nl = nullptr;      // physical nonlinear term (R2C input)
     float4* snap[2] = {nullptr, nullptr};  // level pairs: snap[k % 2] = levels (k, k+1) per node
     float2* psi[2] = {nullptr, nullptr};   // streamfunction level pairs (tracer_velocity = 1)
-    float2* aux_spec = nullptr;  // row-major half spectrum (set-up and field readback)
-    float* aux_phys = nullptr;   // n^2 floats (set-up and field readback)
+    float2* aux_spec = nullptr;
+    float* aux_phys = nullptr;
     double* stage64 = nullptr;  // n^2 doubles: host <-> device field staging
     float2* ex = nullptr;     // exp(-nu kx^2 dt) as (hi, lo) floats, kx = 0..n/2
     float2* ey = nullptr;     // exp(-nu ky^2 dt) as (hi, lo) floats, row index 0..n-1
     float* pre_x = nullptr;   // spline prefilter 3/(2 + cos(k dx)) per kx
     float* pre_y = nullptr;   // ... per row index
-    float2* tw_col = nullptr; // FFT twiddles, length-n transforms
-    float2* tw_row = nullptr; // FFT twiddles, length-n/2 transforms
-    float2* wn = nullptr;     // exp(-2 pi i k / n), k = 0..n/2
     el::SpeciesDev* table = nullptr;  // device copy of h_table
     el::SpeciesDev h_table[el::kMaxSpecies] = {};
     double* red = nullptr;        // reduction partials
@@ -101,7 +97,7 @@ struct el_flow {
     char* pool = nullptr;         // particle pool
     size_t pool_bytes = 0, pool_used = 0;
 
-    cufftHandle plan_r2c = 0, plan_c2r1 = 0;  // set-up and field readback only
+    cufftHandle plan_c2r = 0, plan_r2c = 0, plan_c2r1 = 0;
     bool plans_made = false;
 
     el::Species sp[el::kMaxSpecies];
@@ -158,16 +154,10 @@ el_status fail(el_flow* f, el_status s, const char* fmt, ...);
     } while (0)
 
 // ---- fluid (fluid.cu) -------------------------------------------------------
-// Host-computed FP64 tables of a flow (uploaded into its workspace).
-struct FluidTables {
-    std::vector<float2> ex, ey, tw_col, tw_row, wn;
-    std::vector<float> px, py;
-};
-void fluid_tables(const el_flow_desc& d, FluidTables& t);
 el_status fluid_init(el_flow* f, const double* omega0_host);
-el_status fluid_step(el_flow* f, int64_t step);   // column pass + row pass
-el_status fluid_kernel_setup(el_flow* f);         // shared-memory limits of the passes
+el_status fluid_step(el_flow* f, int64_t step);   // K5+K1, C2R, K3, R2C
 el_status fluid_diagnostics(el_flow* f);          // E, Z, P -> red_out[0..2]
+el_status fluid_refresh_planes(el_flow* f);       // physical planes of the current level
 el_status fluid_get_field(el_flow* f, int which, double* host_nn);
 
 // ---- particles (particles.cu) ---------------------------------------------------

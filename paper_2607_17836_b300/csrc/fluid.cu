@@ -1,75 +1,63 @@
-// Pseudospectral vorticity solver (Sec. 3.1).  One step is two launches of
-// the fused passes in fft.cuh:
+// Pseudospectral vorticity solver (Sec. 3.1): the pointwise kernels around
+// cuFFT's transforms.  Half spectrum [ky][kx], kx = 0..n/2, ky = j for
+// j < n/2 and j - n otherwise; physical arrays [j][i].  One step:
 //
-//   k_column : forward FFT along y of the x-transformed N -> N-hat (Eq. 8),
-//              2/3 rule + AB2 update of omega-hat (Eqs. 9, 10), the velocity,
-//              gradient, spline and streamfunction planes (Eqs. 4-6) and
-//              their inverse FFT along y
-//   k_row    : inverse real FFT along x of the planes, N = u wx + v wy
-//              (Eq. 7), the level pair the particle step reads, forward real
-//              FFT along x of N
+//   K5+K1 k_spectral<true> : 2/3 rule + AB2 update of omega-hat (Eqs. 9, 10),
+//                            then from the new omega-hat: u-hat, v-hat
+//                            (Eqs. 5, 6), i kx omega-hat, i ky omega-hat
+//                            (Eq. 4), scaled by 1/n^2 (the inverse
+//                            normalisation of Sec. 3.1), and for the B-spline
+//                            scheme the prefiltered spline coefficients
+//   cuFFT C2R (batched)    : the planes to physical space
+//   K3 k_nonlinear         : N = u d(omega)/dx + v d(omega)/dy (Eq. 7), and the
+//                            level pair (n, n+1) the particle step reads
+//   cuFFT R2C              : N-hat (Eq. 8)
 //
-// omega-hat, its low part and the AB2 history are stored column-major,
-// [kx][j] with kx = 0..n/2 and ky = j for j < n/2, j - n otherwise, so the
-// column pass reads and writes them in whole columns.  The planes and the
-// x-transformed N live in row space, [y][kx] with a row pitch that is a
-// multiple of 4 (one 32-byte sector per row of a 4-column tile).
-//
-// cuFFT serves only the set-up (the initial field into Fourier space) and
-// the on-demand readback of physical fields (el_get_field).
+// Modes are addressed by a 2-D grid (blockIdx.y = row j), so no thread
+// divides by n/2 + 1.
 #include "common.cuh"
-#include "fft.cuh"
+#include "stages.cuh"
 
-#include <algorithm>
 #include <cmath>
 #include <vector>
 
 namespace el {
 namespace {
 
-constexpr int kProjThreads = 128;
+constexpr int kSpecThreads = 128;
 
-template <int REM>
-__global__ void __launch_bounds__(256) k_column(const __grid_constant__ ColArgs a, int first,
-                                                int advance) {
-    extern __shared__ float2 sm[];
-    column_tile<REM>(a, first, advance, blockIdx.x, sm);
+// Threads cover kx = 0..n/2-1 of row blockIdx.y; the thread of kx = 0 also
+// takes the Nyquist column kx = n/2.
+template <bool ADVANCE>
+__global__ void __launch_bounds__(kSpecThreads) k_spectral(const __grid_constant__ SpecArgs a) {
+    const int i = blockIdx.x * kSpecThreads + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= a.n / 2) return;
+    spectral_mode<ADVANCE>(a, i, j);
+    if (i == 0) spectral_mode<ADVANCE>(a, a.n / 2, j);
 }
 
-template <int REM>
-__global__ void __launch_bounds__(512) k_row(const __grid_constant__ RowArgs a, const RowLevel lv) {
-    extern __shared__ float2 sm[];
-    row_pass<REM>(a, lv, blockIdx.x, sm);
+// N = u wx + v wy at every node and the level pair of the new level
+// (nonlinear_quad).  Four nodes per thread: 16-byte loads of the planes.
+__global__ void k_nonlinear(const float4* __restrict__ phys4, float4* __restrict__ nl4,
+                            const float4* __restrict__ src, float4* __restrict__ dst,
+                            float4* __restrict__ other, size_t n4, int stencil_plane,
+                            int psi_plane, const float2* __restrict__ psi_src,
+                            float2* __restrict__ psi_dst, float2* __restrict__ psi_other) {
+    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n4) return;
+    nonlinear_quad(phys4, nl4, src, dst, other, n4, q, stencil_plane, psi_plane, psi_src, psi_dst,
+                   psi_other);
 }
 
-using ColumnKernel = void (*)(ColArgs, int, int);
-using RowKernel = void (*)(RowArgs, RowLevel);
-const ColumnKernel kColumn[4] = {k_column<0>, k_column<1>, k_column<2>, k_column<3>};
-const RowKernel kRow[4] = {k_row<0>, k_row<1>, k_row<2>, k_row<3>};
-
-// Initial projection: mean removed, 2/3 rule (Sec. 3.1); row-major cuFFT
-// output [j][kx] -> column-major omega-hat [kx][j].
+// Initial projection: mean removed, 2/3 rule (Sec. 3.1).
 __global__ void k_project(const float2* __restrict__ src, float2* __restrict__ what, int n, int nh) {
-    const int i = blockIdx.x * kProjThreads + threadIdx.x, j = blockIdx.y;
+    const int i = blockIdx.x * kSpecThreads + threadIdx.x, j = blockIdx.y;
     if (i >= nh) return;
+    const size_t q = (size_t)j * nh + i;
     const int ky = wavenumber_row(j, n), kx = i;
     const bool keep = kept(kx, ky, n) && !(kx == 0 && ky == 0);
-    what[(size_t)kx * n + j] = keep ? src[(size_t)j * nh + i] : make_float2(0.f, 0.f);
-}
-
-// One plane (or, for p < 0, omega-hat / n^2) of the current level as a
-// row-major half spectrum for cuFFT's C2R.
-__global__ void k_plane_rowmajor(const __grid_constant__ ColArgs a, int p, float2* __restrict__ dst) {
-    const int i = blockIdx.x * kProjThreads + threadIdx.x, j = blockIdx.y;
-    const int n = a.n, nh = n / 2 + 1;
-    if (i >= nh) return;
-    float2 v = make_float2(0.f, 0.f);
-    if (i < n / 2) {
-        const float2 w = a.what[(size_t)i * n + j];
-        const float2 ws = make_float2(w.x * a.scale, w.y * a.scale);
-        v = p < 0 ? ws : plane_value(a, p, ws, i, j);
-    }
-    dst[(size_t)j * nh + i] = v;
+    what[q] = keep ? src[q] : make_float2(0.f, 0.f);
 }
 
 __global__ void k_d2f(const double* __restrict__ src, float* __restrict__ dst, size_t count) {
@@ -83,17 +71,25 @@ __global__ void k_f2d(const float* __restrict__ src, double* __restrict__ dst, s
     if (q < count) dst[q] = (double)src[q * stride + offset];
 }
 
+// omega-hat / n^2 into the auxiliary spectrum (for the physical vorticity).
+__global__ void k_scaled_copy(const float2* __restrict__ src, float2* __restrict__ dst,
+                              size_t nmodes, float scale) {
+    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nmodes) dst[q] = make_float2(src[q].x * scale, src[q].y * scale);
+}
+
 // FP64 partial sums over the half spectrum for E, Z, P (Parseval).  Modes
 // with 0 < kx < n/2 stand for themselves and their conjugates (weight 2).
 __global__ void __launch_bounds__(kRedThreads) k_spec_diag(const float2* __restrict__ what, int n,
-                                                           size_t nmodes, double* __restrict__ partial) {
+                                                           int nh, size_t nmodes,
+                                                           double* __restrict__ partial) {
     double se = 0.0, sz = 0.0, sp = 0.0;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < nmodes;
          q += (size_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(q / n), j = (int)(q - (size_t)kx * n);
-        const int ky = wavenumber_row(j, n);
+        int j = (int)(q / nh), i = (int)(q - (size_t)j * nh);
+        int ky = wavenumber_row(j, n), kx = i;
         double k2 = (double)kx * kx + (double)ky * ky;
-        double wgt = (kx == 0 || kx == n / 2) ? 1.0 : 2.0;
+        double wgt = (i == 0 || i == n / 2) ? 1.0 : 2.0;
         double a = (double)what[q].x, b = (double)what[q].y;
         double m = wgt * (a * a + b * b);
         sz += m;
@@ -138,126 +134,100 @@ __global__ void __launch_bounds__(kRedThreads) k_spec_diag_final(const double* _
 
 }  // namespace
 
-ColArgs column_args(const el_flow* f) {
-    ColArgs a{};
+static el_status fft_exec_c2r(el_flow* f, cufftHandle plan, float2* in, float* out) {
+    cufftResult r = cufftExecC2R(plan, reinterpret_cast<cufftComplex*>(in), out);
+    if (r != CUFFT_SUCCESS) return fail(f, EL_ECUFFT, "cufftExecC2R failed (%d)", (int)r);
+    return EL_OK;
+}
+
+static el_status fft_exec_r2c(el_flow* f, float* in, float2* out) {
+    cufftResult r = cufftExecR2C(f->plan_r2c, in, reinterpret_cast<cufftComplex*>(out));
+    if (r != CUFFT_SUCCESS) return fail(f, EL_ECUFFT, "cufftExecR2C failed (%d)", (int)r);
+    return EL_OK;
+}
+
+static SpecArgs spec_args(el_flow* f, int first) {
+    SpecArgs a{};
     a.what = f->what;
     a.what_lo = f->what_lo;
     a.hist = f->hist;
-    a.nrow = f->nrow;
-    a.planes = f->planes;
+    a.nhat = f->nhat;
+    a.spec = f->spec;
     a.ex = f->ex;
     a.ey = f->ey;
     a.pre_x = f->pre_x;
     a.pre_y = f->pre_y;
-    a.tw = f->tw_col;
-    a.pstride = (size_t)f->n * f->pitch;
     a.n = f->n;
-    a.log2n = f->log2n;
-    a.pitch = f->pitch;
+    a.nh = f->nh;
     a.nplanes = f->nplanes;
-    a.log2tc = f->log2tc;
-    a.mode = f->d.ab2_mode;
     a.spline = f->stencil_plane != 0;
     a.psi_plane = f->psi_plane;
+    a.mode = f->d.ab2_mode;
+    a.first = first;
+    a.nmodes = f->nmodes;
     a.scale = 1.0f / (float)f->n2;
     a.dt = (float)f->d.dt;
     a.nu = (float)f->d.nu;
     return a;
 }
 
-RowArgs row_args(const el_flow* f) {
-    RowArgs r{};
-    r.planes = f->planes;
-    r.nrow = f->nrow;
-    r.tw = f->tw_row;
-    r.wn = f->wn;
-    r.pstride = (size_t)f->n * f->pitch;
-    r.n = f->n;
-    r.log2n = f->log2n;
-    r.pitch = f->pitch;
-    r.nplanes = f->nplanes;
-    r.stencil_plane = f->stencil_plane;
-    r.psi_plane = f->psi_plane;
-    return r;
-}
-
-// Level m is written into pair (m-1, m) = snap[(m + 1) % 2].
-RowLevel row_level(const el_flow* f, int64_t m, bool setup) {
-    RowLevel l{};
-    l.snap_dst = f->snap[(m + 1) % 2];
-    l.snap_src = setup ? nullptr : f->snap[m % 2];
-    l.snap_other = setup ? f->snap[m % 2] : nullptr;
-    l.psi_dst = f->psi[(m + 1) % 2];
-    l.psi_src = setup ? nullptr : f->psi[m % 2];
-    l.psi_other = setup ? f->psi[m % 2] : nullptr;
-    l.setup = setup ? 1 : 0;
-    return l;
-}
-
-size_t max_col_smem_bytes() {
-    size_t m = 0;
-    for (int l = 4; l <= 12; l++) m = std::max(m, col_smem_bytes(l, col_log2tc(1 << l)));
-    return m;
-}
-
-size_t max_row_smem_bytes() { return row_smem_bytes(12, kMaxPlanes); }
-
-el_status fluid_kernel_setup(el_flow* f) {
-    for (int r = 0; r < 4; r++) {
-        EL_CUDA_OK(f, cudaFuncSetAttribute(kRow[r], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)max_row_smem_bytes()));
-        EL_CUDA_OK(f, cudaFuncSetAttribute(kColumn[r], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)max_col_smem_bytes()));
-    }
-    return EL_OK;
-}
-
-// Column pass then row pass producing level m.
-static el_status launch_passes(el_flow* f, int first, int advance, int64_t m, bool setup) {
-    kColumn[f->log2n & 3]<<<col_tiles(f->n, f->log2tc), col_threads(f->n, f->log2tc),
-                            col_smem_bytes(f->log2n, f->log2tc), f->stream>>>(column_args(f), first,
-                                                                               advance);
+// Planes -> physical fields, nonlinear term, the pair (m-1, m) of the new
+// level m (pair (k, k+1) is snap[k % 2]), N-hat.
+static el_status finish_rhs(el_flow* f, int64_t m, bool setup) {
+    const int T = 256;
+    EL_TRY(fft_exec_c2r(f, f->plan_c2r, f->spec, f->phys));
+    size_t n4 = f->n2 / 4;
+    float4* dst = f->snap[(m + 1) % 2];        // pair (m-1, m)
+    const float4* src = f->snap[m % 2];        // pair (m-2, m-1): level m-1 in its second half
+    k_nonlinear<<<blocks_for((int64_t)n4, T), T, 0, f->stream>>>(
+        reinterpret_cast<const float4*>(f->phys), reinterpret_cast<float4*>(f->nl),
+        setup ? nullptr : src, dst, setup ? f->snap[m % 2] : nullptr, n4, f->stencil_plane,
+        f->psi_plane, setup ? nullptr : f->psi[m % 2], f->psi[(m + 1) % 2],
+        setup ? f->psi[m % 2] : nullptr);
     EL_LAUNCHED(f);
-    kRow[(f->log2n - 1) & 3]<<<f->n, row_threads(f->n, f->nplanes),
-                               row_smem_bytes(f->log2n, f->nplanes), f->stream>>>(
-        row_args(f), row_level(f, m, setup));
-    EL_LAUNCHED(f);
+    EL_TRY(fft_exec_r2c(f, f->nl, f->nhat));
     return EL_OK;
 }
 
-static el_status fft_exec_c2r(el_flow* f, float2* in, float* out) {
-    cufftResult r = cufftExecC2R(f->plan_c2r1, reinterpret_cast<cufftComplex*>(in), out);
-    if (r != CUFFT_SUCCESS) return fail(f, EL_ECUFFT, "cufftExecC2R failed (%d)", (int)r);
-    return EL_OK;
+static dim3 spec_grid(el_flow* f) {
+    return dim3((unsigned)((f->n / 2 + kSpecThreads - 1) / kSpecThreads), (unsigned)f->n);
 }
 
 el_status fluid_init(el_flow* f, const double* omega0_host) {
     const int T = 256;
-    EL_CUDA_OK(f, cudaMemcpyAsync(f->stage64, omega0_host, f->n2 * sizeof(double),
+    double* stage = f->stage64;
+    EL_CUDA_OK(f, cudaMemcpyAsync(stage, omega0_host, f->n2 * sizeof(double),
                                   cudaMemcpyHostToDevice, f->stream));
-    k_d2f<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(f->stage64, f->aux_phys, f->n2);
+    k_d2f<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(stage, f->nl, f->n2);
     EL_LAUNCHED(f);
-    cufftResult cr = cufftExecR2C(f->plan_r2c, f->aux_phys, reinterpret_cast<cufftComplex*>(f->aux_spec));
-    if (cr != CUFFT_SUCCESS) return fail(f, EL_ECUFFT, "cufftExecR2C failed (%d)", (int)cr);
-    k_project<<<dim3((unsigned)((f->nh + kProjThreads - 1) / kProjThreads), (unsigned)f->n),
-                kProjThreads, 0, f->stream>>>(f->aux_spec, f->what, f->n, f->nh);
+    EL_TRY(fft_exec_r2c(f, f->nl, f->nhat));
+    k_project<<<dim3((unsigned)((f->nh + kSpecThreads - 1) / kSpecThreads), (unsigned)f->n),
+                kSpecThreads, 0, f->stream>>>(f->nhat, f->what, f->n, f->nh);
     EL_LAUNCHED(f);
     EL_CUDA_OK(f, cudaMemsetAsync(f->hist, 0, f->nmodes * sizeof(float2), f->stream));
     EL_CUDA_OK(f, cudaMemsetAsync(f->what_lo, 0, f->nmodes * sizeof(float2), f->stream));
-    // the planes' Nyquist column (and the row padding) stays zero from here on
-    EL_CUDA_OK(f, cudaMemsetAsync(f->planes, 0,
-                                  (size_t)f->nplanes * f->n * f->pitch * sizeof(float2), f->stream));
-    EL_TRY(fluid_kernel_setup(f));
-    return launch_passes(f, 0, 0, 0, true);
+    k_spectral<false><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, 0));
+    EL_LAUNCHED(f);
+    return finish_rhs(f, 0, true);
 }
 
 // Fluid n -> n+1 for step number n = `step`.
 el_status fluid_step(el_flow* f, int64_t step) {
-    return launch_passes(f, step == 0, 1, step + 1, false);
+    k_spectral<true><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, step == 0));
+    EL_LAUNCHED(f);
+    return finish_rhs(f, step + 1, false);
+}
+
+// The physical planes (u, v, ...) of the current level from omega-hat,
+// without touching N-hat or the level pairs (after a state was loaded).
+el_status fluid_refresh_planes(el_flow* f) {
+    k_spectral<false><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, 0));
+    EL_LAUNCHED(f);
+    return fft_exec_c2r(f, f->plan_c2r, f->spec, f->phys);
 }
 
 el_status fluid_diagnostics(el_flow* f) {
-    k_spec_diag<<<kRedBlocks, kRedThreads, 0, f->stream>>>(f->what, f->n, f->nmodes, f->red);
+    k_spec_diag<<<kRedBlocks, kRedThreads, 0, f->stream>>>(f->what, f->n, f->nh, f->nmodes, f->red);
     EL_LAUNCHED(f);
     double nn = (double)f->n2;
     k_spec_diag_final<<<1, kRedThreads, 0, f->stream>>>(f->red, kRedBlocks, 0.5 / (nn * nn),
@@ -269,13 +239,16 @@ el_status fluid_diagnostics(el_flow* f) {
 el_status fluid_get_field(el_flow* f, int which, double* host_nn) {
     const int T = 256;
     double* out = f->stage64;
-    if (which <= 2) {
-        // 0: omega, 1: u, 2: v of the current level, from omega-hat
-        k_plane_rowmajor<<<dim3((unsigned)((f->nh + kProjThreads - 1) / kProjThreads), (unsigned)f->n),
-                           kProjThreads, 0, f->stream>>>(column_args(f), which - 1, f->aux_spec);
+    if (which == 0) {
+        k_scaled_copy<<<blocks_for((int64_t)f->nmodes, T), T, 0, f->stream>>>(
+            f->what, f->aux_spec, f->nmodes, 1.0f / (float)f->n2);
         EL_LAUNCHED(f);
-        EL_TRY(fft_exec_c2r(f, f->aux_spec, f->aux_phys));
+        EL_TRY(fft_exec_c2r(f, f->plan_c2r1, f->aux_spec, f->aux_phys));
         k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(f->aux_phys, out, f->n2, 1, 0);
+    } else if (which == 1 || which == 2) {
+        // physical planes 0/1 hold u, v of the current level
+        k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(f->phys + (which - 1) * f->n2,
+                                                                   out, f->n2, 1, 0);
     } else {
         // stencil field of the current level n: second half of pair (n-1, n)
         k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(
@@ -289,33 +262,15 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn) {
     return EL_OK;
 }
 
-void fft_twiddles(int log2l, std::vector<float2>& out) {
-    out.clear();
-    const FftSchedule s = fft_schedule(log2l);
-    int64_t ns = 1;
-    for (int p = 0; p < s.npass; p++) {
-        const int64_t R = (int64_t)1 << s.log2r[p];
-        if (p > 0)
-            for (int64_t r = 1; r < R; r++)
-                for (int64_t q = 0; q < ns; q++) {
-                    const double ang = -kTwoPi * (double)(q * r) / (double)(ns * R);
-                    out.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
-                }
-        ns *= R;
-    }
-}
-
 // Host-side FP64 tables: the 1-D integrating factors exp(-nu k^2 dt) as
-// float pairs (hi, lo), the spline prefilter factors 3 / (2 + cos k dx), the
-// FFT twiddles of the column (length n) and row (length n/2) transforms and
-// exp(-2 pi i k / n), k = 0..n/2, of the real-transform split.
-void fluid_tables(const el_flow_desc& d, FluidTables& t) {
-    int n = d.n, nh = n / 2 + 1, log2n = 0;
-    while ((1 << log2n) < n) log2n++;
-    t.ex.resize(nh);
-    t.px.resize(nh);
-    t.ey.resize(n);
-    t.py.resize(n);
+// float pairs (hi, lo), and the spline prefilter factors 3 / (2 + cos k dx).
+void fluid_tables(const el_flow_desc& d, std::vector<float2>& ex, std::vector<float2>& ey,
+                  std::vector<float>& px, std::vector<float>& py) {
+    int n = d.n, nh = n / 2 + 1;
+    ex.resize(nh);
+    px.resize(nh);
+    ey.resize(n);
+    py.resize(n);
     double dxg = kTwoPi / n;
     auto pair = [](double v) {
         float hi = (float)v;
@@ -323,20 +278,13 @@ void fluid_tables(const el_flow_desc& d, FluidTables& t) {
     };
     for (int i = 0; i < nh; i++) {
         double k = i;
-        t.ex[i] = pair(std::exp(-d.nu * k * k * d.dt));
-        t.px[i] = (float)(3.0 / (2.0 + std::cos(k * dxg)));
+        ex[i] = pair(std::exp(-d.nu * k * k * d.dt));
+        px[i] = (float)(3.0 / (2.0 + std::cos(k * dxg)));
     }
     for (int j = 0; j < n; j++) {
         double k = j < n / 2 ? j : j - n;
-        t.ey[j] = pair(std::exp(-d.nu * k * k * d.dt));
-        t.py[j] = (float)(3.0 / (2.0 + std::cos(k * dxg)));
-    }
-    fft_twiddles(log2n, t.tw_col);
-    fft_twiddles(log2n - 1, t.tw_row);
-    t.wn.resize(nh);
-    for (int k = 0; k < nh; k++) {
-        const double ang = -kTwoPi * k / n;
-        t.wn[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        ey[j] = pair(std::exp(-d.nu * k * k * d.dt));
+        py[j] = (float)(3.0 / (2.0 + std::cos(k * dxg)));
     }
 }
 

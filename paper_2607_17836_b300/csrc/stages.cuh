@@ -33,6 +33,163 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+struct SpecArgs {
+    float2* what;       // omega-hat, high part
+    float2* what_lo;    // omega-hat, low part
+    float2* hist;       // AB2 history
+    const float2* nhat; // N-hat of the current level
+    float2* spec;       // nplanes output half spectra
+    const float2* ex;   // exp(-nu kx^2 dt) as (hi, lo)
+    const float2* ey;   // exp(-nu ky^2 dt) as (hi, lo)
+    const float* pre_x;
+    const float* pre_y;
+    int n, nh, nplanes, mode, first;
+    int spline;         // 1: write prefiltered cu, cv to planes 4, 5
+    int psi_plane;      // plane of the streamfunction stencil field, or -1
+    size_t nmodes;
+    float scale, dt, nu;
+};
+
+// AB2 update (when ADVANCE) and the spectral velocity / gradient planes of
+// the resulting omega-hat.
+//
+// omega-hat is held as an unevaluated sum w_hi + w_lo of two floats: one
+// float would round the small per-step change (the viscous decay is only
+// nu k^2 dt of w) the same way step after step and drift by up to half an
+// ulp per step; the pair keeps about 44 bits.  Only w_hi feeds the planes.
+// mode 0 (integrating factor): E = exp(-nu k^2 dt) = ex[kx] * ey[ky] (the 1-D
+//   factors computed on the host in FP64, held as float pairs);
+//   w <- E w - dt (3/2 E N - 1/2 E^2 H), H <- N.
+// mode 1 (Eq. 10 as printed): R = -N - nu k^2 w; w <- w + dt (3/2 R - 1/2 H), H <- R.
+// The first step is forward Euler in either mode.
+template <bool ADVANCE>
+__device__ __forceinline__ void spectral_mode(const SpecArgs& a, int i, int j) {
+    const int n = a.n;
+    const size_t q = (size_t)j * a.nh + i;
+    const int kx = i, ky = wavenumber_row(j, n);
+    const bool keep = kept(kx, ky, n);
+    const float2* __restrict__ nhat = a.nhat;
+    const float2* __restrict__ hist_in = a.hist;
+    const float2* __restrict__ lo_in = a.what_lo;
+    // every load first, so they are all in flight together
+    float2 w = a.what[q];
+    float2 N = make_float2(0.f, 0.f), wl = N, H = N, ea = N, eb = N;
+    if (ADVANCE) {
+        N = nhat[q];
+        wl = lo_in[q];
+        if (!a.first) H = hist_in[q];
+        if (a.mode == 0) {
+            ea = a.ex[i];
+            eb = a.ey[j];
+        }
+        if (!keep) N = make_float2(0.f, 0.f);
+        const float dt = a.dt;
+        float2 inc, hi, lo, hist_out;
+        if (a.mode == 0) {
+            float Eh = ea.x * eb.x;  // E = Eh + El (two-product of the hi parts)
+            float El = fmaf(ea.x, eb.x, -Eh) + fmaf(ea.x, eb.y, ea.y * eb.x);
+            float E2 = Eh * Eh;
+            float c1 = a.first ? dt : 1.5f * dt, c2 = a.first ? 0.f : 0.5f * dt * E2;
+            float px = Eh * w.x, py = Eh * w.y;
+            hi = make_float2(px, py);
+            lo = make_float2(fmaf(Eh, w.x, -px) + fmaf(El, w.x, Eh * wl.x),
+                             fmaf(Eh, w.y, -py) + fmaf(El, w.y, Eh * wl.y));
+            inc = make_float2(fmaf(c2, H.x, -c1 * Eh * N.x), fmaf(c2, H.y, -c1 * Eh * N.y));
+            hist_out = N;
+        } else {
+            float nuk2 = a.nu * (float)(kx * kx + ky * ky);
+            float2 R = make_float2(-N.x - nuk2 * w.x, -N.y - nuk2 * w.y);
+            inc = a.first ? make_float2(dt * R.x, dt * R.y)
+                          : make_float2(dt * (1.5f * R.x - 0.5f * H.x), dt * (1.5f * R.y - 0.5f * H.y));
+            hi = w;
+            lo = wl;
+            hist_out = R;
+        }
+        float sx, exx, sy, eyy;
+        two_sum(hi.x, lo.x + inc.x, sx, exx);
+        two_sum(hi.y, lo.y + inc.y, sy, eyy);
+        w = make_float2(sx, sy);
+        a.hist[q] = hist_out;
+        a.what[q] = w;
+        a.what_lo[q] = make_float2(exx, eyy);
+    }
+    const float dkx = (i == n / 2) ? 0.f : (float)kx;  // Nyquist: zero derivative
+    const float dky = (j == n / 2) ? 0.f : (float)ky;
+    const float k2 = (float)(kx * kx + ky * ky);
+    w.x *= a.scale;
+    w.y *= a.scale;
+    const float ik2 = k2 > 0.f ? 1.f / k2 : 0.f;  // psi-hat(0) = 0 (Eq. 5)
+    const float2 psi = make_float2(w.x * ik2, w.y * ik2);
+    const float2 uh = make_float2(-dky * psi.y, dky * psi.x);  // u-hat = i ky psi-hat
+    const float2 vh = make_float2(dkx * psi.y, -dkx * psi.x);  // v-hat = -i kx psi-hat
+    const size_t m = a.nmodes;
+    float2* __restrict__ spec = a.spec;
+    spec[q] = uh;
+    spec[m + q] = vh;
+    spec[2 * m + q] = make_float2(-dkx * w.y, dkx * w.x);  // i kx omega-hat
+    spec[3 * m + q] = make_float2(-dky * w.y, dky * w.x);  // i ky omega-hat
+    // Interpolating cubic-spline coefficients: (c_{i-1} + 4 c_i + c_{i+1})/6 = f_i
+    // is diagonal in Fourier space with factor (2 + cos k dx)/3 per axis.
+    const float pf = a.spline ? a.pre_x[i] * a.pre_y[j] : 1.0f;
+    if (a.spline) {
+        spec[4 * m + q] = make_float2(uh.x * pf, uh.y * pf);
+        spec[5 * m + q] = make_float2(vh.x * pf, vh.y * pf);
+    }
+    if (a.psi_plane >= 0) spec[(size_t)a.psi_plane * m + q] = make_float2(psi.x * pf, psi.y * pf);
+}
+
+// N = u wx + v wy at four consecutive nodes 4q..4q+3 (Eq. 7), and the
+// level pair (m-1, m) of the new level m: `dst` = (level m-1 read from the
+// second half of `src`, level m), one full 16-byte store per node.  At set-up
+// (src == nullptr) level 0 fills both halves of `dst` and of `other`, so no
+// pair ever holds uninitialised values (a blend weight of 0 times a NaN left
+// in reused memory is NaN).
+__device__ __forceinline__ void nonlinear_quad(const float4* __restrict__ phys4,
+                                               float4* __restrict__ nl4,
+                                               const float4* __restrict__ src,
+                                               float4* __restrict__ dst,
+                                               float4* __restrict__ other, size_t n4, size_t q,
+                                               int stencil_plane, int psi_plane,
+                                               const float2* __restrict__ psi_src,
+                                               float2* __restrict__ psi_dst,
+                                               float2* __restrict__ psi_other) {
+    float4 u = phys4[q], v = phys4[n4 + q], wx = phys4[2 * n4 + q], wy = phys4[3 * n4 + q];
+    nl4[q] = make_float4(fmaf(u.x, wx.x, v.x * wy.x), fmaf(u.y, wx.y, v.y * wy.y),
+                         fmaf(u.z, wx.z, v.z * wy.z), fmaf(u.w, wx.w, v.w * wy.w));
+    if (stencil_plane != 0) {
+        u = phys4[4 * n4 + q];
+        v = phys4[5 * n4 + q];
+    }
+    const float2 s[4] = {make_float2(u.x, v.x), make_float2(u.y, v.y), make_float2(u.z, v.z),
+                         make_float2(u.w, v.w)};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const size_t i = 4 * q + k;
+        if (src) {
+            const float4 old = src[i];
+            dst[i] = make_float4(old.z, old.w, s[k].x, s[k].y);
+        } else {
+            const float4 both = make_float4(s[k].x, s[k].y, s[k].x, s[k].y);
+            dst[i] = both;
+            other[i] = both;
+        }
+    }
+    if (psi_plane >= 0) {  // the streamfunction stencil field, same pair layout (scalar)
+        const float4 ps = phys4[(size_t)psi_plane * n4 + q];
+        const float pk[4] = {ps.x, ps.y, ps.z, ps.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const size_t i = 4 * q + k;
+            if (src) {
+                psi_dst[i] = make_float2(psi_src[i].y, pk[k]);
+            } else {
+                psi_dst[i] = make_float2(pk[k], pk[k]);
+                psi_other[i] = make_float2(pk[k], pk[k]);
+            }
+        }
+    }
+}
+
 // Carry an offset that left [0, 1) into the cell index and the image count.
 __device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off, int& cell,
                                            int& dimg) {
