@@ -319,6 +319,83 @@ def run_serving(dev, count=200, budget_gb=120.0, timeout=90.0):
             "hbm_budget_gb": budget_gb}
 
 
+# Sec. 5.2 with the paper's 2 km domain mapped onto [0, 2 pi): lengths and
+# speeds scale by pi (k = 1, alpha = 3.6 pi, eps = 0.3 L = 0.6 pi), times stay.
+KINEMATIC_PAPER = dict(alpha=3.6 * math.pi, k=1.0, eps=0.6 * math.pi, omega=1.8, phi=0.0)
+
+
+def run_kinematic(count=1000, n=128, dt=1e-3, marks=(1000, 10_000, 100_000)):
+    """The tracer benchmark of Sec. 5.2 at the paper's size: 1000 tracers in
+    the oscillating Taylor-Green flow for 100 h (1e5 steps of 1e-3 h), by the
+    three routes; msd in km^2 (lengths / pi) at 1, 10 and 100 h."""
+    import torch
+    from paper_2607_17836_b300 import elpath
+    xy = inputs.uniform_positions(count, 7)
+    routes = {"analytic": (elpath.ANALYTIC, 0), "velocity_bilinear": (0, 0),
+              "streamfunction_bilinear": (0, 1)}
+    out = {"workload": f"oscillating Taylor-Green (Sec. 5.2), {count} tracers, {n}^2 grid "
+                       f"(the paper's 100^2 rounded up to a power of two), dt = {dt} h, "
+                       f"{marks[-1]} steps", "routes": {}}
+    scale = 1.0 / math.pi ** 2  # (2 pi / L)^2 with L = 2 km
+    for name, (interp, tv) in routes.items():
+        g = elpath.Flow(n, 0.0, dt, None, interp=interp, max_species=1, max_particles=count,
+                        tracer_velocity=tv, kinematic=KINEMATIC_PAPER, sort_every=0)
+        g.set_particles(0, xy, 0.0)
+        st = g.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        done, series, ms = 0, [], 0.0
+        for mark in marks:
+            e0.record(st)
+            g.step(mark - done)
+            e1.record(st)
+            st.synchronize()
+            ms += e0.elapsed_time(e1)
+            done = mark
+            s = g.stats()
+            series.append({"t_h": s["t"], "msd_km2": (s["msd"][0][0] + s["msd"][0][1]) * scale,
+                           "msd_sem_km2": math.hypot(*s["msd_sem"][0]) * scale,
+                           "diffusivity_km2_per_h": (s["diffusivity"][0][0] + s["diffusivity"][0][1]) * scale})
+        out["routes"][name] = {"ms_per_step": ms / done, "particle_steps_per_s": count * done / (ms / 1e3),
+                               "series": series}
+        g.close()
+    a = out["routes"]["analytic"]["series"][-1]["msd_km2"]
+    out["msd_rel_diff_vs_analytic_at_end"] = {
+        k: abs(v["series"][-1]["msd_km2"] - a) / a for k, v in out["routes"].items() if k != "analytic"}
+    return out
+
+
+def run_transport(wl, steps=(500, 1000, 2000)):
+    """Particle-number convergence (Sec. 5.5) on the 1024^2 decaying field:
+    100, 500, 1000 and 2000 tracers in one flow; msd, its standard error and
+    D = msd / 2t per count, and the largest pairwise msd gap in units of the
+    combined standard error."""
+    from paper_2607_17836_b300 import elpath
+    sets = [(100, 31), (500, 32), (1000, 33), (2000, 34)]
+    g = elpath.Flow(wl.n, wl.nu, wl.dt, wl.omega0(), interp=0, max_species=len(sets),
+                    max_particles=sum(c for c, _ in sets), sort_every=20)
+    for k, (c, seed) in enumerate(sets):
+        g.set_particles(k, inputs.uniform_positions(c, seed), 0.0)
+    done, rows = 0, []
+    for mark in steps:
+        g.step(mark - done)
+        done = mark
+        s = g.stats()
+        z = 0.0
+        for i in range(len(sets)):
+            for j in range(i + 1, len(sets)):
+                for a in range(2):
+                    bound = math.hypot(s["msd_sem"][i][a], s["msd_sem"][j][a])
+                    if bound > 0:
+                        z = max(z, abs(s["msd"][i][a] - s["msd"][j][a]) / bound)
+        rows.append({"t": s["t"], "max_gap_in_sem": z,
+                     "by_count": {str(c): {"msd": list(s["msd"][k]), "msd_sem": list(s["msd_sem"][k]),
+                                           "diffusivity": list(s["diffusivity"][k])}
+                                  for k, (c, _) in enumerate(sets)}})
+    g.close()
+    return {"workload": "decaying turbulence 1024^2 (the config-2 field), tracers 100/500/1000/2000",
+            "series": rows}
+
+
 def run_ours(args, wl, scheme, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -450,6 +527,10 @@ def run_ours(args, wl, scheme, world, rank, local):
             "clocks": clocks.summary(), "energy": st["energy"]}
     if not args.no_ensemble:
         line["ensemble"] = run_ensemble(args, dev)
+    if not args.no_kinematic:
+        line["kinematic_tg"] = run_kinematic()
+    if not args.no_transport:
+        line["transport"] = run_transport(wl)
     if not args.no_serving:
         line["serving"] = run_serving(dev)
     if not args.no_cpu_baseline:
@@ -471,6 +552,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-kinematic", action="store_true")
+    ap.add_argument("--no-transport", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()

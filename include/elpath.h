@@ -57,7 +57,11 @@ typedef enum {
 typedef enum {
     EL_BILINEAR = 0,     /* Eq. 16, 2 x 2 nodes                                 */
     EL_CATMULL_ROM = 1,  /* Eqs. 18-19, 4 x 4 nodes i-1..i+2, periodic wrap     */
-    EL_BSPLINE = 2       /* Eqs. 21-22, 4 x 4 nodes, periodic wrap              */
+    EL_BSPLINE = 2,      /* Eqs. 21-22, 4 x 4 nodes, periodic wrap              */
+    EL_ANALYTIC = 3      /* kinematic flows only (el_create_kinematic): the
+                            prescribed velocity evaluated at the particle at
+                            the exact stage time, no grid (Sec. 5.2, approach
+                            (i)); tracers only                               */
 } el_interp;
 
 #define EL_MAX_SPECIES 8
@@ -94,6 +98,34 @@ size_t el_workspace_bytes(const el_flow_desc* desc);
 el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* dev_workspace,
                          size_t workspace_bytes, void* cuda_stream, el_flow** out);
 
+/* The time-periodic kinematic flow of Sec. 5.2 (oscillating Taylor-Green
+ * eddies), prescribed instead of solved:
+ *   psi = (alpha / k) sin(k [x - eps sin(omega t)]) sin(k [y - eps sin(omega t + phi)]),
+ *   u = d psi / dy = alpha sin(k [...x]) cos(k [...y]),
+ *   v = -d psi / dx = -alpha cos(k [...x]) sin(k [...y]),
+ * on the [0, 2 pi)^2 domain (the paper's L maps to 2 pi: lengths scale by
+ * 2 pi / L, speeds too).  k must be a positive integer (periodicity) below
+ * n / 3. */
+typedef struct {
+    double alpha;   /* peak speed                                   */
+    double k;       /* wavenumber (integer >= 1)                    */
+    double eps;     /* oscillation amplitude (length)               */
+    double omega;   /* oscillation frequency                        */
+    double phi;     /* phase between the x and y oscillations       */
+} el_kinematic;
+
+/* A flow whose levels are the kinematic field above at t = step * dt
+ * (level pairs, streamfunction pairs and spline coefficients as for a solved
+ * flow: every interpolant and both tracer paths apply unchanged), plus
+ * interp = EL_ANALYTIC.  Everything else is as el_create_flow (workspace =
+ * el_workspace_bytes(desc)); el_get_stats reports the field's exact E, Z, P;
+ * el_get_field evaluates it on the grid.  Such a flow cannot join a batch,
+ * and its steps run as direct launches (no captured graph).  EL_EINVAL for a
+ * bad k, or EL_ANALYTIC with tracer_velocity = 1. */
+el_status el_create_kinematic(const el_flow_desc* desc, const el_kinematic* kin,
+                              void* dev_workspace, size_t workspace_bytes, void* cuda_stream,
+                              el_flow** out);
+
 /* Place np particles in species slot `species` (0..max_species-1).
  * st = 0: passive tracers (Eq. 2); st > 0: inertial particles (Eq. 3).
  * xy: host, 2*np doubles (x0, y0, x1, y1, ...), any real value: positions are
@@ -118,6 +150,10 @@ typedef struct {
     double cluster[EL_MAX_SPECIES];   /* Var(n)/mean(n) - 1 on a 64 x 64 box grid       */
     int64_t np[EL_MAX_SPECIES];       /* particles per species (0 = empty slot)         */
     int32_t finite;                   /* 1 if every reduced quantity is finite          */
+    /* Transport statistics of Sec. 5.5 / Sec. 6 per species and axis:          */
+    double msd_sem[EL_MAX_SPECIES][2];     /* standard error of msd: sqrt(s^2 / np),    */
+                                           /* s^2 the sample variance of (x - x0)^2     */
+    double diffusivity[EL_MAX_SPECIES][2]; /* D = msd / (2 t) (0 at t = 0)              */
 } el_stats;
 
 /* Diagnostics of the current state, reduced in FP64 in a fixed order (the

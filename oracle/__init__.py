@@ -232,6 +232,30 @@ def msd(x, y, x0, y0):
     return float(np.mean(dx * dx)), float(np.mean(dy * dy))
 
 
+def msd_sem(x, y, x0, y0):
+    """Standard error of the per-axis mean-square displacement (Sec. 5.5):
+    the sample standard deviation of the squared displacements over the
+    particles divided by sqrt(np); two-pass (mean first, then the squared
+    deviations).  0 for fewer than two particles."""
+    out = []
+    for a, a0 in ((x, x0), (y, y0)):
+        d = np.asarray(a, dtype=np.float64) - np.asarray(a0, dtype=np.float64)
+        q = d * d
+        m = q.size
+        if m < 2:
+            out.append(0.0)
+            continue
+        mean = q.sum() / m
+        var = ((q - mean) ** 2).sum() / (m - 1)
+        out.append(float(np.sqrt(var / m)))
+    return tuple(out)
+
+
+def diffusivity(msd_xy, t):
+    """D_i = <(x_i - x_i0)^2> / (2 t) per axis (Sec. 5.5, Sec. 6), 0 at t = 0."""
+    return tuple((m / (2.0 * t)) if t > 0 else 0.0 for m in msd_xy)
+
+
 def cluster_index(x, y, boxes=64):
     """Var(n)/mean(n) - 1 of particle counts on a boxes x boxes grid of the
     periodic domain (0 for uniformly random positions)."""
@@ -242,6 +266,84 @@ def cluster_index(x, y, boxes=64):
     counts = np.bincount(by * boxes + bx, minlength=boxes * boxes).astype(np.float64)
     m = counts.mean()
     return float(counts.var() / m - 1.0) if m > 0 else 0.0
+
+
+# --- the prescribed kinematic flow (Sec. 5.2) -------------------------------------
+# psi = (alpha/k) sin(k[x - eps sin(omega t)]) sin(k[y - eps sin(omega t + phi)]),
+# u = d psi/dy, v = -d psi/dx, written out term by term.
+def kinematic_velocity(x, y, t, alpha, k, eps, omega, phi=0.0):
+    """(u, v) of the oscillating Taylor-Green flow at points (x, y), time t."""
+    ax = k * (np.asarray(x, dtype=np.float64) - eps * np.sin(omega * t))
+    ay = k * (np.asarray(y, dtype=np.float64) - eps * np.sin(omega * t + phi))
+    return alpha * np.sin(ax) * np.cos(ay), -alpha * np.cos(ax) * np.sin(ay)
+
+
+def kinematic_fields(n, t, alpha, k, eps, omega, phi=0.0):
+    """u, v, psi and omega = -laplacian(psi) on the n x n grid ([j][i]) at time t."""
+    xs = np.arange(n) * (TWO_PI / n)
+    x, y = np.meshgrid(xs, xs)  # x varies along i (columns), y along j (rows)
+    ax = k * (x - eps * np.sin(omega * t))
+    ay = k * (y - eps * np.sin(omega * t + phi))
+    psi = (alpha / k) * np.sin(ax) * np.sin(ay)
+    u = alpha * np.sin(ax) * np.cos(ay)
+    v = -alpha * np.cos(ax) * np.sin(ay)
+    return {"u": u, "v": v, "psi": psi, "omega": 2.0 * k * k * psi}
+
+
+def tracers_rk4_analytic(dt, t, x, y, alpha, k, eps, omega, phi=0.0):
+    """One classical RK4 step (Eq. 12) of tracers in the prescribed field,
+    stages at t, t + dt/2, t + dt/2, t + dt; returns the new (x, y)."""
+    vel = lambda px, py, tt: kinematic_velocity(px, py, tt, alpha, k, eps, omega, phi)
+    k1 = vel(x, y, t)
+    k2 = vel(x + 0.5 * dt * k1[0], y + 0.5 * dt * k1[1], t + 0.5 * dt)
+    k3 = vel(x + 0.5 * dt * k2[0], y + 0.5 * dt * k2[1], t + 0.5 * dt)
+    k4 = vel(x + dt * k3[0], y + dt * k3[1], t + dt)
+    return (x + dt / 6.0 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]),
+            y + dt / 6.0 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]))
+
+
+class KinematicRun:
+    """Tracers in the prescribed kinematic flow by one of the three routes of
+    Sec. 5.2: "analytic" (the field at the particle), "velocity" (u, v on the
+    grid, interpolated in space and blended in time) or "psi" (the
+    streamfunction on the grid, interpolated, Eq. 11)."""
+
+    def __init__(self, n, dt, params, xy, approach="analytic", scheme=BILINEAR, prefilter=True):
+        self.n, self.dt, self.p = int(n), float(dt), dict(params)
+        self.p.setdefault("phi", 0.0)
+        self.approach, self.scheme, self.prefilter = approach, int(scheme), bool(prefilter)
+        xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+        self.x, self.y = xy[:, 0].copy(), xy[:, 1].copy()
+        self.x0, self.y0 = self.x.copy(), self.y.copy()
+        self.step_count = 0
+        self._level = self._grid(0.0) if approach != "analytic" else None
+
+    def _grid(self, t):
+        f = kinematic_fields(self.n, t, **self.p)
+        pre = self.scheme == BSPLINE and self.prefilter
+        fix = (lambda a: bspline_prefilter(a)) if pre else (lambda a: a)
+        if self.approach == "psi":
+            return fix(f["psi"])
+        return fix(f["u"]), fix(f["v"])
+
+    @property
+    def t(self):
+        return self.step_count * self.dt
+
+    def step(self, nsteps=1):
+        for _ in range(int(nsteps)):
+            t0 = self.t
+            if self.approach == "analytic":
+                self.x, self.y = tracers_rk4_analytic(self.dt, t0, self.x, self.y, **self.p)
+            else:
+                nxt = self._grid(t0 + self.dt)
+                if self.approach == "psi":
+                    tracers_rk4_psi(self.scheme, self.dt, self._level, nxt, self.x, self.y)
+                else:
+                    particles_rk4(self.scheme, self.dt, 0.0, self._level[0], self._level[1], nxt[0],
+                                  nxt[1], self.x, self.y)
+                self._level = nxt
+            self.step_count += 1
 
 
 # --- coupled driver (Algorithm 1) -------------------------------------------------

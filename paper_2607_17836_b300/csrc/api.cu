@@ -31,7 +31,9 @@ bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 const char* check_desc(const el_flow_desc* d) {
     if (!d) return "desc is NULL";
     if (!is_pow2(d->n) || d->n < 16 || d->n > 4096) return "n must be a power of two in [16, 4096]";
-    if (d->interp < 0 || d->interp > 2) return "interp must be 0, 1 or 2";
+    if (d->interp < 0 || d->interp > 3) return "interp must be 0, 1, 2 or 3";
+    if (d->interp == EL_ANALYTIC && d->tracer_velocity)
+        return "EL_ANALYTIC evaluates the velocity itself: tracer_velocity must be 0";
     if (!std::isfinite(d->nu) || d->nu < 0.0) return "nu must be finite and >= 0";
     if (!std::isfinite(d->dt) || d->dt <= 0.0) return "dt must be finite and > 0";
     if (d->ab2_mode != 0 && d->ab2_mode != 1) return "ab2_mode must be 0 or 1";
@@ -272,9 +274,11 @@ el_status build_graph(el_flow* f, int kind, int phase) {
     return EL_OK;
 }
 
+// Kinematic flows pass the step's time to their kernels as arguments, so
+// they run by direct launches.
 bool graphs_enabled(const el_flow* f) {
     static const bool no_graph = std::getenv("ELPATH_NO_GRAPH") != nullptr;
-    return f->stream != nullptr && !no_graph;
+    return f->stream != nullptr && !no_graph && !f->kinematic;
 }
 
 el_status run_step(el_flow* f, int kind, int64_t step) {
@@ -346,15 +350,29 @@ size_t el_workspace_bytes(const el_flow_desc* desc) {
     return carve(*desc, fft, nullptr, nullptr);
 }
 
-el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* dev_workspace,
-                         size_t workspace_bytes, void* cuda_stream, el_flow** out) {
+}  // extern "C"
+
+// Both creation calls: a solved flow from omega0, or (kin != NULL) the
+// prescribed kinematic flow.
+static el_status create_flow(const el_flow_desc* desc, const double* omega0, const el_kinematic* kin,
+                             void* dev_workspace, size_t workspace_bytes, void* cuda_stream,
+                             el_flow** out) {
     if (!out) return fail(nullptr, EL_EINVAL, "out is NULL");
     *out = nullptr;
     if (const char* why = check_desc(desc)) return fail(nullptr, EL_EINVAL, "%s", why);
-    if (!omega0) return fail(nullptr, EL_EINVAL, "omega0 is NULL");
+    if (!kin && desc->interp == EL_ANALYTIC)
+        return fail(nullptr, EL_EINVAL, "EL_ANALYTIC needs a kinematic flow (el_create_kinematic)");
+    if (kin) {
+        const bool ok = std::isfinite(kin->alpha) && std::isfinite(kin->k) && std::isfinite(kin->eps) &&
+                        std::isfinite(kin->omega) && std::isfinite(kin->phi) && kin->k >= 1.0 &&
+                        kin->k == std::floor(kin->k) && 3.0 * kin->k < desc->n;
+        if (!ok) return fail(nullptr, EL_EINVAL, "kinematic parameters: finite, k an integer in [1, n/3)");
+    } else if (!omega0) {
+        return fail(nullptr, EL_EINVAL, "omega0 is NULL");
+    }
     if (!dev_workspace) return fail(nullptr, EL_EINVAL, "workspace is NULL");
     if ((uintptr_t)dev_workspace % kAlign) return fail(nullptr, EL_EINVAL, "workspace not 256-byte aligned");
-    for (size_t q = 0, nn = (size_t)desc->n * desc->n; q < nn; q++)
+    for (size_t q = 0, nn = omega0 ? (size_t)desc->n * desc->n : 0; q < nn; q++)
         if (!std::isfinite(omega0[q])) return fail(nullptr, EL_EINVAL, "omega0 has a non-finite value");
     size_t fft = 0;
     if (!fft_work_bytes(desc->n, planes_of(*desc), &fft))
@@ -366,6 +384,10 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     el_flow* f = new (std::nothrow) el_flow();
     if (!f) return fail(nullptr, EL_ENOMEM, "host allocation failed");
     f->d = *desc;
+    if (kin) {
+        f->kinematic = 1;
+        f->kin = *kin;
+    }
     f->stream = (cudaStream_t)cuda_stream;
     f->own_stream = f->stream;
     cudaGetDevice(&f->device);
@@ -427,7 +449,7 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
         fail(f, EL_ECUDA, "table upload: %s", cudaGetErrorString(e));
         return bail(EL_ECUDA);
     }
-    el_status s = fluid_init(f, omega0);
+    el_status s = kin ? kinematic_level(f, 0, true) : fluid_init(f, omega0);
     if (s != EL_OK) return bail(s);
     e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) {
@@ -438,6 +460,22 @@ el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* d
     return EL_OK;
 }
 
+extern "C" {
+
+el_status el_create_flow(const el_flow_desc* desc, const double* omega0, void* dev_workspace,
+                         size_t workspace_bytes, void* cuda_stream, el_flow** out) {
+    return create_flow(desc, omega0, nullptr, dev_workspace, workspace_bytes, cuda_stream, out);
+}
+
+el_status el_create_kinematic(const el_flow_desc* desc, const el_kinematic* kin, void* dev_workspace,
+                              size_t workspace_bytes, void* cuda_stream, el_flow** out) {
+    if (!kin) {
+        if (out) *out = nullptr;
+        return fail(nullptr, EL_EINVAL, "kin is NULL");
+    }
+    return create_flow(desc, nullptr, kin, dev_workspace, workspace_bytes, cuda_stream, out);
+}
+
 el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, const double* xy,
                            const double* vxy) {
     if (!f) return EL_EINVAL;
@@ -445,6 +483,8 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
         return fail(f, EL_EINVAL, "species %d outside [0, %d)", species, f->d.max_species);
     if (np < 0 || np > f->d.max_particles) return fail(f, EL_EINVAL, "np %lld out of range", (long long)np);
     if (!std::isfinite(st) || st < 0.0) return fail(f, EL_EINVAL, "st must be finite and >= 0");
+    if (f->d.interp == EL_ANALYTIC && st > 0.0)
+        return fail(f, EL_EINVAL, "EL_ANALYTIC flows take tracers (st = 0) only");
     if (np > 0 && !xy) return fail(f, EL_EINVAL, "xy is NULL");
     for (int64_t q = 0; q < 2 * np; q++)
         if (!std::isfinite(xy[q]) || std::fabs(xy[q]) > 1e9)
@@ -495,14 +535,15 @@ el_status el_step_coupled(el_flow* f, int32_t nsteps) {
 
 el_status el_get_stats(el_flow* f, el_stats* out) {
     if (!f || !out) return EL_EINVAL;
-    EL_TRY(fluid_diagnostics(f));
+    if (!f->kinematic) EL_TRY(fluid_diagnostics(f));
     int ns = f->d.max_species;
     for (int s = 0; s < ns; s++)
-        if (f->sp[s].np > 0) EL_TRY(particles_stats_into(f, s, f->red_out + 3 + 3 * s));
-    double host[3 + 3 * EL_MAX_SPECIES] = {0};
-    EL_CUDA_OK(f, cudaMemcpyAsync(host, f->red_out, sizeof(double) * (3 + 3 * ns), cudaMemcpyDeviceToHost,
+        if (f->sp[s].np > 0) EL_TRY(particles_stats_into(f, s, f->red_out + 3 + 5 * s));
+    double host[3 + 5 * EL_MAX_SPECIES] = {0};
+    EL_CUDA_OK(f, cudaMemcpyAsync(host, f->red_out, sizeof(double) * (3 + 5 * ns), cudaMemcpyDeviceToHost,
                                   f->stream));
     EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
+    if (f->kinematic) kinematic_diagnostics(f, host);
     *out = el_stats{};
     out->t = (double)f->step * f->d.dt;
     out->step = f->step;
@@ -513,10 +554,20 @@ el_status el_get_stats(el_flow* f, el_stats* out) {
     for (int s = 0; s < ns; s++) {
         out->np[s] = f->sp[s].np;
         if (f->sp[s].np == 0) continue;
-        out->msd[s][0] = host[3 + 3 * s];
-        out->msd[s][1] = host[4 + 3 * s];
-        out->cluster[s] = host[5 + 3 * s];
-        finite = finite && std::isfinite(host[3 + 3 * s]) && std::isfinite(host[4 + 3 * s]);
+        const double* h = host + 3 + 5 * s;
+        out->msd[s][0] = h[0];
+        out->msd[s][1] = h[1];
+        out->cluster[s] = h[2];
+        // standard error of the mean squared displacement per axis: the
+        // sample variance of the squared displacements over np particles,
+        // np / (np - 1) (<d^4> - <d^2>^2), divided by np
+        const double np = (double)f->sp[s].np;
+        for (int a = 0; a < 2; a++) {
+            const double var = np > 1.0 ? std::max(0.0, h[3 + a] - h[a] * h[a]) / (np - 1.0) : 0.0;
+            out->msd_sem[s][a] = std::sqrt(var);
+            out->diffusivity[s][a] = out->t > 0.0 ? h[a] / (2.0 * out->t) : 0.0;
+        }
+        finite = finite && std::isfinite(h[0]) && std::isfinite(h[1]);
     }
     out->finite = finite ? 1 : 0;
     if (!finite) return fail(f, EL_ENONFINITE, "non-finite diagnostics at step %lld", (long long)f->step);
@@ -540,6 +591,7 @@ el_status el_sample_velocity(el_flow* f, int64_t np, const double* d_xy, double 
     if (!f) return EL_EINVAL;
     if (np < 0 || (np > 0 && (!d_xy || !d_uv))) return fail(f, EL_EINVAL, "bad sample arrays");
     if (!(theta >= 0.0 && theta <= 1.0)) return fail(f, EL_EINVAL, "theta must be in [0, 1]");
+    if (f->d.interp == EL_ANALYTIC) return fail(f, EL_EINVAL, "EL_ANALYTIC has no grid interpolant");
     return sample_velocity(f, np, d_xy, theta, d_uv);
 }
 

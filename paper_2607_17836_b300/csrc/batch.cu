@@ -435,6 +435,7 @@ el_status el_batch_create(int32_t max_members, void* dev_workspace, size_t bytes
 el_status el_batch_add(el_batch* b, el_flow* f) {
     if (!b || !f) return EL_EINVAL;
     if (f->batch) return bfail(b, EL_ESTATE, "flow already belongs to a batch");
+    if (f->kinematic) return bfail(b, EL_EINVAL, "kinematic flows step alone");
     if ((int)b->members.size() >= b->max_members) return bfail(b, EL_EINVAL, "batch is full");
     int dev = 0;
     cudaGetDevice(&dev);

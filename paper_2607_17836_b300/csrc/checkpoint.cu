@@ -28,7 +28,7 @@ using namespace el;
 namespace {
 
 constexpr char kMagic[8] = {'E', 'L', 'S', 'T', 'A', 'T', 'E', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 
 struct CkptHeader {
     char magic[8];
@@ -40,6 +40,9 @@ struct CkptHeader {
     int64_t since_sort;
     int64_t np[EL_MAX_SPECIES];
     double st[EL_MAX_SPECIES];
+    int32_t kinematic;          // 1: the prescribed field of Sec. 5.2 (parameters below)
+    int32_t reserved;
+    el_kinematic kin;
 };
 
 uint64_t fnv1a(const unsigned char* p, size_t n) {
@@ -90,10 +93,13 @@ size_t image_bytes(const std::vector<Section>& s) {
     return b + sizeof(uint64_t);
 }
 
-bool same_desc(const el_flow_desc& a, const el_flow_desc& b) {
+bool same_flow(const CkptHeader& h, const el_flow* f) {
+    const el_flow_desc &a = h.desc, &b = f->d;
     return a.n == b.n && a.interp == b.interp && std::memcmp(&a.nu, &b.nu, sizeof(double)) == 0 &&
            std::memcmp(&a.dt, &b.dt, sizeof(double)) == 0 && a.ab2_mode == b.ab2_mode &&
-           a.bspline_prefilter == b.bspline_prefilter && a.tracer_velocity == b.tracer_velocity;
+           a.bspline_prefilter == b.bspline_prefilter && a.tracer_velocity == b.tracer_velocity &&
+           h.kinematic == f->kinematic &&
+           (!f->kinematic || std::memcmp(&h.kin, &f->kin, sizeof(el_kinematic)) == 0);
 }
 
 }  // namespace
@@ -109,6 +115,8 @@ el_status el_save_state(el_flow* f, void* host_buf, size_t* bytes) {
     h.desc = f->d;
     h.step = f->step;
     h.since_sort = f->since_sort;
+    h.kinematic = f->kinematic;
+    h.kin = f->kin;
     for (int k = 0; k < f->d.max_species; k++) {
         h.np[k] = f->sp[k].np;
         h.st[k] = f->sp[k].st;
@@ -156,8 +164,9 @@ el_status el_load_state(el_flow* f, const void* host_buf, size_t bytes) {
     uint64_t sum = 0;
     std::memcpy(&sum, in + bytes - sizeof sum, sizeof sum);
     if (fnv1a(in, bytes - sizeof sum) != sum) return fail(f, EL_EINVAL, "state image checksum mismatch");
-    if (!same_desc(h.desc, f->d))
-        return fail(f, EL_EINVAL, "state image was saved by a flow with another n, scheme, nu, dt or mode");
+    if (!same_flow(h, f))
+        return fail(f, EL_EINVAL,
+                    "state image was saved by a flow with another n, scheme, nu, dt, mode or field");
     if (h.step < 0 || h.since_sort < 0) return fail(f, EL_EINVAL, "state image has a negative step");
     for (int k = 0; k < EL_MAX_SPECIES; k++) {
         if (h.np[k] < 0 || (h.np[k] > 0 && k >= f->d.max_species))

@@ -117,6 +117,9 @@ struct el_flow {
     cudaStream_t side = nullptr;       // second branch of the overlapped step
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
+    int kinematic = 0;         // 1: the prescribed field of Sec. 5.2 replaces the solver
+    el_kinematic kin{};
+
     std::string err;
 };
 
@@ -157,6 +160,12 @@ el_status fail(el_flow* f, el_status s, const char* fmt, ...);
 el_status fluid_init(el_flow* f, const double* omega0_host);
 el_status fluid_step(el_flow* f, int64_t step);   // K5+K1, C2R, K3, R2C
 el_status fluid_diagnostics(el_flow* f);          // E, Z, P -> red_out[0..2]
+// ---- prescribed kinematic flow (kinematic.cu) --------------------------------------
+struct KinArgs;
+KinArgs kinematic_stage_args(const el_flow* f, int64_t step);  // the field at RK4 stage times
+el_status kinematic_level(el_flow* f, int64_t m, bool setup);  // level m into its pair
+el_status kinematic_get_field(el_flow* f, int which, double* host_nn);  // omega, u, v at t_n
+void kinematic_diagnostics(const el_flow* f, double* e3);  // exact E, Z, P
 el_status fluid_refresh_planes(el_flow* f);       // physical planes of the current level
 el_status fluid_get_field(el_flow* f, int which, double* host_nn);
 
@@ -165,7 +174,8 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
                         const double* vxy);
 el_status particles_step_all(el_flow* f, int64_t step);  // K6, every species in one launch
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
-el_status particles_stats_into(el_flow* f, int s, double* out3);  // msd x, msd y, cluster
+// msd x, msd y, cluster, <dx^4>, <dy^4> (the squared displacements' second moments)
+el_status particles_stats_into(el_flow* f, int s, double* out5);
 el_status sample_velocity(el_flow* f, int64_t np, const double* d_xy, double theta, double* d_uv);
 
 void drop_graphs(el_flow* f);                     // api.cu

@@ -213,6 +213,7 @@ el_status fluid_init(el_flow* f, const double* omega0_host) {
 
 // Fluid n -> n+1 for step number n = `step`.
 el_status fluid_step(el_flow* f, int64_t step) {
+    if (f->kinematic) return kinematic_level(f, step + 1, false);
     k_spectral<true><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, step == 0));
     EL_LAUNCHED(f);
     return finish_rhs(f, step + 1, false);
@@ -221,6 +222,7 @@ el_status fluid_step(el_flow* f, int64_t step) {
 // The physical planes (u, v, ...) of the current level from omega-hat,
 // without touching N-hat or the level pairs (after a state was loaded).
 el_status fluid_refresh_planes(el_flow* f) {
+    if (f->kinematic) return EL_OK;  // nothing spectral to rebuild
     k_spectral<false><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, 0));
     EL_LAUNCHED(f);
     return fft_exec_c2r(f, f->plan_c2r, f->spec, f->phys);
@@ -237,6 +239,7 @@ el_status fluid_diagnostics(el_flow* f) {
 }
 
 el_status fluid_get_field(el_flow* f, int which, double* host_nn) {
+    if (f->kinematic && which <= 2) return kinematic_get_field(f, which, host_nn);
     const int T = 256;
     double* out = f->stage64;
     if (which == 0) {

@@ -119,12 +119,26 @@ __device__ __forceinline__ void cubic_weights2(float2 s, float2 w[4]) {
 // loaded once and re-used, and only a stage that crosses into another cell
 // fetches again.  (ci, cj) are the cell's unwrapped indices; addresses wrap.
 // THETA: 0 = level n, 1 = mid-way (theta = 1/2), 2 = level n+1 (Eq. 23).
+// The prescribed kinematic velocity of Sec. 5.2 at the three RK4 stage
+// times (t_n, t_n + dt/2, t_n + dt): u = alpha sin(k x - sx) cos(k y - sy),
+// v = -alpha cos(k x - sx) sin(k y - sy), with sx = k eps sin(omega t) and
+// sy = k eps sin(omega t + phi) computed on the host in FP64.
+struct KinArgs {
+    float alpha;         // peak speed
+    float dk;            // 2 pi / n: radians per grid unit at unit wavenumber
+    float sx[3], sy[3];  // phase shifts at the stage times
+    int kw;              // integer wavenumber k
+    int mask;            // n - 1
+};
+
 template <int SCHEME>
 struct Stencil {
     static constexpr int W = SCHEME == 0 ? 2 : 4;
     static constexpr int O = SCHEME == 0 ? 0 : -1;  // first node relative to the cell
     int ci, cj;
     float4 v[W * W];
+
+    __device__ __forceinline__ void bind(const KinArgs*) {}
 
     __device__ __forceinline__ void load(const float4* __restrict__ snap, int n, int i, int j) {
         const int m = n - 1;
@@ -189,6 +203,38 @@ struct Stencil {
         int i = ci0 + (int)flx, j = cj0 + (int)fly;
         if (i != ci || j != cj) load(snap, n, i, j);
         return eval<THETA>(fsub2(l, make_float2(flx, fly)));
+    }
+};
+
+// EL_ANALYTIC: the kinematic field itself at the particle (no grid, no
+// stencil); THETA selects the stage time.  The integer part of k x in grid
+// units is reduced modulo n exactly before the phase is formed.
+template <>
+struct Stencil<3> {
+    const KinArgs* kin;
+    int ci, cj;
+
+    __device__ __forceinline__ void bind(const KinArgs* k) { kin = k; }
+    __device__ __forceinline__ void load(const float4*, int, int i, int j) {
+        ci = i;
+        cj = j;
+    }
+    template <int THETA>
+    __device__ __forceinline__ float2 value(int i, int j, float2 l) const {
+        const float fx = (float)((kin->kw * i) & kin->mask) + (float)kin->kw * l.x;
+        const float fy = (float)((kin->kw * j) & kin->mask) + (float)kin->kw * l.y;
+        float snx, csx, sny, csy;
+        sincosf(fmaf(kin->dk, fx, -kin->sx[THETA]), &snx, &csx);
+        sincosf(fmaf(kin->dk, fy, -kin->sy[THETA]), &sny, &csy);
+        return make_float2(kin->alpha * snx * csy, -kin->alpha * csx * sny);
+    }
+    template <int THETA>
+    __device__ __forceinline__ float2 first_stage(float2 o) const {
+        return value<THETA>(ci, cj, o);
+    }
+    template <int THETA>
+    __device__ __forceinline__ float2 at(const float4*, int, int ci0, int cj0, float2 l) {
+        return value<THETA>(ci0, cj0, l);
     }
 };
 

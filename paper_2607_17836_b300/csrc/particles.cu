@@ -39,6 +39,7 @@ struct RK4Args {
     int n, log2n, nspecies;
     float dt, h;              // h = dt * n / (2 pi): grid units per unit velocity
     unsigned block_begin[kMaxSpecies];
+    KinArgs kin;              // EL_ANALYTIC only: the prescribed field at the stage times
 };
 
 // K6: one RK4 step of every species in one launch (blocks are split between
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_
     const SpeciesDev& sd = a.table[s];
     const int p = (int)(blockIdx.x - a.block_begin[s]) * (int)blockDim.x + (int)threadIdx.x;
     if (p >= sd.np) return;
-    rk4_particle<SCHEME, PSI>(a.snap, a.psi, a.n, a.log2n, a.dt, a.h, sd, p);
+    rk4_particle<SCHEME, PSI>(a.snap, a.psi, a.n, a.log2n, a.dt, a.h, sd, p, &a.kin);
 }
 
 // FP64 position -> (cell, offset, image), Sec. 3.2: mapped periodically onto
@@ -147,14 +148,16 @@ __global__ void k_unsplit(const uint32_t* __restrict__ cell, const float2* __res
 __global__ void k_msd(const uint32_t* __restrict__ cell, const float2* __restrict__ off,
                       const int2* __restrict__ img, const uint32_t* __restrict__ id,
                       const double2* __restrict__ x0, int64_t np, double dx,
-                      double2* __restrict__ out) {
+                      double2* __restrict__ out, double2* __restrict__ out2) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     uint32_t k = id[p];
     double2 x = unwrapped(cell[p], off[p], img[p], dx);
     double2 r = x0[k];
     double ddx = x.x - r.x, ddy = x.y - r.y;
-    out[k] = make_double2(ddx * ddx, ddy * ddy);
+    const double sx = ddx * ddx, sy = ddy * ddy;
+    out[k] = make_double2(sx, sy);          // squared displacement per axis
+    out2[k] = make_double2(sx * sx, sy * sy);  // its square (for the standard error)
 }
 
 // Particle counts on the kBoxes x kBoxes box grid (integer atomics: exact).
@@ -304,7 +307,10 @@ el_status particles_step_all(el_flow* f, int64_t step) {
     // empty slots share block_begin with the next slot, so the last slot with
     // a given block_begin (the non-empty one) wins the select in the kernel
     const int T = f->rk4_threads;
-    if (f->psi_plane < 0) {
+    if (f->d.interp == EL_ANALYTIC) {
+        a.kin = kinematic_stage_args(f, step);
+        k_rk4<3, false><<<blocks, T, 0, f->stream>>>(a);
+    } else if (f->psi_plane < 0) {
         switch (f->d.interp) {
             case EL_BILINEAR: k_rk4<0, false><<<blocks, T, 0, f->stream>>>(a); break;
             case EL_CATMULL_ROM: k_rk4<1, false><<<blocks, T, 0, f->stream>>>(a); break;
@@ -345,15 +351,20 @@ el_status particles_get(el_flow* f, int s, double* xy, double* vxy) {
 
 // Mean-square displacement (out3[0], out3[1]) and clustering index (out3[2])
 // of species s, into device memory.
-el_status particles_stats_into(el_flow* f, int s, double* out3) {
+el_status particles_stats_into(el_flow* f, int s, double* out5) {
     Species& sp = f->sp[s];
     const int T = 256;
     const int cur = sp.cur;
+    // the sort buffer holds 32 bytes per particle: both term arrays fit
     double2* terms = reinterpret_cast<double2*>(sp.cell[cur ^ 1]);
+    double2* terms2 = terms + sp.np;
     k_msd<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[cur], sp.off[cur], sp.img[cur],
-                                                     sp.id[cur], sp.x0, sp.np, kTwoPi / f->n, terms);
+                                                     sp.id[cur], sp.x0, sp.np, kTwoPi / f->n, terms,
+                                                     terms2);
     EL_LAUNCHED(f);
-    EL_TRY(reduce_double2(f, terms, sp.np, out3));
+    EL_TRY(reduce_double2(f, terms, sp.np, out5));
+    EL_TRY(reduce_double2(f, terms2, sp.np, out5 + 3));
+    double* out3 = out5;
     EL_CUDA_OK(f, cudaMemsetAsync(f->boxes, 0, sizeof(unsigned long long) * kBoxes * kBoxes,
                                   f->stream));
     k_box<<<blocks_for(sp.np, T), T, 0, f->stream>>>(sp.cell[cur], sp.off[cur], sp.np, f->n,

@@ -215,7 +215,8 @@ __device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off
 template <int SCHEME, bool PSI>
 __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
                                              const float2* __restrict__ psi, int n, int log2n,
-                                             float dt, float h, const SpeciesDev& sd, int p) {
+                                             float dt, float h, const SpeciesDev& sd, int p,
+                                             const KinArgs* kin = nullptr) {
     const int cur = sd.cur;
     uint32_t* __restrict__ cellp = sd.cell[cur];
     float2* __restrict__ offp = sd.off[cur];
@@ -225,6 +226,7 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
     const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
     const float2 o = EL_STATE_LD(offp + p);
     Stencil<SCHEME> st;
+    st.bind(kin);  // the prescribed field of EL_ANALYTIC; unused by the grid schemes
     st.load(snap, n, ci, cj);
     const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
     const float2 two = make_float2(2.0f, 2.0f);

@@ -15,13 +15,14 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libelpath.so")
 
-BILINEAR, CATMULL_ROM, BSPLINE = 0, 1, 2
+BILINEAR, CATMULL_ROM, BSPLINE, ANALYTIC = 0, 1, 2, 3
 MAX_SPECIES = 8
 STATUS = {0: "EL_OK", 1: "EL_EINVAL", 2: "EL_ENOMEM", 3: "EL_ECUDA", 4: "EL_ECUFFT",
           5: "EL_ESTATE", 6: "EL_ENONFINITE", 7: "EL_ETIMEOUT"}
 
 # Public C symbols, in include/elpath.h order.
-SYMBOLS = ("el_workspace_bytes", "el_create_flow", "el_set_particles", "el_step_coupled",
+SYMBOLS = ("el_workspace_bytes", "el_create_flow", "el_create_kinematic", "el_set_particles",
+           "el_step_coupled",
            "el_get_stats", "el_get_particles", "el_get_field", "el_sample_velocity",
            "el_profile_step", "el_get_tuning", "el_set_tuning", "el_autotune",
            "el_kernel_launches", "el_batch_workspace_bytes", "el_batch_create", "el_batch_add",
@@ -51,12 +52,18 @@ class el_tuning(ctypes.Structure):
                 ("sort_shift", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
 
 
+class el_kinematic(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("k", ctypes.c_double), ("eps", ctypes.c_double),
+                ("omega", ctypes.c_double), ("phi", ctypes.c_double)]
+
+
 class el_stats(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_int64), ("energy", ctypes.c_double),
                 ("enstrophy", ctypes.c_double), ("palinstrophy", ctypes.c_double),
                 ("msd", (ctypes.c_double * 2) * MAX_SPECIES),
                 ("cluster", ctypes.c_double * MAX_SPECIES), ("np", ctypes.c_int64 * MAX_SPECIES),
-                ("finite", ctypes.c_int32)]
+                ("finite", ctypes.c_int32), ("msd_sem", (ctypes.c_double * 2) * MAX_SPECIES),
+                ("diffusivity", (ctypes.c_double * 2) * MAX_SPECIES)]
 
 
 _lib = None
@@ -77,6 +84,9 @@ def load(path: str = LIB_PATH):
     lib.el_workspace_bytes.restype = ctypes.c_size_t
     lib.el_create_flow.argtypes = [ctypes.POINTER(el_flow_desc), D, V, ctypes.c_size_t, V,
                                    ctypes.POINTER(P)]
+    lib.el_create_kinematic.argtypes = [ctypes.POINTER(el_flow_desc), ctypes.POINTER(el_kinematic),
+                                        V, ctypes.c_size_t, V, ctypes.POINTER(P)]
+    lib.el_create_kinematic.restype = ctypes.c_int
     lib.el_set_particles.argtypes = [P, I32, I64, ctypes.c_double, D, D]
     lib.el_step_coupled.argtypes = [P, I32]
     lib.el_get_stats.argtypes = [P, ctypes.POINTER(el_stats)]
@@ -170,7 +180,10 @@ class Flow:
 
     def __init__(self, n, nu, dt, omega0, interp=BILINEAR, ab2_mode=0, bspline_prefilter=True,
                  max_species=0, max_particles=0, sort_every=0, stream=None, device=None,
-                 workspace=None, tracer_velocity=0):
+                 workspace=None, tracer_velocity=0, kinematic=None):
+        """omega0: initial vorticity (n x n) of a solved flow; or, with
+        kinematic = dict(alpha=, k=, eps=, omega=, phi=), the prescribed
+        oscillating Taylor-Green field (el_create_kinematic; omega0 unused)."""
         import torch
         lib = load()
         self._lib = lib
@@ -185,15 +198,25 @@ class Flow:
             workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.workspace = workspace
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
-        w0 = _host_f64(omega0)
-        if w0.shape != (self.n, self.n):
-            raise ValueError(f"omega0 must be {self.n}x{self.n}")
         h = ctypes.c_void_p()
-        with torch.cuda.device(self.device):
-            st = lib.el_create_flow(ctypes.byref(self.desc), _dptr(w0),
-                                    ctypes.c_void_p(workspace.data_ptr()),
-                                    ctypes.c_size_t(workspace.numel()),
-                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if kinematic is not None:
+            kin = el_kinematic(float(kinematic["alpha"]), float(kinematic["k"]),
+                               float(kinematic["eps"]), float(kinematic["omega"]),
+                               float(kinematic.get("phi", 0.0)))
+            with torch.cuda.device(self.device):
+                st = lib.el_create_kinematic(ctypes.byref(self.desc), ctypes.byref(kin),
+                                             ctypes.c_void_p(workspace.data_ptr()),
+                                             ctypes.c_size_t(workspace.numel()),
+                                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        else:
+            w0 = _host_f64(omega0)
+            if w0.shape != (self.n, self.n):
+                raise ValueError(f"omega0 must be {self.n}x{self.n}")
+            with torch.cuda.device(self.device):
+                st = lib.el_create_flow(ctypes.byref(self.desc), _dptr(w0),
+                                        ctypes.c_void_p(workspace.data_ptr()),
+                                        ctypes.c_size_t(workspace.numel()),
+                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         if st != 0:
             raise ElpathError(st, lib.el_last_error(None).decode())
         self._h = h
@@ -242,7 +265,10 @@ class Flow:
                 "palinstrophy": s.palinstrophy,
                 "msd": [(s.msd[k][0], s.msd[k][1]) for k in range(MAX_SPECIES)],
                 "cluster": [s.cluster[k] for k in range(MAX_SPECIES)],
-                "np": [s.np[k] for k in range(MAX_SPECIES)], "finite": bool(s.finite)}
+                "np": [s.np[k] for k in range(MAX_SPECIES)], "finite": bool(s.finite),
+                "msd_sem": [(s.msd_sem[k][0], s.msd_sem[k][1]) for k in range(MAX_SPECIES)],
+                "diffusivity": [(s.diffusivity[k][0], s.diffusivity[k][1])
+                                for k in range(MAX_SPECIES)]}
 
     def particles(self, species, count):
         xy = np.empty((count, 2))

@@ -51,8 +51,9 @@ int main(void) {{
   printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(el_flow_desc), offsetof(el_flow_desc, nu),
          offsetof(el_flow_desc, dt), offsetof(el_flow_desc, max_particles),
          offsetof(el_flow_desc, sort_every), offsetof(el_flow_desc, tracer_velocity));
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(el_stats), offsetof(el_stats, msd),
-         offsetof(el_stats, cluster), offsetof(el_stats, np), offsetof(el_stats, finite));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(el_stats), offsetof(el_stats, msd),
+         offsetof(el_stats, cluster), offsetof(el_stats, np), offsetof(el_stats, finite),
+         offsetof(el_stats, msd_sem), offsetof(el_stats, diffusivity));
   return 0;
 }}
 """)
@@ -64,7 +65,8 @@ int main(void) {{
     D, S = elpath.el_flow_desc, elpath.el_stats
     assert d == [ctypes.sizeof(D), D.nu.offset, D.dt.offset, D.max_particles.offset,
                  D.sort_every.offset, D.tracer_velocity.offset]
-    assert s == [ctypes.sizeof(S), S.msd.offset, S.cluster.offset, S.np.offset, S.finite.offset]
+    assert s == [ctypes.sizeof(S), S.msd.offset, S.cluster.offset, S.np.offset, S.finite.offset,
+                 S.msd_sem.offset, S.diffusivity.offset]
 
 
 def test_calls_without_device_fail_cleanly(lib):

@@ -180,3 +180,35 @@ def test_streamfunction_and_velocity_tracers_agree_short_time():
     b.step(100)
     d = np.hypot(a.species[0].x - b.species[0].x, a.species[0].y - b.species[0].y)
     assert 1e-6 < d.max() < 1e-3   # paths differ, by O(dx^2) of the distance travelled
+
+
+def test_msd_standard_error_against_the_statistics_module_and_closed_forms():
+    import statistics
+    rng = np.random.default_rng(11)
+    x0, y0 = rng.uniform(0, 6, 257), rng.uniform(0, 6, 257)
+    x, y = x0 + rng.normal(0, 0.7, 257), y0 + rng.normal(0, 1.3, 257)
+    sx, sy = oracle.msd_sem(x, y, x0, y0)
+    for got, d in ((sx, x - x0), (sy, y - y0)):
+        q = [float(v) * float(v) for v in d]
+        assert got == pytest.approx(statistics.stdev(q) / np.sqrt(len(q)), rel=1e-12)
+    # every particle displaced alike: no spread (up to the rounding of x0 + d - x0)
+    assert oracle.msd_sem(x0 + 0.4, y0 - 2.0, x0, y0) == pytest.approx((0.0, 0.0), abs=1e-15)
+    # half displaced by a, half not: squared displacements a^2 and 0,
+    # sample variance n a^4 / (4 (n - 1)), standard error a^2 / (2 sqrt(n - 1))
+    n, a = 100, 0.3
+    xs = np.zeros(n)
+    xs[: n // 2] = a
+    sx, sy = oracle.msd_sem(xs, np.zeros(n), np.zeros(n), np.zeros(n))
+    assert sx == pytest.approx(a * a / (2.0 * np.sqrt(n - 1)), rel=1e-12) and sy == 0.0
+    assert oracle.msd_sem([1.0], [2.0], [0.0], [0.0]) == (0.0, 0.0)
+
+
+def test_diffusivity_of_ballistic_motion():
+    # x = x0 + U t: msd = U^2 t^2, so D = U^2 t / 2
+    t, ux, uy = 3.5, 0.2, -1.1
+    x0 = np.linspace(0, 1, 50)
+    m = oracle.msd(x0 + ux * t, x0 + uy * t, x0, x0)
+    dxy = oracle.diffusivity(m, t)
+    assert dxy[0] == pytest.approx(ux * ux * t / 2, rel=1e-12)
+    assert dxy[1] == pytest.approx(uy * uy * t / 2, rel=1e-12)
+    assert oracle.diffusivity(m, 0.0) == (0.0, 0.0)
