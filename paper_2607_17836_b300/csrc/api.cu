@@ -218,17 +218,36 @@ enum { kFluidStep = 0, kParticleStep = 1, kOverlapStep = 2 };
 // on a forked branch alongside the fluid step of n+1.  The two are
 // independent: particles of step n read the level pair (n, n+1); the fluid
 // step of n+1 only reads that pair's second half and writes pair (n+1, n+2).
+#ifndef EL_FLUID_BRANCH_PRIORITY
+#define EL_FLUID_BRANCH_PRIORITY 1
+#endif
+
 el_status enqueue_step(el_flow* f, int kind, int64_t step) {
     if (kind == kFluidStep) return fluid_step(f, step);
     if (kind == kParticleStep) return particles_step_all(f, step);
     EL_CUDA_OK(f, cudaEventRecord(f->ev_fork, f->stream));
     EL_CUDA_OK(f, cudaStreamWaitEvent(f->side, f->ev_fork, 0));
     cudaStream_t main = f->stream;
+#if EL_FLUID_BRANCH_PRIORITY
+    // The fluid chain (several short kernels) goes on the high-priority side
+    // branch, so its blocks are dispatched as soon as the particle kernel's
+    // blocks free an SM instead of after the particle kernel.
+    EL_TRY(particles_step_all(f, step));
+    f->stream = f->side;
+    cufftSetStream(f->plan_c2r, f->side);
+    cufftSetStream(f->plan_r2c, f->side);
+    el_status s = fluid_step(f, step + 1);
+    cufftSetStream(f->plan_c2r, main);
+    cufftSetStream(f->plan_r2c, main);
+    f->stream = main;
+    EL_TRY(s);
+#else
     f->stream = f->side;
     el_status s = particles_step_all(f, step);
     f->stream = main;
     EL_TRY(s);
     EL_TRY(fluid_step(f, step + 1));
+#endif
     EL_CUDA_OK(f, cudaEventRecord(f->ev_join, f->side));
     EL_CUDA_OK(f, cudaStreamWaitEvent(f->stream, f->ev_join, 0));
     return EL_OK;
@@ -266,7 +285,8 @@ el_status build_graph(el_flow* f, int kind, int phase) {
         return s;
     }
     if (e != cudaSuccess) return fail(f, EL_ECUDA, "stream capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(slot, g, 0);
+    // kernel nodes keep the priority of the stream they were captured on
+    e = cudaGraphInstantiate(slot, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(f, EL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     *count = f->launches - before;
@@ -414,7 +434,10 @@ static el_status create_flow(const el_flow_desc* desc, const double* omega0, con
         return s;
     };
     if (f->stream) {
-        cudaError_t es = cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking);
+        int lo_prio = 0, hi_prio = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        cudaError_t es = cudaStreamCreateWithPriority(&f->side, cudaStreamNonBlocking,
+                                                      EL_FLUID_BRANCH_PRIORITY ? hi_prio : lo_prio);
         if (es == cudaSuccess) es = cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming);
         if (es == cudaSuccess) es = cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming);
         if (es != cudaSuccess) {
