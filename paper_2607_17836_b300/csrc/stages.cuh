@@ -206,46 +206,43 @@ __device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off
     off = o;
 }
 
-// One RK4 step of particle p of species sd (Eq. 12 tracers, Eq. 14 inertial)
-// between levels n and n+1, read from their level pair `snap`: stage 1
-// (theta = 0) and stage 4 (theta = 1) read one half of each node without
-// blending.  All (x, y) and (u, v) arithmetic is on float pairs (one paired
-// FP32 instruction per two lanes of work).  h = dt * n / (2 pi): grid units
-// per unit velocity.
-template <int SCHEME, bool PSI>
-__device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
-                                             const float2* __restrict__ psi, int n, int log2n,
-                                             float dt, float h, const SpeciesDev& sd, int p,
-                                             const KinArgs* kin = nullptr) {
-    const int cur = sd.cur;
-    uint32_t* __restrict__ cellp = sd.cell[cur];
-    float2* __restrict__ offp = sd.off[cur];
-    // the particle state is streamed once per step: evict-first loads and
-    // stores keep the caches for the level pair the gathers re-read
-    const uint32_t c = EL_STATE_LD(cellp + p);
-    const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
-    const float2 o = EL_STATE_LD(offp + p);
+// A particle between the load of its state and stencil and its update.
+template <int SCHEME>
+struct ParticleRK4 {
+    int p, ci, cj;
+    float2 o, v;
     Stencil<SCHEME> st;
-    st.bind(kin);  // the prescribed field of EL_ANALYTIC; unused by the grid schemes
-    st.load(snap, n, ci, cj);
+};
+
+// The particle state (streamed once per step: evict-first loads keep the
+// caches for the level pair the gathers re-read).
+template <int SCHEME>
+__device__ __forceinline__ void rk4_load_state(const SpeciesDev& sd, int p, ParticleRK4<SCHEME>& q) {
+    const int cur = sd.cur;
+    const uint32_t c = EL_STATE_LD(sd.cell[cur] + p);
+    q.p = p;
+    q.ci = (int)(c & 0xffffu);
+    q.cj = (int)(c >> 16);
+    q.o = EL_STATE_LD(sd.off[cur] + p);
+    q.v = sd.inertial ? EL_STATE_LD(sd.vel[cur] + p) : make_float2(0.f, 0.f);
+}
+
+// One RK4 step (Eq. 12 tracers, Eq. 14 inertial) between levels n and n+1,
+// read from their level pair `snap`, of a particle whose state and stencil
+// are loaded: stage 1 (theta = 0) and stage 4 (theta = 1) read one half of
+// each node without blending.  All (x, y) and (u, v) arithmetic is on float
+// pairs (one paired FP32 instruction per two lanes of work).  h = dt * n /
+// (2 pi): grid units per unit velocity.  Writes the new state.
+template <int SCHEME>
+__device__ __forceinline__ void rk4_finish(const float4* __restrict__ snap, int n, int log2n, float dt,
+                                           float h, const SpeciesDev& sd, ParticleRK4<SCHEME>& q) {
+    const int cur = sd.cur, p = q.p, ci = q.ci, cj = q.cj;
+    const float2 o = q.o;
+    Stencil<SCHEME>& st = q.st;
     const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
     const float2 two = make_float2(2.0f, 2.0f);
     float2 np2;
-    float2 vnew = make_float2(0.f, 0.f);
-    const bool inertial = sd.inertial;
-    if (PSI && !inertial) {
-        // Eq. 11: the streamfunction at (x +- dx, y) and (x, y +- dy), each
-        // interpolated in space and time, and centred differences; the
-        // neighbours sit one grid unit away, so they share the offsets.
-        const float inv2d = (float)n * (float)(1.0 / (4.0 * 3.14159265358979323846));
-        float2 k1 = psi_velocity<SCHEME, 0>(psi, n, ci, cj, o, inv2d);
-        float2 k2 = psi_velocity<SCHEME, 1>(psi, n, ci, cj, __ffma2_rn(h2, k1, o), inv2d);
-        float2 k3 = psi_velocity<SCHEME, 1>(psi, n, ci, cj, __ffma2_rn(h2, k2, o), inv2d);
-        float2 k4 = psi_velocity<SCHEME, 2>(psi, n, ci, cj, __ffma2_rn(h1, k3, o), inv2d);
-        float2 sum = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(k2, k3), k1), k4);
-        const float h6 = h * (1.0f / 6.0f);
-        np2 = __ffma2_rn(make_float2(h6, h6), sum, o);
-    } else if (!inertial) {
+    if (!sd.inertial) {
         // Eq. 12, stages at t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
         float2 k1 = st.template first_stage<0>(o);
         float2 k2 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, k1, o));
@@ -259,8 +256,7 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
         // v_s = v + c_s dt a_{s-1}, a_s = (u(x_s, t_s) - v_s) / St (Eq. 13).
         const float2 ist = make_float2(sd.inv_st, sd.inv_st);
         const float2 d2 = make_float2(0.5f * dt, 0.5f * dt), d1 = make_float2(dt, dt);
-        float2* __restrict__ velp = sd.vel[cur];
-        const float2 v = EL_STATE_LD(velp + p);
+        const float2 v = q.v;
         float2 u1 = st.template first_stage<0>(o);
         float2 a1 = __fmul2_rn(fsub2(u1, v), ist);
         float2 v2 = __ffma2_rn(d2, a1, v);
@@ -276,20 +272,71 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
         float2 sx = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(v2, v3), v), v4);
         float2 sa = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(a2, a3), a1), a4);
         np2 = __ffma2_rn(make_float2(h6, h6), sx, o);
-        vnew = __ffma2_rn(make_float2(d6, d6), sa, v);
-        EL_STATE_ST(velp + p, vnew);
+        EL_STATE_ST(sd.vel[cur] + p, __ffma2_rn(make_float2(d6, d6), sa, v));
     }
     float ox, oy;
     int ni, nj, dix, diy;
     carry_axis(np2.x, ci, log2n, ox, ni, dix);
     carry_axis(np2.y, cj, log2n, oy, nj, diy);
-    EL_STATE_ST(cellp + p, (uint32_t)ni | ((uint32_t)nj << 16));
-    EL_STATE_ST(offp + p, make_float2(ox, oy));
+    EL_STATE_ST(sd.cell[cur] + p, (uint32_t)ni | ((uint32_t)nj << 16));
+    EL_STATE_ST(sd.off[cur] + p, make_float2(ox, oy));
     if (dix | diy) {  // crossed the periodic boundary: rare read-modify-write
         int2* imgp = sd.img[cur];
         int2 m = imgp[p];
         imgp[p] = make_int2(m.x + dix, m.y + diy);
     }
+}
+
+// Tracers driven by the streamfunction (tracer_velocity = 1, Eq. 11): the
+// streamfunction at (x +- dx, y) and (x, y +- dy), each interpolated in space
+// and time, and centred differences; the neighbours sit one grid unit away,
+// so they share the offsets.
+template <int SCHEME>
+__device__ __forceinline__ void rk4_psi_tracer(const float2* __restrict__ psi, int n, int log2n,
+                                               float h, const SpeciesDev& sd, int p) {
+    const int cur = sd.cur;
+    const uint32_t c = EL_STATE_LD(sd.cell[cur] + p);
+    const int ci = (int)(c & 0xffffu), cj = (int)(c >> 16);
+    const float2 o = EL_STATE_LD(sd.off[cur] + p);
+    const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
+    const float2 two = make_float2(2.0f, 2.0f);
+    const float inv2d = (float)n * (float)(1.0 / (4.0 * 3.14159265358979323846));
+    float2 k1 = psi_velocity<SCHEME, 0>(psi, n, ci, cj, o, inv2d);
+    float2 k2 = psi_velocity<SCHEME, 1>(psi, n, ci, cj, __ffma2_rn(h2, k1, o), inv2d);
+    float2 k3 = psi_velocity<SCHEME, 1>(psi, n, ci, cj, __ffma2_rn(h2, k2, o), inv2d);
+    float2 k4 = psi_velocity<SCHEME, 2>(psi, n, ci, cj, __ffma2_rn(h1, k3, o), inv2d);
+    float2 sum = __fadd2_rn(__ffma2_rn(two, __fadd2_rn(k2, k3), k1), k4);
+    const float h6 = h * (1.0f / 6.0f);
+    const float2 np2 = __ffma2_rn(make_float2(h6, h6), sum, o);
+    float ox, oy;
+    int ni, nj, dix, diy;
+    carry_axis(np2.x, ci, log2n, ox, ni, dix);
+    carry_axis(np2.y, cj, log2n, oy, nj, diy);
+    EL_STATE_ST(sd.cell[cur] + p, (uint32_t)ni | ((uint32_t)nj << 16));
+    EL_STATE_ST(sd.off[cur] + p, make_float2(ox, oy));
+    if (dix | diy) {
+        int2* imgp = sd.img[cur];
+        int2 m = imgp[p];
+        imgp[p] = make_int2(m.x + dix, m.y + diy);
+    }
+}
+
+// One RK4 step of particle p of species sd between levels n and n+1 (the
+// streamfunction path for tracers when PSI).
+template <int SCHEME, bool PSI>
+__device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
+                                             const float2* __restrict__ psi, int n, int log2n,
+                                             float dt, float h, const SpeciesDev& sd, int p,
+                                             const KinArgs* kin = nullptr) {
+    if (PSI && !sd.inertial) {
+        rk4_psi_tracer<SCHEME>(psi, n, log2n, h, sd, p);
+        return;
+    }
+    ParticleRK4<SCHEME> q;
+    rk4_load_state(sd, p, q);
+    q.st.bind(kin);  // the prescribed field of EL_ANALYTIC; unused by the grid schemes
+    q.st.load(snap, n, q.ci, q.cj);
+    rk4_finish(snap, n, log2n, dt, h, sd, q);
 }
 
 }  // namespace el
