@@ -113,12 +113,6 @@ __device__ __forceinline__ void cubic_weights2(float2 s, float2 w[4]) {
     }
 }
 
-// Register-resident copy of the W x W stencil nodes (both time levels) of
-// one cell.  A particle moves a fraction of a cell per step, so its four RK4
-// stages nearly always fall in the cell of the previous stage: the stencil is
-// loaded once and re-used, and only a stage that crosses into another cell
-// fetches again.  (ci, cj) are the cell's unwrapped indices; addresses wrap.
-// THETA: 0 = level n, 1 = mid-way (theta = 1/2), 2 = level n+1 (Eq. 23).
 // The prescribed kinematic velocity of Sec. 5.2 at the three RK4 stage
 // times (t_n, t_n + dt/2, t_n + dt): u = alpha sin(k x - sx) cos(k y - sy),
 // v = -alpha cos(k x - sx) sin(k y - sy), with sx = k eps sin(omega t) and
@@ -131,6 +125,12 @@ struct KinArgs {
     int mask;            // n - 1
 };
 
+// Register-resident copy of the W x W stencil nodes (both time levels) of
+// one cell.  A particle moves a fraction of a cell per step, so its four RK4
+// stages nearly always fall in the cell of the previous stage: the stencil is
+// loaded once and re-used, and only a stage that crosses into another cell
+// fetches again.  (ci, cj) are the cell's unwrapped indices; addresses wrap.
+// THETA: 0 = level n, 1 = mid-way (theta = 1/2), 2 = level n+1 (Eq. 23).
 template <int SCHEME>
 struct Stencil {
     static constexpr int W = SCHEME == 0 ? 2 : 4;
