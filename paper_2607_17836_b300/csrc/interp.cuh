@@ -195,14 +195,24 @@ struct Stencil {
         return eval<THETA>(o);
     }
 
-    // Fluid velocity at grid-unit position (ci0 + l.x, cj0 + l.y).
+    // Fluid velocity at grid-unit position (ci0 + l.x, cj0 + l.y).  For the
+    // bilinear scheme the common case, a stage inside the cached cell
+    // (ci0, cj0), skips the floor: there floor(l) = 0 and l - 0 = l exactly
+    // (measured 5 % faster for bilinear, 5 % slower for the cubic schemes,
+    // whose register budget it upsets).
     template <int THETA>
     __device__ __forceinline__ float2 at(const float4* __restrict__ snap, int n, int ci0, int cj0,
                                          float2 l) {
-        float flx = floorf(l.x), fly = floorf(l.y);
-        int i = ci0 + (int)flx, j = cj0 + (int)fly;
-        if (i != ci || j != cj) load(snap, n, i, j);
-        return eval<THETA>(fsub2(l, make_float2(flx, fly)));
+        float2 s = l;
+        const bool home = SCHEME == 0 && ci == ci0 && cj == cj0 && l.x >= 0.f && l.x < 1.f &&
+                          l.y >= 0.f && l.y < 1.f;
+        if (!home) {
+            const float flx = floorf(l.x), fly = floorf(l.y);
+            const int i = ci0 + (int)flx, j = cj0 + (int)fly;
+            if (i != ci || j != cj) load(snap, n, i, j);
+            s = fsub2(l, make_float2(flx, fly));
+        }
+        return eval<THETA>(s);
     }
 };
 
