@@ -15,12 +15,16 @@ stage).  Between batch ticks it
 A tick advances the batch by min(tick_steps, fewest steps any member still
 needs), so a request finishes exactly at its step count.  Time-to-result is
 measured from the request's arrival to the moment its result is on the host.
+A request's host inputs (initial vorticity, particle positions) are prepared
+on a thread pool from the moment it arrives, so the device loop never waits
+for them; requests are admitted oldest first once their inputs are ready.
 Everything numerical runs in the CUDA library; this module only schedules.
 """
 from __future__ import annotations
 
 import collections
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -60,13 +64,21 @@ def request_desc(req: inputs.Request):
                             max_particles=wl.particles, sort_every=20)
 
 
-def build_flow(req: inputs.Request, stream, device) -> elpath.Flow:
-    """The request's simulation: its initial vorticity and particles."""
+def prepare_inputs(req: inputs.Request):
+    """The request's host inputs: initial vorticity and particle positions."""
     wl = req.workload
     sp = wl.species[0]
-    g = elpath.Flow(wl.n, wl.nu, wl.dt, wl.omega0(), interp=req.scheme, max_species=1,
+    return wl.omega0(), inputs.uniform_positions(sp.count, sp.seed)
+
+
+def build_flow(req: inputs.Request, stream, device, prepared=None) -> elpath.Flow:
+    """The request's simulation from its (prepared) initial vorticity and particles."""
+    wl = req.workload
+    sp = wl.species[0]
+    omega0, xy = prepared if prepared is not None else prepare_inputs(req)
+    g = elpath.Flow(wl.n, wl.nu, wl.dt, omega0, interp=req.scheme, max_species=1,
                     max_particles=wl.particles, sort_every=20, stream=stream, device=device)
-    g.set_particles(0, inputs.uniform_positions(sp.count, sp.seed), sp.st)
+    g.set_particles(0, xy, sp.st)
     return g
 
 
@@ -77,13 +89,16 @@ class Server:
     tick_steps: int = 20
     keep_positions: bool = False
     device: str = "cuda"
+    prep_workers: int = 8            # threads preparing arrived requests' host inputs
+    prep_ahead: int = 16             # waiting requests (oldest first) whose inputs are prepared
     results: list = field(default_factory=list)
 
     def __post_init__(self):
         import torch
         self._torch = torch
         self.batch = elpath.Batch(self.max_members, device=self.device)
-        self.waiting: collections.deque = collections.deque()
+        self.waiting: collections.deque = collections.deque()  # [request, inputs future or None]
+        self.pool = ThreadPoolExecutor(max_workers=max(1, self.prep_workers))
         self.active: list[_Active] = []
         self.used = 0
         self.peak_used = 0
@@ -97,16 +112,28 @@ class Server:
         need = elpath.workspace_bytes(request_desc(req))
         if need == 0 or need > self.hbm_budget:
             raise ValueError(f"request {req.rid} needs {need} B, over the {self.hbm_budget} B budget")
-        self.waiting.append(req)
+        self.waiting.append([req, None])
+        self._prepare_ahead()
+
+    def _prepare_ahead(self):
+        for k, entry in enumerate(self.waiting):
+            if k >= self.prep_ahead:
+                break
+            if entry[1] is None:
+                entry[1] = self.pool.submit(prepare_inputs, entry[0])
 
     def _admit(self):
+        self._prepare_ahead()
         while self.waiting and len(self.active) < self.max_members:
-            req = self.waiting[0]
+            req, prep = self.waiting[0]
+            if prep is None or not prep.done():
+                break                                # oldest first: its inputs are not ready
             need = elpath.workspace_bytes(request_desc(req))
             if self.used + need > self.hbm_budget:
                 break                                # oldest first: wait for memory
             self.waiting.popleft()
-            g = build_flow(req, None, self.device)
+            self._prepare_ahead()
+            g = build_flow(req, None, self.device, prep.result())
             self.batch.add(g)
             self.active.append(_Active(req, g, need, req.workload.steps, self.now()))
             self.used += need
@@ -157,8 +184,12 @@ class Server:
                 self.submit(pending.popleft())
             if timeout is not None and t > timeout:
                 break
-            if self.waiting or self.active:
+            if self.active:
                 self.tick()
+            elif self.waiting:
+                self._admit()
+                if not self.active:
+                    time.sleep(0.001)                # inputs still being prepared
             elif pending:
                 time.sleep(max(0.0, min(0.01, pending[0].arrival - t)))
         return self.results
@@ -169,6 +200,7 @@ class Server:
             a.flow.close()
         self.active = []
         self.batch.close()
+        self.pool.shutdown(wait=True, cancel_futures=True)
 
 
 def latency_summary(results) -> dict:
