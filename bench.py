@@ -86,18 +86,71 @@ def recorded_traffic(scheme_name):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
+    """SM clocks and clock-event (throttle) reasons sampled during the timed
+    region: through NVML every 5 ms (read-only queries of the driver's
+    libnvidia-ml), else nvidia-smi every 50 ms."""
 
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, device=None):
         self.index = index
-        self.rows = []
+        self.device = device
+        self.rows = []          # (sm_mhz, max_mhz, set of reason names)
         self.proc = None
+        self.nvml = None
+        self.stop = threading.Event()
+
+    def _nvml_handle(self):
+        """Read-only NVML queries for this process's CUDA device (matched by
+        UUID, else by PCI bus id, else the only device), through ctypes on the
+        driver's libnvidia-ml: returns a function giving (sm MHz, max sm MHz,
+        clock-event reason bits)."""
+        import ctypes
+        import torch
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        prop = torch.cuda.get_device_properties(self.device if self.device is not None else self.index)
+        h = ctypes.c_void_p()
+        found = False
+        uuid = getattr(prop, "uuid", None)
+        if uuid is not None:
+            found = nv.nvmlDeviceGetHandleByUUID(f"GPU-{uuid}".encode(), ctypes.byref(h)) == 0
+        if not found:
+            bus = f"{prop.pci_domain_id:08X}:{prop.pci_bus_id:02X}:{prop.pci_device_id:02X}.0"
+            found = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+        if not found:
+            cnt = ctypes.c_uint(0)
+            if nv.nvmlDeviceGetCount_v2(ctypes.byref(cnt)) == 0 and cnt.value == 1:
+                found = nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) == 0
+        if not found:
+            raise RuntimeError("no NVML handle for this device")
+        reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        sm, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+
+        def read():
+            if (nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) != 0 or      # 1: NVML_CLOCK_SM
+                    nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) != 0 or
+                    reasons_fn(h, ctypes.byref(rs)) != 0):
+                raise RuntimeError("NVML query failed")
+            return float(sm.value), float(mx.value), int(rs.value)
+        read()
+        return read
 
     def __enter__(self):
+        self.nvml_error = None
+        try:
+            self.nvml = self._nvml_handle()
+            self.thread = threading.Thread(target=self._poll_nvml, daemon=True)
+            self.thread.start()
+            return self
+        except Exception as e:
+            self.nvml = None
+            self.nvml_error = repr(e)[:200]
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
@@ -109,13 +162,30 @@ class ClockSampler:
             self.proc = None
         return self
 
+    # NVML clock-event reason bits of NAMES: HW slowdown, HW thermal, SW thermal, SW power cap
+    BITS = (0x8, 0x40, 0x20, 0x4)
+
+    def _poll_nvml(self):
+        read = self.nvml
+        while not self.stop.is_set():
+            try:
+                sm, mx, r = read()
+            except Exception:
+                break
+            self.rows.append((sm, mx, {n for n, b in zip(self.NAMES, self.BITS) if r & b}))
+            self.stop.wait(0.005)
+
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) == 7:
-                self.rows.append(parts)
+            if len(parts) == 7 and parts[0].replace(".", "").isdigit():
+                self.rows.append((float(parts[0]), float(parts[1]),
+                                  {n for n, v in zip(self.NAMES, parts[3:]) if v == "Active"}))
 
     def __exit__(self, *exc):
+        self.stop.set()
+        if self.nvml:
+            self.thread.join(timeout=2)
         if self.proc:
             self.proc.terminate()
             try:
@@ -126,13 +196,11 @@ class ClockSampler:
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": sorted(set().union(*(r[2] for r in self.rows))),
+                "samples": len(self.rows), "source": "nvml" if self.nvml else "nvidia-smi",
+                **({"nvml_error": self.nvml_error} if self.nvml_error else {})}
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -429,7 +497,7 @@ def run_ours(args, wl, scheme, world, rank, local):
         dist.barrier()
     torch.cuda.synchronize(dev)
     launches0 = flow.kernel_launches()
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local, dev) as clocks:
         t_wall0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for k, c in enumerate(chunks):
