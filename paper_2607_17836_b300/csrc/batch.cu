@@ -71,7 +71,10 @@ __host__ __device__ __forceinline__ int spec_chunks(int n) {
     return c < 1 ? 1 : c;
 }
 
-__global__ void __launch_bounds__(kBSpecThreads) k_batch_spectral(const __grid_constant__ BatchArgs b) {
+// `ahead` = 1: the fluid step one past each member's step counter (the
+// fluid branch of the overlapped step), 0: the step at the counter.
+__global__ void __launch_bounds__(kBSpecThreads) k_batch_spectral(const __grid_constant__ BatchArgs b,
+                                                                  int ahead) {
     for (int t = blockIdx.x; t < b.spec_tasks; t += gridDim.x) {
         const int m = owner_of(b.spec_begin, b.nmembers, t);
         const MemberDev& md = b.members[m];
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(kBSpecThreads) k_batch_spectral(const __grid_c
         const int chunks = spec_chunks(md.n);
         const int j = local / chunks, i = (local - j * chunks) * kBSpecThreads + threadIdx.x;
         SpecArgs a = md.spec;
-        a.first = md.step == 0;
+        a.first = md.step + ahead == 0;
         if (i < md.n / 2) {
             spectral_mode<true>(a, i, j);
             if (i == 0) spectral_mode<true>(a, md.n / 2, j);
@@ -87,12 +90,13 @@ __global__ void __launch_bounds__(kBSpecThreads) k_batch_spectral(const __grid_c
     }
 }
 
-__global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_constant__ BatchArgs b,
+                                                                   int ahead) {
     for (int t = blockIdx.x; t < b.nl_tasks; t += gridDim.x) {
         const int m = owner_of(b.nl_begin, b.nmembers, t);
         const MemberDev& md = b.members[m];
         const size_t q = (size_t)(t - b.nl_begin[m]) * kBNlThreads + threadIdx.x;
-        const long long lv = md.step + 1;  // the level this step produces
+        const long long lv = md.step + 1 + ahead;  // the level this step produces
         if (q < md.n4)
             nonlinear_quad(md.phys4, md.nl4, md.snap[lv % 2], md.snap[(lv + 1) % 2], nullptr,
                            md.n4, q, md.stencil_plane, md.psi_plane, md.psi[lv % 2],
@@ -151,8 +155,13 @@ struct el_batch {
     int grid_spec = 0, grid_nl = 0, grid_rk[3] = {0, 0, 0};
     bool scheme_used[3] = {false, false, false};
     bool tables_valid = false;
-    cudaGraphExec_t graph = nullptr;
-    int64_t graph_kernels = 0;
+    // one coupled step of every member in three captured forms (fluid of
+    // step s, particles of s alongside fluid of s + 1, particles of the last
+    // step); the fluid branch runs at the highest stream priority
+    cudaGraphExec_t graph[3] = {};
+    int64_t graph_kernels[3] = {};
+    cudaStream_t fluid = nullptr;
+    cudaEvent_t f_fork = nullptr, f_join = nullptr;
     cudaStream_t side[kSideStreams] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
     int sms = 0;
@@ -301,9 +310,9 @@ el_status rebuild_tables(el_batch* b) {
     return EL_OK;
 }
 
-// cuFFT of every member on forked branches of the capture.
-el_status fork_ffts(el_batch* b, bool c2r) {
-    BT_CUDA(b, cudaEventRecord(b->fork_ev, b->stream));
+// cuFFT of every member on forked branches of the capture (from `origin`).
+el_status fork_ffts(el_batch* b, cudaStream_t origin, bool c2r) {
+    BT_CUDA(b, cudaEventRecord(b->fork_ev, origin));
     for (int k = 0; k < kSideStreams; k++) BT_CUDA(b, cudaStreamWaitEvent(b->side[k], b->fork_ev, 0));
     for (size_t m = 0; m < b->members.size(); m++) {
         el_flow* f = b->members[m];
@@ -316,19 +325,27 @@ el_status fork_ffts(el_batch* b, bool c2r) {
     }
     for (int k = 0; k < kSideStreams; k++) {
         BT_CUDA(b, cudaEventRecord(b->join_ev[k], b->side[k]));
-        BT_CUDA(b, cudaStreamWaitEvent(b->stream, b->join_ev[k], 0));
+        BT_CUDA(b, cudaStreamWaitEvent(origin, b->join_ev[k], 0));
     }
     return EL_OK;
 }
 
-el_status capture_body(el_batch* b) {
+// The fluid step (every member) on stream s: spectral stage, C2R, nonlinear
+// stage and level pair, R2C.
+el_status enqueue_fluid(el_batch* b, cudaStream_t s, int ahead) {
     const BatchArgs& a = b->args;
-    k_batch_spectral<<<b->grid_spec, kBSpecThreads, 0, b->stream>>>(a);
+    k_batch_spectral<<<b->grid_spec, kBSpecThreads, 0, s>>>(a, ahead);
     b->launches++;
-    EL_TRY(fork_ffts(b, true));
-    k_batch_nonlinear<<<b->grid_nl, kBNlThreads, 0, b->stream>>>(a);
+    EL_TRY(fork_ffts(b, s, true));
+    k_batch_nonlinear<<<b->grid_nl, kBNlThreads, 0, s>>>(a, ahead);
     b->launches++;
-    EL_TRY(fork_ffts(b, false));
+    return fork_ffts(b, s, false);
+}
+
+// The particle step (every member, one launch per scheme present) and the
+// per-member step counters.
+el_status enqueue_particles(el_batch* b) {
+    const BatchArgs& a = b->args;
     if (a.rk_tasks > 0) {
         int threads = b->members.empty() ? 256 : b->members[0]->rk4_threads;
         if (b->scheme_used[0]) k_batch_rk4<0><<<b->grid_rk[0], threads, 0, b->stream>>>(a);
@@ -336,21 +353,42 @@ el_status capture_body(el_batch* b) {
         if (b->scheme_used[2]) k_batch_rk4<2><<<b->grid_rk[2], threads, 0, b->stream>>>(a);
         b->launches += (int)b->scheme_used[0] + (int)b->scheme_used[1] + (int)b->scheme_used[2];
     }
-    k_batch_advance<<<1, 256, 0, b->stream>>>(b->d_members, a.nmembers);
-    b->launches++;
+    return EL_OK;
+}
+
+enum { kBatchFluid = 0, kBatchOverlap = 1, kBatchLast = 2 };
+
+el_status capture_body(el_batch* b, int kind) {
+    const BatchArgs& a = b->args;
+    if (kind == kBatchFluid) {
+        EL_TRY(enqueue_fluid(b, b->stream, 0));
+    } else {
+        if (kind == kBatchOverlap) {  // fluid of s + 1 on a forked, high-priority branch
+            BT_CUDA(b, cudaEventRecord(b->f_fork, b->stream));
+            BT_CUDA(b, cudaStreamWaitEvent(b->fluid, b->f_fork, 0));
+            EL_TRY(enqueue_fluid(b, b->fluid, 1));
+        }
+        EL_TRY(enqueue_particles(b));
+        if (kind == kBatchOverlap) {
+            BT_CUDA(b, cudaEventRecord(b->f_join, b->fluid));
+            BT_CUDA(b, cudaStreamWaitEvent(b->stream, b->f_join, 0));
+        }
+        k_batch_advance<<<1, 256, 0, b->stream>>>(b->d_members, a.nmembers);
+        b->launches++;
+    }
     BT_CUDA(b, cudaGetLastError());
     return EL_OK;
 }
 
-el_status build_batch_graph(el_batch* b) {
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
+el_status build_batch_graph(el_batch* b, int kind) {
+    if (b->graph[kind]) {
+        cudaGraphExecDestroy(b->graph[kind]);
+        b->graph[kind] = nullptr;
     }
     int64_t before = b->launches;
     cudaGraph_t g = nullptr;
     BT_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    el_status s = capture_body(b);
+    el_status s = capture_body(b, kind);
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     for (el_flow* f : b->members) {  // plans back on the batch stream
         cufftSetStream(f->plan_c2r, b->stream);
@@ -361,19 +399,27 @@ el_status build_batch_graph(el_batch* b) {
         return s;
     }
     if (e != cudaSuccess) return bfail(b, EL_ECUDA, "batch capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&b->graph, g, 0);
+    // kernel nodes keep the priority of the stream they were captured on
+    e = cudaGraphInstantiate(&b->graph[kind], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return bfail(b, EL_ECUDA, "batch graph: %s", cudaGetErrorString(e));
-    b->graph_kernels = b->launches - before;
+    b->graph_kernels[kind] = b->launches - before;
     b->launches = before;
+    return EL_OK;
+}
+
+el_status launch_graph(el_batch* b, int kind) {
+    if (!b->graph[kind]) EL_TRY(build_batch_graph(b, kind));
+    BT_CUDA(b, cudaGraphLaunch(b->graph[kind], b->stream));
+    b->launches += b->graph_kernels[kind];
     return EL_OK;
 }
 
 void invalidate(el_batch* b) {
     b->tables_valid = false;
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
+    for (cudaGraphExec_t& g : b->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
     }
 }
 
@@ -419,8 +465,13 @@ el_status el_batch_create(int32_t max_members, void* dev_workspace, size_t bytes
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    int lo_prio = 0, hi_prio = 0;
+    if (err == cudaSuccess) err = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     for (int k = 0; k < kSideStreams && err == cudaSuccess; k++)
-        err = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+        err = cudaStreamCreateWithPriority(&b->side[k], cudaStreamNonBlocking, hi_prio);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&b->fluid, cudaStreamNonBlocking, hi_prio);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->f_fork, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->f_join, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
     for (int k = 0; k < kSideStreams && err == cudaSuccess; k++)
         err = cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming);
@@ -475,6 +526,11 @@ el_status el_batch_step(el_batch* b, int32_t nsteps) {
     if (nsteps < 0) return bfail(b, EL_EINVAL, "nsteps < 0");
     if (b->members.empty()) return EL_OK;
     if (!b->tables_valid) EL_TRY(rebuild_tables(b));
+    if (nsteps == 0) return EL_OK;
+    // As in el_step_coupled, the fluid runs one step ahead inside the call:
+    // fluid of s0, then particles of s alongside fluid of s + 1, then the
+    // particles of the last step; every member ends at the same level.
+    EL_TRY(launch_graph(b, kBatchFluid));
     for (int32_t k = 0; k < nsteps; k++) {
         for (el_flow* f : b->members) {
             if (f->d.sort_every > 0 && f->since_sort >= f->d.sort_every) {
@@ -485,9 +541,7 @@ el_status el_batch_step(el_batch* b, int32_t nsteps) {
                 f->since_sort = 0;
             }
         }
-        if (!b->graph) EL_TRY(build_batch_graph(b));
-        BT_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
-        b->launches += b->graph_kernels;
+        EL_TRY(launch_graph(b, k + 1 < nsteps ? kBatchOverlap : kBatchLast));
         for (el_flow* f : b->members) {
             f->step++;
             f->since_sort++;
@@ -508,12 +562,16 @@ el_status el_batch_destroy(el_batch* b) {
     if (!b) return EL_EINVAL;
     if (b->stream || !b->members.empty()) cudaStreamSynchronize(b->stream);
     while (!b->members.empty()) el_batch_remove(b, b->members.back());
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaGraphExec_t g : b->graph)
+        if (g) cudaGraphExecDestroy(g);
     for (int k = 0; k < kSideStreams; k++) {
         if (b->side[k]) cudaStreamDestroy(b->side[k]);
         if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
     }
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->fluid) cudaStreamDestroy(b->fluid);
+    if (b->f_fork) cudaEventDestroy(b->f_fork);
+    if (b->f_join) cudaEventDestroy(b->f_join);
     delete b;
     return EL_OK;
 }
