@@ -158,7 +158,10 @@ typedef struct {
 
 /* Diagnostics of the current state, reduced in FP64 in a fixed order (the
  * same inputs give the same bits).  Synchronises the stream.  Returns
- * EL_ENONFINITE (with *out filled) if a NaN/Inf was found. */
+ * EL_ENONFINITE (with *out filled) if a NaN/Inf was found.  In a library
+ * built with EL_CHECK_BOUNDS=1 (a debug build) it returns EL_ESTATE if any
+ * particle step met a particle whose split state broke its invariants
+ * (cell index >= n or offset outside [0, 1)); el_last_error says which. */
 el_status el_get_stats(el_flow* flow, el_stats* out);
 
 /* Particles of one species in their original order: unwrapped positions

@@ -141,6 +141,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* px = take(nh * 4);
     char* py = take(n * 4);
     char* table = take(sizeof(SpeciesDev) * kMaxSpecies);
+    char* check = take(4 * sizeof(uint32_t));
     char* red = take((size_t)kRedBlocks * 3 * 8);
     char* red_out = take(64 * 8);
     char* boxes = take((size_t)kBoxes * kBoxes * 8);
@@ -170,6 +171,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->pre_x = (float*)px;
         f->pre_y = (float*)py;
         f->table = (SpeciesDev*)table;
+        f->check = (uint32_t*)check;
         f->red = (double*)red;
         f->red_out = (double*)red_out;
         f->boxes = (unsigned long long*)boxes;
@@ -314,6 +316,7 @@ el_status run_step(el_flow* f, int kind, int64_t step) {
 
 el_status maybe_sort(el_flow* f) {
     if (f->d.sort_every > 0 && f->since_sort >= f->d.sort_every) {
+        NvtxRange range("rebin");
         for (int s = 0; s < f->d.max_species; s++) EL_TRY(particles_sort(f, s));
         f->since_sort = 0;
     }
@@ -377,6 +380,7 @@ size_t el_workspace_bytes(const el_flow_desc* desc) {
 static el_status create_flow(const el_flow_desc* desc, const double* omega0, const el_kinematic* kin,
                              void* dev_workspace, size_t workspace_bytes, void* cuda_stream,
                              el_flow** out) {
+    NvtxRange range("el_create_flow");
     if (!out) return fail(nullptr, EL_EINVAL, "out is NULL");
     *out = nullptr;
     if (const char* why = check_desc(desc)) return fail(nullptr, EL_EINVAL, "%s", why);
@@ -472,6 +476,11 @@ static el_status create_flow(const el_flow_desc* desc, const double* omega0, con
         fail(f, EL_ECUDA, "table upload: %s", cudaGetErrorString(e));
         return bail(EL_ECUDA);
     }
+    e = cudaMemsetAsync(f->check, 0, 4 * sizeof(uint32_t), f->stream);
+    if (e != cudaSuccess) {
+        fail(f, EL_ECUDA, "check word: %s", cudaGetErrorString(e));
+        return bail(EL_ECUDA);
+    }
     el_status s = kin ? kinematic_level(f, 0, true) : fluid_init(f, omega0);
     if (s != EL_OK) return bail(s);
     e = cudaStreamSynchronize(f->stream);
@@ -502,6 +511,7 @@ el_status el_create_kinematic(const el_flow_desc* desc, const el_kinematic* kin,
 el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, const double* xy,
                            const double* vxy) {
     if (!f) return EL_EINVAL;
+    NvtxRange range("el_set_particles");
     if (species < 0 || species >= f->d.max_species)
         return fail(f, EL_EINVAL, "species %d outside [0, %d)", species, f->d.max_species);
     if (np < 0 || np > f->d.max_particles) return fail(f, EL_EINVAL, "np %lld out of range", (long long)np);
@@ -532,6 +542,7 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
 // level, so every other call sees a consistent state.
 el_status el_step_coupled(el_flow* f, int32_t nsteps) {
     if (!f) return EL_EINVAL;
+    NvtxRange range("el_step_coupled");
     if (f->batch) return fail(f, EL_ESTATE, "flow belongs to a batch: step it with el_batch_step");
     if (nsteps < 0) return fail(f, EL_EINVAL, "nsteps < 0");
     if (nsteps == 0) return EL_OK;
@@ -558,6 +569,7 @@ el_status el_step_coupled(el_flow* f, int32_t nsteps) {
 
 el_status el_get_stats(el_flow* f, el_stats* out) {
     if (!f || !out) return EL_EINVAL;
+    NvtxRange range("el_get_stats");
     if (!f->kinematic) EL_TRY(fluid_diagnostics(f));
     int ns = f->d.max_species;
     for (int s = 0; s < ns; s++)
@@ -566,6 +578,14 @@ el_status el_get_stats(el_flow* f, el_stats* out) {
     EL_CUDA_OK(f, cudaMemcpyAsync(host, f->red_out, sizeof(double) * (3 + 5 * ns), cudaMemcpyDeviceToHost,
                                   f->stream));
     EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
+    if (EL_CHECK_BOUNDS) {
+        uint32_t chk[4] = {0, 0, 0, 0};
+        EL_CUDA_OK(f, cudaMemcpy(chk, f->check, sizeof chk, cudaMemcpyDeviceToHost));
+        if (chk[0] != 0)
+            return fail(f, EL_ESTATE,
+                        "particle state invariant violated %u times (first: particle %u of species %u)",
+                        chk[0], chk[1], chk[2]);
+    }
     if (f->kinematic) kinematic_diagnostics(f, host);
     *out = el_stats{};
     out->t = (double)f->step * f->d.dt;
@@ -682,6 +702,7 @@ el_status el_set_tuning(el_flow* f, const el_tuning* t) {
 
 el_status el_autotune(el_flow* f, int32_t trial_steps, el_tuning* best) {
     if (!f || !best) return EL_EINVAL;
+    NvtxRange range("el_autotune");
     if (f->batch) return fail(f, EL_ESTATE, "flow belongs to a batch: use el_batch_autotune");
     if (trial_steps < 1) return fail(f, EL_EINVAL, "trial_steps must be >= 1");
     el_tuning start{};

@@ -523,6 +523,7 @@ el_status el_batch_remove(el_batch* b, el_flow* f) {
 
 el_status el_batch_step(el_batch* b, int32_t nsteps) {
     if (!b) return EL_EINVAL;
+    NvtxRange range("el_batch_step");
     if (nsteps < 0) return bfail(b, EL_EINVAL, "nsteps < 0");
     if (b->members.empty()) return EL_OK;
     if (!b->tables_valid) EL_TRY(rebuild_tables(b));

@@ -108,6 +108,7 @@ extern "C" {
 
 el_status el_save_state(el_flow* f, void* host_buf, size_t* bytes) {
     if (!f || !bytes) return EL_EINVAL;
+    NvtxRange range("el_save_state");
     CkptHeader h{};
     std::memcpy(h.magic, kMagic, sizeof kMagic);
     h.version = kVersion;
@@ -150,6 +151,7 @@ el_status el_save_state(el_flow* f, void* host_buf, size_t* bytes) {
 
 el_status el_load_state(el_flow* f, const void* host_buf, size_t bytes) {
     if (!f || !host_buf) return EL_EINVAL;
+    NvtxRange range("el_load_state");
     if (f->batch) return fail(f, EL_ESTATE, "flow belongs to a batch: remove it before loading");
     const unsigned char* in = static_cast<const unsigned char*>(host_buf);
     CkptHeader h{};

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <cstdio>
@@ -18,6 +19,14 @@ constexpr int kBoxes = 64;          // clustering-index box grid (kBoxes x kBoxe
 constexpr int kRedBlocks = 512;     // fixed grid of the FP64 reductions (fixed order)
 constexpr int kRedThreads = 256;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// EL_CHECK_BOUNDS=1 builds a debug library whose particle kernel checks each
+// particle's split state (cell indices below n, offsets in [0, 1)) before
+// its step and counts violations in a device word (no trap); el_get_stats
+// then reports them as EL_ESTATE.
+#ifndef EL_CHECK_BOUNDS
+#define EL_CHECK_BOUNDS 0
+#endif
 
 // Device-resident descriptor of one species, read by the particle step.
 // `cur` selects the current buffer of each pair; the sort flips it on the
@@ -88,6 +97,7 @@ struct el_flow {
     float* pre_y = nullptr;   // ... per row index
     el::SpeciesDev* table = nullptr;  // device copy of h_table
     el::SpeciesDev h_table[el::kMaxSpecies] = {};
+    uint32_t* check = nullptr;    // EL_CHECK_BOUNDS builds: violations, first particle, its species
     double* red = nullptr;        // reduction partials
     double* red_out = nullptr;    // reduced scalars (device)
     unsigned long long* boxes = nullptr;  // kBoxes^2 counters
@@ -124,6 +134,15 @@ struct el_flow {
 };
 
 namespace el {
+
+// NVTX range over a host-side stage of the library (shown by profilers; a
+// no-op when none is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- launch helpers -------------------------------------------------------
 inline unsigned blocks_for(int64_t work, int threads) {

@@ -213,6 +213,7 @@ el_status fluid_init(el_flow* f, const double* omega0_host) {
 
 // Fluid n -> n+1 for step number n = `step`.
 el_status fluid_step(el_flow* f, int64_t step) {
+    NvtxRange range("fluid_step");
     if (f->kinematic) return kinematic_level(f, step + 1, false);
     k_spectral<true><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, step == 0));
     EL_LAUNCHED(f);

@@ -40,6 +40,7 @@ struct RK4Args {
     float dt, h;              // h = dt * n / (2 pi): grid units per unit velocity
     unsigned block_begin[kMaxSpecies];
     KinArgs kin;              // EL_ANALYTIC only: the prescribed field at the stage times
+    uint32_t* check;          // EL_CHECK_BOUNDS builds: the flow's violation words
 };
 
 // K6: one RK4 step of every species in one launch (blocks are split between
@@ -53,6 +54,18 @@ __global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_
     const SpeciesDev& sd = a.table[s];
     const int p = (int)(blockIdx.x - a.block_begin[s]) * (int)blockDim.x + (int)threadIdx.x;
     if (p >= sd.np) return;
+#if EL_CHECK_BOUNDS
+    {
+        const uint32_t c = sd.cell[sd.cur][p];
+        const float2 o = sd.off[sd.cur][p];
+        const bool bad = (c & 0xffffu) >= (uint32_t)a.n || (c >> 16) >= (uint32_t)a.n ||
+                         !(o.x >= 0.f && o.x < 1.f) || !(o.y >= 0.f && o.y < 1.f);
+        if (bad && atomicAdd(a.check, 1u) == 0u) {
+            a.check[1] = (uint32_t)p;
+            a.check[2] = (uint32_t)s;
+        }
+    }
+#endif
     rk4_particle<SCHEME, PSI>(a.snap, a.psi, a.n, a.log2n, a.dt, a.h, sd, p, &a.kin);
 }
 
@@ -286,10 +299,12 @@ el_status particles_restore_table(el_flow* f, int s) {
 // K6 for every species of the flow in one launch, step number `step`
 // (levels step and step + 1: pair snap[step % 2]).
 el_status particles_step_all(el_flow* f, int64_t step) {
+    NvtxRange range("particles_step");
     RK4Args a{};
     a.snap = f->snap[step % 2];
     a.psi = f->psi_plane >= 0 ? f->psi[step % 2] : nullptr;
     a.table = f->table;
+    a.check = f->check;
     a.n = f->n;
     a.log2n = f->log2n;
     a.dt = (float)f->d.dt;

@@ -1,0 +1,76 @@
+"""Failure detection without any GPU fault, and determinism.
+
+A simulation made unstable on the host (a time step far beyond the AB2
+stability limit) blows up; el_get_stats reports it as EL_ENONFINITE with the
+flow still usable (readback works, it can be destroyed cleanly).  Identical
+runs give identical bits (the reductions are in a fixed order and no kernel
+depends on scheduling), whatever the block size of the particle step:
+a cheap race detector.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_17836_b300 import elpath, inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_blow_up_is_reported_as_non_finite():
+    n = 64
+    g = elpath.Flow(n, 1e-4, 2.0, inputs.decaying_turbulence(n, 3, k0=6.0), interp=1,
+                    max_species=1, max_particles=500)
+    g.set_particles(0, inputs.uniform_positions(500, 4), 1.0)
+    status = None
+    for _ in range(40):
+        g.step(5)
+        s = g.stats(allow_nonfinite=True)
+        if not s["finite"]:
+            with pytest.raises(elpath.ElpathError) as e:
+                g.stats()
+            status = e.value.status
+            break
+    assert status == 6                                 # EL_ENONFINITE
+    # the flow is still usable: readback and destruction work
+    w = g.field(0)
+    assert w.shape == (n, n)
+    xy, _ = g.particles(0, 500)
+    assert xy.shape == (500, 2)
+    g.close()
+
+
+def test_stable_runs_report_finite_statistics():
+    n = 64
+    g = elpath.Flow(n, 1e-3, 1e-3, inputs.decaying_turbulence(n, 3, k0=6.0), interp=0,
+                    max_species=1, max_particles=500)
+    g.set_particles(0, inputs.uniform_positions(500, 4), 0.0)
+    g.step(200)
+    assert g.stats()["finite"]
+    g.close()
+
+
+def run(case_threads, interp, sort_every):
+    n = 128
+    g = elpath.Flow(n, 1e-4, 5e-4, inputs.decaying_turbulence(n, 12), interp=interp,
+                    max_species=2, max_particles=6000, sort_every=sort_every)
+    g.set_particles(0, inputs.uniform_positions(3000, 1), 0.0)
+    g.set_particles(1, inputs.uniform_positions(3000, 2), 1.0)
+    g.set_tuning(case_threads, sort_every, 0)
+    g.step(150)
+    s = g.stats()
+    out = [g.field(0)] + list(g.particles(0, 3000)) + list(g.particles(1, 3000))
+    out.append(np.array([s["energy"], s["enstrophy"], s["palinstrophy"]]
+                        + [m for p in s["msd"] for m in p] + s["cluster"]
+                        + [m for p in s["msd_sem"] for m in p]))
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("interp", [0, 1, 2])
+def test_reruns_are_bitwise_identical(interp):
+    a = run(256, interp, 10)
+    b = run(256, interp, 10)
+    c = run(128, interp, 17)          # another block size and re-binning cadence
+    for x, y, z in zip(a, b, c):
+        np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(x, z)
