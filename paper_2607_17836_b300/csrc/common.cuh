@@ -114,6 +114,8 @@ struct el_flow {
 
     int64_t step = 0;          // coupled steps taken
     int rk4_threads = 256;     // threads per block of the particle step (tunable)
+    int prefetch_threads = 0;  // block size the cached prefetch distance was computed for
+    int prefetch_particles = 0;
     int sort_shift = 0;        // re-binning key: tiles of 2^sort_shift cells per side
     el_batch* batch = nullptr; // the batch this flow is a member of, if any
     cudaStream_t own_stream = nullptr;  // stream given at creation (restored on batch removal)

@@ -245,6 +245,7 @@ __device__ __forceinline__ void rk4_finish(const float4* __restrict__ snap, int 
     if (!sd.inertial) {
         // Eq. 12, stages at t, t + dt/2, t + dt/2, t + dt (theta = 0, 1/2, 1/2, 1)
         float2 k1 = st.template first_stage<0>(o);
+        st.to_mid();
         float2 k2 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, k1, o));
         float2 k3 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, k2, o));
         float2 k4 = st.template at<2>(snap, n, ci, cj, __ffma2_rn(h1, k3, o));
@@ -258,6 +259,7 @@ __device__ __forceinline__ void rk4_finish(const float4* __restrict__ snap, int 
         const float2 d2 = make_float2(0.5f * dt, 0.5f * dt), d1 = make_float2(dt, dt);
         const float2 v = q.v;
         float2 u1 = st.template first_stage<0>(o);
+        st.to_mid();
         float2 a1 = __fmul2_rn(fsub2(u1, v), ist);
         float2 v2 = __ffma2_rn(d2, a1, v);
         float2 u2 = st.template at<1>(snap, n, ci, cj, __ffma2_rn(h2, v, o));
