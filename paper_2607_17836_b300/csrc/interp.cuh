@@ -87,9 +87,16 @@ __device__ __forceinline__ float2 fluid_at(const float4* __restrict__ snap, int 
     }
 }
 
-// a - b on float pairs: one paired FMA (b * -1 + a is exact before rounding).
+// a - b on float pairs: one paired subtraction, rounded to nearest per lane
+// (no constant pair (-1, -1) to keep in registers, as b * -1 + a would need).
 __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
-    return __ffma2_rn(make_float2(-1.0f, -1.0f), b, a);
+    float2 r;
+    asm("{\n\t.reg .b64 x, y, d;\n\t"
+        "mov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "sub.rn.f32x2 d, x, y;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
 }
 
 __device__ __forceinline__ float2 pair(float x) { return make_float2(x, x); }
@@ -217,8 +224,11 @@ struct Stencil {
     __device__ __forceinline__ float2 at(const float4* __restrict__ snap, int n, int ci0, int cj0,
                                          float2 l) {
         float2 s = l;
-        const bool home = SCHEME == 0 && ci == ci0 && cj == cj0 && l.x >= 0.f && l.x < 1.f &&
-                          l.y >= 0.f && l.y < 1.f;
+        // 0 <= l < 1 on both axes as one unsigned compare of the bit
+        // patterns: non-negative floats order like their bits, below 1.0f's,
+        // and any sign bit (or NaN) makes the pattern larger
+        const bool home = SCHEME == 0 && ci == ci0 && cj == cj0 &&
+                          max(__float_as_uint(l.x), __float_as_uint(l.y)) < 0x3f800000u;
         if (!home) {
             const float flx = floorf(l.x), fly = floorf(l.y);
             const int i = ci0 + (int)flx, j = cj0 + (int)fly;

@@ -202,7 +202,7 @@ __device__ __forceinline__ void carry_axis(float x, int c, int log2n, float& off
     }
     int c2 = c + k;
     dimg = c2 >> log2n;              // floor division by n
-    cell = c2 - (dimg << log2n);
+    cell = c2 & ((1 << log2n) - 1);  // the remainder, in [0, n)
     off = o;
 }
 
