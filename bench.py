@@ -44,6 +44,12 @@ SORT_EVERY = 20
 BYTES_TRACER = 2 * (4 + 8)
 BYTES_INERTIAL = 2 * (4 + 8 + 8)
 FLUSH_BYTES = 256 << 20
+# Snapshot bytes one particle-step gathers, per interpolation width W (W x W
+# nodes of (u, v) in FP32): the plain form fetches the nodes at each of its 6
+# snapshot evaluations (levels n and n+1 at stages 1 and 4, both at stages 2
+# and 3); the kernel here fetches each node once as one 16-byte level pair.
+GATHER_PLAIN = {0: 6 * 4 * 8, 1: 6 * 16 * 8, 2: 6 * 16 * 8}
+GATHER_CACHED = {0: 4 * 16, 1: 16 * 16, 2: 16 * 16}
 CHUNK = 10          # coupled steps per el_step_coupled call in the timed region
 
 
@@ -54,6 +60,27 @@ def measured_peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+def l2_copy_gbs(dev, mib=24, reps=20):
+    """Read + write bandwidth of a device copy whose source and destination
+    (2 x mib MiB) stay resident in L2: the best of `reps` batches of 20 copies,
+    CUDA events around each batch."""
+    import torch
+    src = torch.empty(mib << 20, dtype=torch.uint8, device=dev)
+    dst = torch.empty_like(src)
+    for _ in range(5):
+        dst.copy_(src)
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            dst.copy_(src)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3 / 20)
+    return 2 * src.numel() / best / 1e9
 
 
 def kernel_source_hash():
@@ -580,6 +607,20 @@ def run_ours(args, wl, scheme, world, rank, local):
 
     if rank != 0:
         return
+    # The gather's L2 side (the level pair, 16 N^2 B, is L2-resident): snapshot
+    # bytes per particle-step over the particle stage's time, against an
+    # L2-resident copy measured here.
+    l2_peak = l2_copy_gbs(dev)
+    parts_per_s = wl.particles / (part_ms * 1e-3)
+    gather = {"scheme": args.scheme, "unit": "GB/s",
+              "plain_bytes_per_particle_step": GATHER_PLAIN[scheme],
+              "cached_bytes_per_particle_step": GATHER_CACHED[scheme],
+              "achieved_plain": GATHER_PLAIN[scheme] * parts_per_s / 1e9,
+              "achieved_cached": GATHER_CACHED[scheme] * parts_per_s / 1e9,
+              "l2_copy_peak": l2_peak,
+              "peak_kind": "measured in this run: torch copy of a 2 x 24 MiB L2-resident buffer",
+              "frac_plain": GATHER_PLAIN[scheme] * parts_per_s / 1e9 / l2_peak,
+              "frac_cached": GATHER_CACHED[scheme] * parts_per_s / 1e9 / l2_peak}
     value = aggregate_rate(wl.particles * args.steps, world, total_ms * 1e-3)
     srt = sorted(step_ms)
     p50 = srt[len(srt) // 2]
@@ -603,6 +644,7 @@ def run_ours(args, wl, scheme, world, rank, local):
             "e2e": {"value": e2e_value, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "what": "set_particles from pinned host + K steps + stats + particles back"},
+            "l2_gather": gather,
             "roofline_16M": roof16, "tuning": tuning,
             "gpu_launches": launches, "wall_s": t_wall,
             "clocks": clocks.summary(), "energy": st["energy"]}
