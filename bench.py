@@ -62,27 +62,6 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def l2_read_gbs(dev, mib=24, reps=20):
-    """Read bandwidth of a plain streaming read of an L2-resident buffer
-    (mib MiB of FP32, summed by torch): the best of `reps` batches of 20 sums,
-    CUDA events around each batch."""
-    import torch
-    x = torch.ones((mib << 20) // 4, dtype=torch.float32, device=dev)
-    out = torch.empty((), dtype=torch.float32, device=dev)
-    for _ in range(5):
-        torch.sum(x, dim=0, out=out)
-    best = float("inf")
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(20):
-            torch.sum(x, dim=0, out=out)
-        e1.record()
-        e1.synchronize()
-        best = min(best, e0.elapsed_time(e1) * 1e-3 / 20)
-    return x.numel() * 4 / best / 1e9
-
-
 def kernel_source_hash():
     h = hashlib.sha256()
     for rel in ("paper_2607_17836_b300/csrc/particles.cu", "paper_2607_17836_b300/csrc/interp.cuh",
@@ -92,12 +71,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(scheme_name):
-    """DRAM bytes per particle-step of the RK4 kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+def recorded_profile(scheme_name):
+    """Figures of the RK4 kernel from the committed ncu summary
+    (profiles/k_rk4_<scheme>_traffic.txt), if they were taken on the current
+    kernel source; else an empty dict."""
     p = os.path.join(ROOT, "profiles", f"k_rk4_{scheme_name}_traffic.txt")
     if not os.path.exists(p):
-        return None
+        return {}
     vals = {}
     with open(p) as fh:
         for line in fh:
@@ -105,9 +85,15 @@ def recorded_traffic(scheme_name):
                 k, v = line.strip().split("=", 1)
                 vals[k.strip()] = v.strip()
     if vals.get("source_hash") != kernel_source_hash():
-        return None
+        return {}
+    return vals
+
+
+def recorded_traffic(scheme_name):
+    """DRAM bytes per particle-step of the RK4 kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
     try:
-        return float(vals["dram_bytes_per_particle_step"])
+        return float(recorded_profile(scheme_name)["dram_bytes_per_particle_step"])
     except (KeyError, ValueError):
         return None
 
@@ -608,19 +594,23 @@ def run_ours(args, wl, scheme, world, rank, local):
     if rank != 0:
         return
     # The gather's L2 side (the level pair, 16 N^2 B, is L2-resident): snapshot
-    # bytes per particle-step over the particle stage's time, against a
-    # streaming read of an L2-resident buffer measured here.
-    l2_peak = l2_read_gbs(dev)
+    # bytes per particle-step over the particle stage's time, and the L2
+    # throughput ncu measured for the same kernel (percent of the hardware's
+    # peak; a library copy or reduction does not reach that peak, so none is
+    # timed here as a denominator).
     parts_per_s = wl.particles / (part_ms * 1e-3)
+    try:
+        lts_pct = float(recorded_profile(args.scheme)["lts_throughput_pct"])
+    except (KeyError, ValueError):
+        lts_pct = None
     gather = {"scheme": args.scheme, "unit": "GB/s",
               "plain_bytes_per_particle_step": GATHER_PLAIN[scheme],
               "cached_bytes_per_particle_step": GATHER_CACHED[scheme],
               "achieved_plain": GATHER_PLAIN[scheme] * parts_per_s / 1e9,
               "achieved_cached": GATHER_CACHED[scheme] * parts_per_s / 1e9,
-              "l2_read_peak": l2_peak,
-              "peak_kind": "measured in this run: torch sum of a 24 MiB L2-resident FP32 buffer",
-              "frac_plain": GATHER_PLAIN[scheme] * parts_per_s / 1e9 / l2_peak,
-              "frac_cached": GATHER_CACHED[scheme] * parts_per_s / 1e9 / l2_peak}
+              "l2_throughput_pct_of_peak": lts_pct,
+              "l2_source": "ncu lts__throughput of the same kernel and workload "
+                           "(profiles/k_rk4_<scheme>_traffic.txt), null if the kernel changed since"}
     value = aggregate_rate(wl.particles * args.steps, world, total_ms * 1e-3)
     srt = sorted(step_ms)
     p50 = srt[len(srt) // 2]
