@@ -31,6 +31,12 @@ constexpr int kRK4MaxThreads = 512;
 #ifndef EL_RK4_CUBIC_MIN_BLOCKS
 #define EL_RK4_CUBIC_MIN_BLOCKS 1
 #endif
+// The cubic kernels' register cap: 96 (4-8 B of spills) fits 5 blocks of 128
+// threads per SM against 4 at their natural 120, and measured 8-10 % faster at
+// 1024^2 (4 and 16 particles per cell); 80 spills 250 B and is slower.
+#ifndef EL_RK4_CUBIC_MAXNREG
+#define EL_RK4_CUBIC_MAXNREG 96
+#endif
 #ifndef EL_RK4_PREFETCH_WAVES
 #define EL_RK4_PREFETCH_WAVES 1.0
 #endif
@@ -84,7 +90,8 @@ __device__ __forceinline__ int species_of(const unsigned (&begin)[kMaxSpecies], 
 // a grid-stride loop over runs measured 15-18 % slower (more spills, and a
 // block no longer retires between runs).
 template <int SCHEME, bool PSI>
-__global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_MIN_BLOCKS : EL_RK4_CUBIC_MIN_BLOCKS) k_rk4(const __grid_constant__ RK4Args a) {
+__global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_MIN_BLOCKS : EL_RK4_CUBIC_MIN_BLOCKS)
+    __maxnreg__(SCHEME == 1 || SCHEME == 2 ? EL_RK4_CUBIC_MAXNREG : 128) k_rk4(const __grid_constant__ RK4Args a) {
     const int s = species_of(a.block_begin, blockIdx.x);
     const SpeciesDev& sd = a.table[s];
     const int first = (int)(blockIdx.x - a.block_begin[s]) * (int)blockDim.x;
