@@ -74,3 +74,38 @@ def test_reruns_are_bitwise_identical(interp):
     for x, y, z in zip(a, b, c):
         np.testing.assert_array_equal(x, y)
         np.testing.assert_array_equal(x, z)
+
+
+def test_non_finite_host_inputs_are_refused_and_leave_the_flow_unchanged():
+    # NaN / Inf injected through every host input: the initial vorticity,
+    # particle positions (and positions too far out for the image count),
+    # particle velocities and the Stokes number.  Each call fails with
+    # EL_EINVAL before any device work, and a flow keeps its state.
+    n = 32
+    w0 = inputs.decaying_turbulence(n, 3, k0=4.0)
+    for bad in (np.nan, np.inf, -np.inf):
+        w = w0.copy()
+        w[5, 7] = bad
+        with pytest.raises(elpath.ElpathError) as e:
+            elpath.Flow(n, 1e-3, 1e-3, w, interp=0, max_species=1, max_particles=10)
+        assert e.value.status == 1 and "non-finite" in str(e.value)
+    g = elpath.Flow(n, 1e-3, 1e-3, w0, interp=1, max_species=2, max_particles=200)
+    xy = inputs.uniform_positions(100, 5)
+    g.set_particles(0, xy, 1.0)
+    g.step(3)
+    before = [g.field(0)] + list(g.particles(0, 100))
+    for bad_xy, bad_v, st in ((np.nan, 0.0, 1.0), (np.inf, 0.0, 0.0), (2e9, 0.0, 0.0),
+                              (0.5, np.nan, 1.0), (0.5, 0.0, np.nan), (0.5, 0.0, np.inf)):
+        p = xy.copy()
+        p[17, 1] = bad_xy if bad_xy != 0.5 else p[17, 1]
+        v = np.zeros_like(p)
+        v[3, 0] = bad_v
+        with pytest.raises(elpath.ElpathError) as e:
+            g.set_particles(0, p, st, v)
+        assert e.value.status == 1
+    after = [g.field(0)] + list(g.particles(0, 100))
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+    g.step(2)                                        # still steps normally
+    assert g.stats()["finite"]
+    g.close()
