@@ -128,8 +128,12 @@ el_status el_create_kinematic(const el_flow_desc* desc, const el_kinematic* kin,
 
 /* Place np particles in species slot `species` (0..max_species-1).
  * st = 0: passive tracers (Eq. 2); st > 0: inertial particles (Eq. 3).
- * xy: host, 2*np doubles (x0, y0, x1, y1, ...), any real value: positions are
- * unwrapped and mapped periodically for field evaluation (Sec. 3.2).
+ * xy: host, 2*np doubles (x0, y0, x1, y1, ...), finite and at most 1e9 in
+ * magnitude: positions are unwrapped and mapped periodically for field
+ * evaluation (Sec. 3.2).  A non-finite or larger position, or a non-finite
+ * velocity, gives EL_EINVAL naming its first index, with the slot unchanged
+ * (checked on the device after the copy when the slot already has the
+ * capacity, else on the host before it is carved).
  * vxy: host, 2*np doubles of initial particle velocity, or NULL for zero slip
  * (velocity = interpolated fluid velocity at the position, current level).
  * Re-placing a slot replaces its particles; the positions passed become the

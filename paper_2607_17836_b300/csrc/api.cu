@@ -142,6 +142,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* py = take(n * 4);
     char* table = take(sizeof(SpeciesDev) * kMaxSpecies);
     char* check = take(4 * sizeof(uint32_t));
+    char* bad_input = take(sizeof(unsigned long long));
     char* red = take((size_t)kRedBlocks * 3 * 8);
     char* red_out = take(64 * 8);
     char* boxes = take((size_t)kBoxes * kBoxes * 8);
@@ -172,6 +173,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->pre_y = (float*)py;
         f->table = (SpeciesDev*)table;
         f->check = (uint32_t*)check;
+        f->bad_input = (unsigned long long*)bad_input;
         f->red = (double*)red;
         f->red_out = (double*)red_out;
         f->boxes = (unsigned long long*)boxes;
@@ -519,17 +521,24 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
     if (f->d.interp == EL_ANALYTIC && st > 0.0)
         return fail(f, EL_EINVAL, "EL_ANALYTIC flows take tracers (st = 0) only");
     if (np > 0 && !xy) return fail(f, EL_EINVAL, "xy is NULL");
-    for (int64_t q = 0; q < 2 * np; q++)
-        if (!std::isfinite(xy[q]) || std::fabs(xy[q]) > 1e9)
-            return fail(f, EL_EINVAL, "xy[%lld] is not finite or beyond 1e9", (long long)q);
-    if (vxy && st > 0.0)
-        for (int64_t q = 0; q < 2 * np; q++)
-            if (!std::isfinite(vxy[q])) return fail(f, EL_EINVAL, "vxy[%lld] is not finite", (long long)q);
     Species& sp = f->sp[species];
+    // Positions (finite, |x| <= 1e9) and velocities (finite) are checked on
+    // the device after the copy when the species already has the capacity
+    // (the copy lands in scratch, so a refused call still changes nothing);
+    // a call that must first carve capacity checks them here.
+    const bool check_on_device = np <= sp.cap;
+    if (!check_on_device) {
+        for (int64_t q = 0; q < 2 * np; q++)
+            if (!(std::fabs(xy[q]) <= 1e9))
+                return fail(f, EL_EINVAL, "xy[%lld] is not finite or beyond 1e9", (long long)q);
+        if (vxy && st > 0.0)
+            for (int64_t q = 0; q < 2 * np; q++)
+                if (!std::isfinite(vxy[q])) return fail(f, EL_EINVAL, "vxy[%lld] is not finite", (long long)q);
+    }
     if (!carve_species(f, sp, np))
         return fail(f, EL_EINVAL, "particle capacity exhausted (max_particles=%lld)",
                     (long long)f->d.max_particles);
-    EL_TRY(particles_set(f, species, np, st, xy, vxy));
+    EL_TRY(particles_set(f, species, np, st, xy, vxy, check_on_device));
     drop_graphs(f);
     batch_member_changed(f->batch);
     if (f->d.sort_every > 0) f->since_sort = f->d.sort_every;  // bin the new particles first

@@ -98,6 +98,7 @@ struct el_flow {
     el::SpeciesDev* table = nullptr;  // device copy of h_table
     el::SpeciesDev h_table[el::kMaxSpecies] = {};
     uint32_t* check = nullptr;    // EL_CHECK_BOUNDS builds: violations, first particle, its species
+    unsigned long long* bad_input = nullptr;  // first bad index of an uploaded particle set
     double* red = nullptr;        // reduction partials
     double* red_out = nullptr;    // reduced scalars (device)
     unsigned long long* boxes = nullptr;  // kBoxes^2 counters
@@ -192,7 +193,7 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn);
 
 // ---- particles (particles.cu) ---------------------------------------------------
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
-                        const double* vxy);
+                        const double* vxy, bool check_on_device);
 el_status particles_step_all(el_flow* f, int64_t step);  // K6, every species in one launch
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
 // msd x, msd y, cluster, <dx^4>, <dy^4> (the squared displacements' second moments)

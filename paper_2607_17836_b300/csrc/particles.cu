@@ -18,6 +18,8 @@
 #include "common.cuh"
 #include "stages.cuh"
 
+#include <algorithm>
+
 namespace el {
 namespace {
 
@@ -151,6 +153,21 @@ __device__ float2 fluid_at_scheme(int scheme, const float4* snap, int n, int ci,
     if (scheme == 0) return fluid_at_dispatch<0>(snap, n, ci, cj, ox, oy, wa, wb);
     if (scheme == 1) return fluid_at_dispatch<1>(snap, n, ci, cj, ox, oy, wa, wb);
     return fluid_at_dispatch<2>(snap, n, ci, cj, ox, oy, wa, wb);
+}
+
+// The smallest index of an uploaded value that set_particles refuses: a
+// position that is not finite or beyond 1e9 in magnitude (index into xy), else
+// a velocity that is not finite (index into vxy, tagged kBadVelocity); the
+// word stays all ones when every value is good.
+constexpr unsigned long long kBadVelocity = 1ull << 62;
+
+__global__ void k_check_inputs(const double* __restrict__ xy, const double* __restrict__ vxy,
+                               int64_t count, unsigned long long* __restrict__ first_bad) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (!(fabs(xy[q]) <= 1e9)) atomicMin(first_bad, (unsigned long long)q);
+        if (vxy && !isfinite(vxy[q])) atomicMin(first_bad, kBadVelocity | (unsigned long long)q);
+    }
 }
 
 // K9: split-precision state from FP64 positions; velocity from vxy, or zero
@@ -297,7 +314,7 @@ static el_status upload_table(el_flow* f) {
 }
 
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
-                        const double* vxy) {
+                        const double* vxy, bool check_on_device) {
     Species& sp = f->sp[s];
     const int T = 256;
     const int cur = sp.cur;
@@ -310,6 +327,23 @@ el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* 
         EL_CUDA_OK(f, cudaMemcpyAsync(stage + 2 * np, vxy, (size_t)np * 2 * sizeof(double),
                                       cudaMemcpyHostToDevice, f->stream));
         d_vxy = stage + 2 * np;
+    }
+    if (check_on_device && np > 0) {
+        // the staged values, before anything of the species changes
+        unsigned long long first = 0;
+        EL_CUDA_OK(f, cudaMemsetAsync(f->bad_input, 0xff, sizeof first, f->stream));
+        const int64_t cnt = 2 * np;
+        const unsigned grid = (unsigned)std::min<int64_t>(blocks_for(cnt, T), 4096);
+        k_check_inputs<<<grid, T, 0, f->stream>>>(stage, d_vxy, cnt, f->bad_input);
+        EL_LAUNCHED(f);
+        EL_CUDA_OK(f, cudaMemcpyAsync(&first, f->bad_input, sizeof first, cudaMemcpyDeviceToHost,
+                                      f->stream));
+        EL_CUDA_OK(f, cudaStreamSynchronize(f->stream));
+        if (first != ~0ull) {
+            if (first & kBadVelocity)
+                return fail(f, EL_EINVAL, "vxy[%lld] is not finite", (long long)(first & ~kBadVelocity));
+            return fail(f, EL_EINVAL, "xy[%lld] is not finite or beyond 1e9", (long long)first);
+        }
     }
     if (np > 0) {
         k_init<<<blocks_for(np, T), T, 0, f->stream>>>(

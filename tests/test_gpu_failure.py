@@ -80,7 +80,9 @@ def test_non_finite_host_inputs_are_refused_and_leave_the_flow_unchanged():
     # NaN / Inf injected through every host input: the initial vorticity,
     # particle positions (and positions too far out for the image count),
     # particle velocities and the Stokes number.  Each call fails with
-    # EL_EINVAL before any device work, and a flow keeps its state.
+    # EL_EINVAL and a flow keeps its state.  Positions and velocities are
+    # checked on the host when the species needs new capacity, on the device
+    # (after the copy into scratch) when it has it: both paths are taken.
     n = 32
     w0 = inputs.decaying_turbulence(n, 3, k0=4.0)
     for bad in (np.nan, np.inf, -np.inf):
@@ -94,15 +96,26 @@ def test_non_finite_host_inputs_are_refused_and_leave_the_flow_unchanged():
     g.set_particles(0, xy, 1.0)
     g.step(3)
     before = [g.field(0)] + list(g.particles(0, 100))
-    for bad_xy, bad_v, st in ((np.nan, 0.0, 1.0), (np.inf, 0.0, 0.0), (2e9, 0.0, 0.0),
-                              (0.5, np.nan, 1.0), (0.5, 0.0, np.nan), (0.5, 0.0, np.inf)):
+    # (position value at xy[17, 1] = element 35, velocity at vxy[3, 0] =
+    # element 6, Stokes number, expected message)
+    cases = ((np.nan, 0.0, 1.0, "xy[35]"), (np.inf, 0.0, 0.0, "xy[35]"), (2e9, 0.0, 0.0, "xy[35]"),
+             (None, np.nan, 1.0, "vxy[6]"), (None, 0.0, np.nan, "st must"),
+             (None, 0.0, np.inf, "st must"))
+    for bad_xy, bad_v, st, msg in cases:
         p = xy.copy()
-        p[17, 1] = bad_xy if bad_xy != 0.5 else p[17, 1]
+        if bad_xy is not None:
+            p[17, 1] = bad_xy
         v = np.zeros_like(p)
         v[3, 0] = bad_v
         with pytest.raises(elpath.ElpathError) as e:
             g.set_particles(0, p, st, v)
-        assert e.value.status == 1
+        assert e.value.status == 1 and msg in str(e.value), str(e.value)
+    for bad in (np.nan, np.inf):                     # species 1 has no capacity yet: host check
+        p = xy.copy()
+        p[40, 0] = bad
+        with pytest.raises(elpath.ElpathError) as e:
+            g.set_particles(1, p, 0.0)
+        assert e.value.status == 1 and "xy[80]" in str(e.value)
     after = [g.field(0)] + list(g.particles(0, 100))
     for a, b in zip(before, after):
         np.testing.assert_array_equal(a, b)
