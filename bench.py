@@ -64,7 +64,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_2607_17836_b300/csrc/particles.cu", "paper_2607_17836_b300/csrc/interp.cuh",
+    for rel in ("paper_2607_17836_b300/csrc/rk4.cu", "paper_2607_17836_b300/csrc/interp.cuh",
                 "paper_2607_17836_b300/csrc/stages.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())

@@ -132,8 +132,7 @@ el_status el_create_kinematic(const el_flow_desc* desc, const el_kinematic* kin,
  * magnitude: positions are unwrapped and mapped periodically for field
  * evaluation (Sec. 3.2).  A non-finite or larger position, or a non-finite
  * velocity, gives EL_EINVAL naming its first index, with the slot unchanged
- * (checked on the device after the copy when the slot already has the
- * capacity, else on the host before it is carved).
+ * (the values are checked on the device, on the staged copy).
  * vxy: host, 2*np doubles of initial particle velocity, or NULL for zero slip
  * (velocity = interpolated fluid velocity at the position, current level).
  * Re-placing a slot replaces its particles; the positions passed become the

@@ -523,22 +523,20 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
     if (np > 0 && !xy) return fail(f, EL_EINVAL, "xy is NULL");
     Species& sp = f->sp[species];
     // Positions (finite, |x| <= 1e9) and velocities (finite) are checked on
-    // the device after the copy when the species already has the capacity
-    // (the copy lands in scratch, so a refused call still changes nothing);
-    // a call that must first carve capacity checks them here.
-    const bool check_on_device = np <= sp.cap;
-    if (!check_on_device) {
-        for (int64_t q = 0; q < 2 * np; q++)
-            if (!(std::fabs(xy[q]) <= 1e9))
-                return fail(f, EL_EINVAL, "xy[%lld] is not finite or beyond 1e9", (long long)q);
-        if (vxy && st > 0.0)
-            for (int64_t q = 0; q < 2 * np; q++)
-                if (!std::isfinite(vxy[q])) return fail(f, EL_EINVAL, "vxy[%lld] is not finite", (long long)q);
-    }
+    // the device, on the staged copy, before anything of the slot changes.
+    // Capacity carved for this call is host bookkeeping only, handed back if
+    // the check refuses the data, so a refused call changes nothing.
+    const Species kept = sp;
+    const size_t kept_used = f->pool_used;
     if (!carve_species(f, sp, np))
         return fail(f, EL_EINVAL, "particle capacity exhausted (max_particles=%lld)",
                     (long long)f->d.max_particles);
-    EL_TRY(particles_set(f, species, np, st, xy, vxy, check_on_device));
+    const el_status placed = particles_set(f, species, np, st, xy, vxy);
+    if (placed == EL_EINVAL) {
+        sp = kept;
+        f->pool_used = kept_used;
+    }
+    if (placed != EL_OK) return placed;
     drop_graphs(f);
     batch_member_changed(f->batch);
     if (f->d.sort_every > 0) f->since_sort = f->d.sort_every;  // bin the new particles first

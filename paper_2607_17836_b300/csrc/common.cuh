@@ -193,7 +193,7 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn);
 
 // ---- particles (particles.cu) ---------------------------------------------------
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
-                        const double* vxy, bool check_on_device);
+                        const double* vxy);
 el_status particles_step_all(el_flow* f, int64_t step);  // K6, every species in one launch
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
 // msd x, msd y, cluster, <dx^4>, <dy^4> (the squared displacements' second moments)

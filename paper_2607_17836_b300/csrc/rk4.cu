@@ -1,0 +1,183 @@
+// K6: the particle step (Secs. 2.2, 2.3, 3.3, 3.4; Algorithm 1): one RK4 step
+// of every species (Eq. 12 tracers, Eq. 14 inertial) in one launch, between
+// fluid levels n and n+1, fused with the gathers (Eqs. 15-22), the time blend
+// (Eqs. 23-24) and the wrap/carry write-back of the split-precision state
+// (cell, FP32 offset, int32 image; see particles.cu).
+#include "common.cuh"
+#include "stages.cuh"
+
+namespace el {
+namespace {
+
+constexpr int kRK4MaxThreads = 512;
+// Blocks of kRK4MaxThreads per SM the kernels are compiled for, which caps
+// their registers (2 -> 64, 3 -> 40): occupancy hides the two dependent
+// memory round trips of a particle (state, then stencil).
+#ifndef EL_RK4_BILINEAR_MIN_BLOCKS
+#define EL_RK4_BILINEAR_MIN_BLOCKS 3
+#endif
+#ifndef EL_RK4_CUBIC_MIN_BLOCKS
+#define EL_RK4_CUBIC_MIN_BLOCKS 1
+#endif
+// The cubic kernels' register cap: 96 (4-8 B of spills) fits 5 blocks of 128
+// threads per SM against 4 at their natural 120, and measured 8-10 % faster at
+// 1024^2 (4 and 16 particles per cell); 80 spills 250 B and is slower.
+#ifndef EL_RK4_CUBIC_MAXNREG
+#define EL_RK4_CUBIC_MAXNREG 96
+#endif
+#ifndef EL_RK4_PREFETCH_WAVES
+#define EL_RK4_PREFETCH_WAVES 1.0
+#endif
+
+struct RK4Args {
+    const float4* snap;
+    const float2* psi;        // streamfunction pair (tracer_velocity = 1), else nullptr
+    const SpeciesDev* table;  // device-resident: the sort flips `cur` there
+    int n, log2n;
+    float dt, h;              // h = dt * n / (2 pi): grid units per unit velocity
+    unsigned block_begin[kMaxSpecies];
+    KinArgs kin;              // EL_ANALYTIC only: the prescribed field at the stage times
+    uint32_t* check;          // EL_CHECK_BOUNDS builds: the flow's violation words
+    int prefetch;             // particles ahead whose state a block prefetches into L2 (0: none)
+};
+
+// Bulk prefetch into L2 of the state of the block `ahead` particles later in
+// the same species (its cell, offset and velocity rows), issued by thread 0.
+// The state stream is latency-bound: a block that waits on its own loads and
+// then on its L2 gathers keeps few HBM requests in flight, so the block about
+// one resident wave earlier asks for them.  Only whole 16-byte units inside
+// [q0, np) are prefetched (start aligned: q0 is a multiple of the block size,
+// the arrays 256-byte aligned); a prefetch changes no data and waits for
+// nothing.
+__device__ __forceinline__ void prefetch_state(const SpeciesDev& sd, int first, int ahead) {
+    const int q0 = first + ahead;
+    if (threadIdx.x != 0 || ahead <= 0 || q0 >= sd.np) return;
+    const unsigned cnt = (unsigned)min((int)blockDim.x, sd.np - q0);
+    const unsigned b4 = (cnt * 4u) & ~15u, b8 = (cnt * 8u) & ~15u;
+    const int cur = sd.cur;
+    if (b4) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.cell[cur] + q0), "r"(b4) : "memory");
+    if (b8) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.off[cur] + q0), "r"(b8) : "memory");
+    if (b8 && sd.inertial)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.vel[cur] + q0), "r"(b8) : "memory");
+}
+
+// The species of block b: the largest k with block_begin[k] <= b (ascending;
+// slots past the last species hold UINT_MAX), by a three-step binary search.
+__device__ __forceinline__ int species_of(const unsigned (&begin)[kMaxSpecies], unsigned b) {
+    static_assert(kMaxSpecies == 8, "three halvings");
+    int s = 0;
+    if (b >= begin[s + 4]) s += 4;
+    if (b >= begin[s + 2]) s += 2;
+    if (b >= begin[s + 1]) s += 1;
+    return s;
+}
+
+// K6: one RK4 step of every species in one launch (blocks are split between
+// species by block_begin), between levels n and n+1 (rk4_particle).  One
+// block per run of particles: at the register cap that gives 75 % occupancy
+// a grid-stride loop over runs measured 15-18 % slower (more spills, and a
+// block no longer retires between runs).
+template <int SCHEME, bool PSI>
+__global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_MIN_BLOCKS : EL_RK4_CUBIC_MIN_BLOCKS)
+    __maxnreg__(SCHEME == 1 || SCHEME == 2 ? EL_RK4_CUBIC_MAXNREG : 128) k_rk4(const __grid_constant__ RK4Args a) {
+    const int s = species_of(a.block_begin, blockIdx.x);
+    const SpeciesDev& sd = a.table[s];
+    const int first = (int)(blockIdx.x - a.block_begin[s]) * (int)blockDim.x;
+    prefetch_state(sd, first, a.prefetch);
+    const int p = first + (int)threadIdx.x;
+    if (p >= sd.np) return;
+#if EL_CHECK_BOUNDS
+    {
+        const uint32_t c = sd.cell[sd.cur][p];
+        const float2 o = sd.off[sd.cur][p];
+        const bool bad = (c & 0xffffu) >= (uint32_t)a.n || (c >> 16) >= (uint32_t)a.n ||
+                         !(o.x >= 0.f && o.x < 1.f) || !(o.y >= 0.f && o.y < 1.f);
+        if (bad && atomicAdd(a.check, 1u) == 0u) {
+            a.check[1] = (uint32_t)p;
+            a.check[2] = (uint32_t)s;
+        }
+    }
+#endif
+    rk4_particle<SCHEME, PSI>(a.snap, a.psi, a.n, a.log2n, a.dt, a.h, sd, p, &a.kin);
+}
+}  // namespace
+
+// Resident blocks of k_rk4 on the whole GPU at the flow's block size.
+template <int SCHEME, bool PSI>
+static int rk4_wave_blocks(int threads) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rk4<SCHEME, PSI>, threads, 0);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm * sms;
+}
+
+// The prefetch distance of k_rk4 in particles, cached per block size:
+// EL_RK4_PREFETCH_WAVES resident waves (SMs x resident blocks), a whole number
+// of blocks.  Measured at 1024^2: 0.5, 1 and 2 waves time alike, 4-5 % faster
+// than no prefetch for every scheme and particle count.
+static int rk4_prefetch_distance(el_flow* f) {
+    const int T = f->rk4_threads;
+    if (f->prefetch_threads == T) return f->prefetch_particles;
+    int wave = 0;
+    const bool psi = f->psi_plane >= 0;
+    switch (f->d.interp) {
+        case EL_BILINEAR: wave = psi ? rk4_wave_blocks<0, true>(T) : rk4_wave_blocks<0, false>(T); break;
+        case EL_CATMULL_ROM: wave = psi ? rk4_wave_blocks<1, true>(T) : rk4_wave_blocks<1, false>(T); break;
+        case EL_BSPLINE: wave = psi ? rk4_wave_blocks<2, true>(T) : rk4_wave_blocks<2, false>(T); break;
+        default: wave = rk4_wave_blocks<3, false>(T); break;
+    }
+    f->prefetch_particles = (int)((double)wave * EL_RK4_PREFETCH_WAVES + 0.5) * T;
+    f->prefetch_threads = T;
+    return f->prefetch_particles;
+}
+
+// K6 for every species of the flow in one launch, step number `step`
+// (levels step and step + 1: pair snap[step % 2]).
+el_status particles_step_all(el_flow* f, int64_t step) {
+    NvtxRange range("particles_step");
+    RK4Args a{};
+    a.snap = f->snap[step % 2];
+    a.psi = f->psi_plane >= 0 ? f->psi[step % 2] : nullptr;
+    a.table = f->table;
+    a.check = f->check;
+    a.n = f->n;
+    a.log2n = f->log2n;
+    a.dt = (float)f->d.dt;
+    a.h = (float)(f->d.dt * (double)f->n / kTwoPi);
+    a.prefetch = rk4_prefetch_distance(f);
+    unsigned blocks = 0;
+    int ns = 0;
+    for (int s = 0; s < f->d.max_species; s++) {
+        // every slot up to the last non-empty one takes part (empty ones get no blocks)
+        a.block_begin[s] = blocks;
+        blocks += f->sp[s].np > 0 ? blocks_for(f->sp[s].np, f->rk4_threads) : 0;
+        if (f->sp[s].np > 0) ns = s + 1;
+    }
+    if (ns == 0) return EL_OK;
+    // empty slots share block_begin with the next slot, so the last slot with
+    // a given block_begin (the non-empty one) wins the select in the kernel;
+    // slots past max_species are never selected
+    for (int s = f->d.max_species; s < kMaxSpecies; s++) a.block_begin[s] = 0xffffffffu;
+    const int T = f->rk4_threads;
+    if (f->d.interp == EL_ANALYTIC) {
+        a.kin = kinematic_stage_args(f, step);
+        k_rk4<3, false><<<blocks, T, 0, f->stream>>>(a);
+    } else if (f->psi_plane < 0) {
+        switch (f->d.interp) {
+            case EL_BILINEAR: k_rk4<0, false><<<blocks, T, 0, f->stream>>>(a); break;
+            case EL_CATMULL_ROM: k_rk4<1, false><<<blocks, T, 0, f->stream>>>(a); break;
+            default: k_rk4<2, false><<<blocks, T, 0, f->stream>>>(a); break;
+        }
+    } else {
+        switch (f->d.interp) {
+            case EL_BILINEAR: k_rk4<0, true><<<blocks, T, 0, f->stream>>>(a); break;
+            case EL_CATMULL_ROM: k_rk4<1, true><<<blocks, T, 0, f->stream>>>(a); break;
+            default: k_rk4<2, true><<<blocks, T, 0, f->stream>>>(a); break;
+        }
+    }
+    EL_LAUNCHED(f);
+    return EL_OK;
+}
+
+}  // namespace el

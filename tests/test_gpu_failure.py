@@ -81,8 +81,9 @@ def test_non_finite_host_inputs_are_refused_and_leave_the_flow_unchanged():
     # particle positions (and positions too far out for the image count),
     # particle velocities and the Stokes number.  Each call fails with
     # EL_EINVAL and a flow keeps its state.  Positions and velocities are
-    # checked on the host when the species needs new capacity, on the device
-    # (after the copy into scratch) when it has it: both paths are taken.
+    # checked on the device, on the staged copy; capacity carved for a refused
+    # call is handed back (species 1 below has none before the bad calls, and
+    # takes a good set afterwards).
     n = 32
     w0 = inputs.decaying_turbulence(n, 3, k0=4.0)
     for bad in (np.nan, np.inf, -np.inf):
@@ -110,15 +111,19 @@ def test_non_finite_host_inputs_are_refused_and_leave_the_flow_unchanged():
         with pytest.raises(elpath.ElpathError) as e:
             g.set_particles(0, p, st, v)
         assert e.value.status == 1 and msg in str(e.value), str(e.value)
-    for bad in (np.nan, np.inf):                     # species 1 has no capacity yet: host check
-        p = xy.copy()
-        p[40, 0] = bad
-        with pytest.raises(elpath.ElpathError) as e:
-            g.set_particles(1, p, 0.0)
-        assert e.value.status == 1 and "xy[80]" in str(e.value)
+    for _ in range(3):                               # species 1 has no capacity yet
+        for bad in (np.nan, np.inf):
+            p = xy.copy()
+            p[40, 0] = bad
+            with pytest.raises(elpath.ElpathError) as e:
+                g.set_particles(1, p, 0.0)
+            assert e.value.status == 1 and "xy[80]" in str(e.value)
     after = [g.field(0)] + list(g.particles(0, 100))
     for a, b in zip(before, after):
         np.testing.assert_array_equal(a, b)
-    g.step(2)                                        # still steps normally
-    assert g.stats()["finite"]
+    assert g.stats()["np"][1] == 0
+    g.set_particles(1, xy, 0.0)                      # the refused carves were handed back:
+    g.step(2)                                        # 200 = max_particles still fits
+    s = g.stats()
+    assert s["finite"] and s["np"][:2] == [100, 100]
     g.close()
