@@ -361,17 +361,35 @@ def run_ensemble(args, dev, members=64, steps=20):
     ev[3].record(batch.stream)
     batch.synchronize()
     bat_ms = ev[2].elapsed_time(ev[3])
+    launches = (batch.kernel_launches() - launches0) / steps
+    batch.close()
+    # the same members in a batch with one FFT pool per grid size (each
+    # member's transforms batched with the others of its size)
+    sizes = {n: sum(1 for w in wls if w.n == n) for n in (256, 512, 1024)}
+    pooled = elpath.Batch(members, device=dev)
+    pool_bytes = sum(pooled.add_fft_pool(n, c) for n, c in sizes.items() if c > 0)
+    for g in flows:
+        pooled.add(g)
+    pooled.step(3)
+    ev[2].record(pooled.stream)
+    pooled.step(steps)
+    ev[3].record(pooled.stream)
+    pooled.synchronize()
+    pool_ms = ev[2].elapsed_time(ev[3])
+    pooled.close()
     out = {"workload": f"{members} decaying-turbulence members, n in {{256, 512, 1024}}, "
                        f"1e4-1e6 particles each (log-uniform), St in {{0, 0.1, 1, 10}}",
            "members": members, "particles": total, "steps": steps,
-           "sizes": {str(n): sum(1 for w in wls if w.n == n) for n in (256, 512, 1024)},
-           "batched_particle_steps_per_s": total * steps / (bat_ms * 1e-3),
+           "sizes": {str(n): c for n, c in sizes.items()},
+           "batched_particle_steps_per_s": total * steps / (pool_ms * 1e-3),
            "sequential_particle_steps_per_s": total * steps / (seq_ms * 1e-3),
-           "speedup": seq_ms / bat_ms, "batched_ms_per_step": bat_ms / steps,
+           "speedup": seq_ms / pool_ms, "batched_ms_per_step": pool_ms / steps,
            "sequential_ms_per_step": seq_ms / steps,
-           "batched_launches_per_step": (batch.kernel_launches() - launches0) / steps,
+           "batched_launches_per_step": launches,
+           "fft_pools": {"bytes": pool_bytes,
+                         "without_pools_particle_steps_per_s": total * steps / (bat_ms * 1e-3),
+                         "without_pools_ms_per_step": bat_ms / steps},
            "tuning": tuning}
-    batch.close()
     for g in flows:
         g.close()
     torch.cuda.empty_cache()

@@ -248,8 +248,25 @@ el_status el_batch_autotune(el_batch* batch, int32_t trial_steps, el_tuning* bes
 int32_t el_batch_size(const el_batch* batch);
 int64_t el_batch_kernel_launches(const el_batch* batch);
 const char* el_batch_last_error(const el_batch* batch);
-/* Remove every member and free the batch's host state. */
+/* Remove every member and free the batch's host state (and its pools' plans). */
 el_status el_batch_destroy(el_batch* batch);
+
+/* FFT pools (optional).  The transforms of Eqs. 4-8 for members of one class
+ * -- the grid n and the inverse-transform plane count that `desc` implies
+ * (4, +2 with the B-spline prefilter, +1 with tracer_velocity = 1) -- can run
+ * as one batched cuFFT call per transform over a pool of `slots` members,
+ * instead of one call per member (cuFFT's time per plane falls steeply with
+ * the batch count).  A pool is device memory the caller provides and keeps
+ * until el_batch_destroy, at least el_batch_fft_pool_bytes(desc, slots)
+ * bytes, 256-byte aligned (0: invalid desc or slots outside [1, 4096]).
+ * A flow added with el_batch_add after the pool takes a free slot of a pool
+ * of its class if there is one (else it transforms alone, as before); it
+ * keeps the slot until it leaves.  The results equal the per-member path's up
+ * to the rounding of cuFFT's batched kernels.  EL_ENOMEM when `bytes` is too
+ * small; EL_ECUFFT when the plans cannot be made. */
+size_t el_batch_fft_pool_bytes(const el_flow_desc* desc, int32_t slots);
+el_status el_batch_add_fft_pool(el_batch* batch, const el_flow_desc* desc, int32_t slots,
+                                void* dev_workspace, size_t bytes);
 
 /* Mean-square displacement and clustering index of np particles, computed
  * without allocating any memory.  The paper has no counterpart: this is a

@@ -339,6 +339,10 @@ bool species_fit(const el_flow* f, const int64_t* np) {
 
 bool carve_species_slot(el_flow* f, int s, int64_t np) { return carve_species(f, f->sp[s], np); }
 
+const char* flow_desc_problem(const el_flow_desc* d) { return check_desc(d); }
+
+int flow_planes(const el_flow_desc& d) { return planes_of(d); }
+
 void drop_graphs(el_flow* f) {
     for (int k = 0; k < 2; k++) {
         cudaGraphExec_t* gs[3] = {&f->g_fluid[k], &f->g_part[k], &f->g_both[k]};

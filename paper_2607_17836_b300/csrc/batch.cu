@@ -6,6 +6,8 @@
 //   cuFFT C2R per member, on forked branches (they run concurrently)
 //   k_batch_nonlinear (persistent, every member's nodes)   nonlinear term + snapshot
 //   cuFFT R2C per member, on forked branches
+//     (members in a slot of an FFT pool: one batched C2R and one batched R2C
+//     per pool instead, over the pool's contiguous slots)
 //   k_batch_rk4<S>    (persistent, every member's species) RK4 particle step,
 //                     one launch per interpolation scheme present
 //   k_batch_advance                                        per-member step counters
@@ -136,8 +138,29 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 using namespace el;
 
+// An FFT pool: caller-provided memory holding the transient transform
+// buffers of `slots` members of one class (grid n, inverse-FFT planes P) one
+// after another, so that one cuFFT plan transforms every slot at once (cuFFT's
+// time per plane falls steeply with the batch count).  Slot s: spectral
+// planes spec + s P nmodes, physical planes phys + s P n^2, nonlinear term
+// nl + s n^2, its transform nhat + s nmodes (N-hat is carried from one step
+// to the next, so it moves into the slot when the member joins and back to
+// the member when it leaves).
+struct FftPool {
+    int n = 0, planes = 0, slots = 0;
+    size_t nmodes = 0, n2 = 0;
+    float2* spec = nullptr;
+    float* phys = nullptr;
+    float* nl = nullptr;
+    float2* nhat = nullptr;
+    void* work = nullptr;
+    cufftHandle c2r = 0, r2c = 0;
+    std::vector<el_flow*> member;  // occupant of each slot (nullptr: free)
+};
+
 struct el_batch {
     cudaStream_t stream = nullptr;
+    std::vector<FftPool> pools;
     int max_members = 0;
     std::vector<el_flow*> members;
     // device tables (in the caller's workspace)
@@ -194,7 +217,7 @@ size_t table_bytes(int max_members) {
            2 * align_up((e + 1) * sizeof(int)) + align_up(e * sizeof(void*));
 }
 
-MemberDev member_of(el_flow* f) {
+MemberDev member_of(const el_batch* b, el_flow* f) {
     MemberDev md{};
     SpecArgs& a = md.spec;
     a.what = f->what;
@@ -232,6 +255,14 @@ MemberDev member_of(el_flow* f) {
     md.dt = (float)f->d.dt;
     md.h = (float)(f->d.dt * (double)f->n / kTwoPi);
     md.step = f->step;
+    if (f->fft_pool >= 0) {  // its transform buffers live in a pool slot
+        const FftPool& p = b->pools[f->fft_pool];
+        const size_t k = (size_t)f->fft_slot;
+        a.spec = p.spec + k * p.planes * p.nmodes;
+        a.nhat = p.nhat + k * p.nmodes;
+        md.phys4 = reinterpret_cast<const float4*>(p.phys + k * p.planes * p.n2);
+        md.nl4 = reinterpret_cast<float4*>(p.nl + k * p.n2);
+    }
     return md;
 }
 
@@ -248,7 +279,7 @@ el_status rebuild_tables(el_batch* b) {
     for (int m = 0; m < M; m++) {
         el_flow* f = b->members[m];
         rk_threads = f->rk4_threads;  // one block size for the whole batch
-        b->h_members.push_back(member_of(f));
+        b->h_members.push_back(member_of(b, f));
         b->h_spec_begin.push_back(b->h_spec_begin.back() + f->n * spec_chunks(f->n));
         b->h_nl_begin.push_back(b->h_nl_begin.back() +
                                 (int)((f->n2 / 4 + kBNlThreads - 1) / kBNlThreads));
@@ -314,9 +345,22 @@ el_status rebuild_tables(el_batch* b) {
 el_status fork_ffts(el_batch* b, cudaStream_t origin, bool c2r) {
     BT_CUDA(b, cudaEventRecord(b->fork_ev, origin));
     for (int k = 0; k < kSideStreams; k++) BT_CUDA(b, cudaStreamWaitEvent(b->side[k], b->fork_ev, 0));
+    size_t branch = 0;
+    for (FftPool& p : b->pools) {
+        if (std::find_if(p.member.begin(), p.member.end(), [](el_flow* f) { return f != nullptr; }) ==
+            p.member.end())
+            continue;
+        cudaStream_t s = b->side[branch++ % kSideStreams];
+        cufftHandle plan = c2r ? p.c2r : p.r2c;
+        if (cufftSetStream(plan, s) != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cufftSetStream");
+        cufftResult r = c2r ? cufftExecC2R(plan, reinterpret_cast<cufftComplex*>(p.spec), p.phys)
+                            : cufftExecR2C(plan, p.nl, reinterpret_cast<cufftComplex*>(p.nhat));
+        if (r != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cuFFT exec (pool) failed (%d)", (int)r);
+    }
     for (size_t m = 0; m < b->members.size(); m++) {
         el_flow* f = b->members[m];
-        cudaStream_t s = b->side[m % kSideStreams];
+        if (f->fft_pool >= 0) continue;
+        cudaStream_t s = b->side[branch++ % kSideStreams];
         cufftHandle plan = c2r ? f->plan_c2r : f->plan_r2c;
         if (cufftSetStream(plan, s) != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cufftSetStream");
         cufftResult r = c2r ? cufftExecC2R(plan, reinterpret_cast<cufftComplex*>(f->spec), f->phys)
@@ -394,6 +438,10 @@ el_status build_batch_graph(el_batch* b, int kind) {
         cufftSetStream(f->plan_c2r, b->stream);
         cufftSetStream(f->plan_r2c, b->stream);
     }
+    for (FftPool& p : b->pools) {
+        cufftSetStream(p.c2r, b->stream);
+        cufftSetStream(p.r2c, b->stream);
+    }
     if (s != EL_OK) {
         if (g) cudaGraphDestroy(g);
         return s;
@@ -412,6 +460,79 @@ el_status launch_graph(el_batch* b, int kind) {
     if (!b->graph[kind]) EL_TRY(build_batch_graph(b, kind));
     BT_CUDA(b, cudaGraphLaunch(b->graph[kind], b->stream));
     b->launches += b->graph_kernels[kind];
+    return EL_OK;
+}
+
+// Byte offsets of a pool's arrays and its total size for (n, planes, slots)
+// and a cuFFT work area of `work` bytes.
+struct PoolLayout {
+    size_t spec, phys, nl, nhat, work, total;
+};
+
+PoolLayout pool_layout(int n, int planes, int slots, size_t work) {
+    const size_t nm = (size_t)n * (n / 2 + 1), n2 = (size_t)n * n, k = (size_t)slots;
+    PoolLayout l{};
+    l.spec = 0;
+    l.phys = l.spec + align_up(k * planes * nm * sizeof(float2));
+    l.nl = l.phys + align_up(k * planes * n2 * sizeof(float));
+    l.nhat = l.nl + align_up(k * n2 * sizeof(float));
+    l.work = l.nhat + align_up(k * nm * sizeof(float2));
+    l.total = l.work + align_up(work);
+    return l;
+}
+
+// The pool's two plans (C2R over slots x planes, R2C over slots), with the
+// work area left to the caller; `work` = the larger of their work areas.
+cufftResult pool_plans(int n, int planes, int slots, cufftHandle* c2r, cufftHandle* r2c, size_t* work) {
+    int dims[2] = {n, n};
+    size_t w0 = 0, w1 = 0;
+    cufftResult r;
+    *c2r = *r2c = 0;
+    if ((r = cufftCreate(c2r)) != CUFFT_SUCCESS) return r;
+    if ((r = cufftCreate(r2c)) != CUFFT_SUCCESS) return r;
+    cufftSetAutoAllocation(*c2r, 0);
+    cufftSetAutoAllocation(*r2c, 0);
+    if ((r = cufftMakePlanMany(*c2r, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, slots * planes,
+                               &w0)) != CUFFT_SUCCESS)
+        return r;
+    if ((r = cufftMakePlanMany(*r2c, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, slots, &w1)) !=
+        CUFFT_SUCCESS)
+        return r;
+    *work = std::max(w0, w1);
+    return CUFFT_SUCCESS;
+}
+
+// Put a joining member into a free slot of a pool of its class, if any;
+// its N-hat moves into the slot (stream-ordered on the batch stream).
+el_status pool_join(el_batch* b, el_flow* f) {
+    for (size_t q = 0; q < b->pools.size(); q++) {
+        FftPool& p = b->pools[q];
+        if (p.n != f->n || p.planes != f->nplanes) continue;
+        for (int k = 0; k < p.slots; k++) {
+            if (p.member[k]) continue;
+            float2* slot_nhat = p.nhat + (size_t)k * p.nmodes;
+            BT_CUDA(b, cudaMemcpyAsync(slot_nhat, f->nhat, p.nmodes * sizeof(float2),
+                                       cudaMemcpyDeviceToDevice, b->stream));
+            p.member[k] = f;
+            f->fft_pool = (int)q;
+            f->fft_slot = k;
+            f->nhat_cur = slot_nhat;
+            return EL_OK;
+        }
+    }
+    return EL_OK;
+}
+
+// A leaving member takes its N-hat back from its slot and frees it.
+el_status pool_leave(el_batch* b, el_flow* f) {
+    if (f->fft_pool < 0) return EL_OK;
+    FftPool& p = b->pools[f->fft_pool];
+    BT_CUDA(b, cudaMemcpyAsync(f->nhat, f->nhat_cur, p.nmodes * sizeof(float2),
+                               cudaMemcpyDeviceToDevice, b->stream));
+    BT_CUDA(b, cudaStreamSynchronize(b->stream));
+    p.member[f->fft_slot] = nullptr;
+    f->fft_pool = f->fft_slot = -1;
+    f->nhat_cur = nullptr;
     return EL_OK;
 }
 
@@ -437,6 +558,67 @@ extern "C" {
 size_t el_batch_workspace_bytes(int32_t max_members) {
     if (max_members <= 0 || max_members > 4096) return 0;
     return table_bytes(max_members);
+}
+
+size_t el_batch_fft_pool_bytes(const el_flow_desc* desc, int32_t slots) {
+    if (flow_desc_problem(desc) || slots < 1 || slots > 4096) return 0;
+    const int planes = flow_planes(*desc);
+    cufftHandle c2r = 0, r2c = 0;
+    size_t work = 0;
+    const cufftResult r = pool_plans(desc->n, planes, slots, &c2r, &r2c, &work);
+    if (c2r) cufftDestroy(c2r);
+    if (r2c) cufftDestroy(r2c);
+    if (r != CUFFT_SUCCESS) return 0;
+    return pool_layout(desc->n, planes, slots, work).total;
+}
+
+el_status el_batch_add_fft_pool(el_batch* b, const el_flow_desc* desc, int32_t slots,
+                                void* dev_workspace, size_t bytes) {
+    if (!b || !desc) return EL_EINVAL;
+    if (const char* why = flow_desc_problem(desc)) return bfail(b, EL_EINVAL, "%s", why);
+    if (slots < 1 || slots > 4096) return bfail(b, EL_EINVAL, "slots out of range");
+    if (!dev_workspace || (uintptr_t)dev_workspace % kAlign)
+        return bfail(b, EL_EINVAL, "pool memory NULL or not 256-byte aligned");
+    FftPool p;
+    p.n = desc->n;
+    p.planes = flow_planes(*desc);
+    p.slots = slots;
+    p.nmodes = (size_t)p.n * (p.n / 2 + 1);
+    p.n2 = (size_t)p.n * p.n;
+    size_t work = 0;
+    cufftResult r = pool_plans(p.n, p.planes, slots, &p.c2r, &p.r2c, &work);
+    const PoolLayout l = pool_layout(p.n, p.planes, slots, work);
+    if (r == CUFFT_SUCCESS && bytes < l.total) {
+        cufftDestroy(p.c2r);
+        cufftDestroy(p.r2c);
+        return bfail(b, EL_ENOMEM, "pool memory has %zu bytes, needs %zu", bytes, l.total);
+    }
+    char* base = static_cast<char*>(dev_workspace);
+    p.spec = reinterpret_cast<float2*>(base + l.spec);
+    p.phys = reinterpret_cast<float*>(base + l.phys);
+    p.nl = reinterpret_cast<float*>(base + l.nl);
+    p.nhat = reinterpret_cast<float2*>(base + l.nhat);
+    p.work = base + l.work;
+    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(p.c2r, p.work);
+    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(p.r2c, p.work);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(p.c2r, b->stream);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(p.r2c, b->stream);
+    if (r != CUFFT_SUCCESS) {
+        if (p.c2r) cufftDestroy(p.c2r);
+        if (p.r2c) cufftDestroy(p.r2c);
+        return bfail(b, EL_ECUFFT, "pool plans failed (%d)", (int)r);
+    }
+    // free slots hold zeros (their transforms run with the occupied ones)
+    cudaError_t e = cudaMemsetAsync(base, 0, l.work, b->stream);
+    if (e != cudaSuccess) {
+        cufftDestroy(p.c2r);
+        cufftDestroy(p.r2c);
+        return bfail(b, EL_ECUDA, "pool clear: %s", cudaGetErrorString(e));
+    }
+    p.member.assign((size_t)slots, nullptr);
+    b->pools.push_back(std::move(p));
+    invalidate(b);
+    return EL_OK;
 }
 
 el_status el_batch_create(int32_t max_members, void* dev_workspace, size_t bytes,
@@ -502,7 +684,7 @@ el_status el_batch_add(el_batch* b, el_flow* f) {
     f->batch = b;
     b->members.push_back(f);
     invalidate(b);
-    return EL_OK;
+    return pool_join(b, f);
 }
 
 el_status el_batch_remove(el_batch* b, el_flow* f) {
@@ -510,6 +692,7 @@ el_status el_batch_remove(el_batch* b, el_flow* f) {
     auto it = std::find(b->members.begin(), b->members.end(), f);
     if (it == b->members.end()) return bfail(b, EL_EINVAL, "flow is not a member");
     BT_CUDA(b, cudaStreamSynchronize(b->stream));
+    EL_TRY(pool_leave(b, f));
     b->members.erase(it);
     f->stream = f->own_stream;
     cufftSetStream(f->plan_c2r, f->stream);
@@ -563,6 +746,10 @@ el_status el_batch_destroy(el_batch* b) {
     if (!b) return EL_EINVAL;
     if (b->stream || !b->members.empty()) cudaStreamSynchronize(b->stream);
     while (!b->members.empty()) el_batch_remove(b, b->members.back());
+    for (FftPool& p : b->pools) {
+        if (p.c2r) cufftDestroy(p.c2r);
+        if (p.r2c) cufftDestroy(p.r2c);
+    }
     for (cudaGraphExec_t g : b->graph)
         if (g) cudaGraphExecDestroy(g);
     for (int k = 0; k < kSideStreams; k++) {

@@ -68,7 +68,7 @@ std::vector<Section> sections(el_flow* f, const int64_t* np, const double* st, i
     s.push_back({f->what, nm});
     s.push_back({f->what_lo, nm});
     s.push_back({f->hist, nm});
-    s.push_back({f->nhat, nm});
+    s.push_back({f->nhat_cur ? f->nhat_cur : f->nhat, nm});  // a batch FFT pool may hold it
     const int pair = (int)((step + 1) % 2);  // pair (n-1, n): level n in its second half
     s.push_back({f->snap[pair], f->n2 * sizeof(float4)});
     if (f->psi_plane >= 0) s.push_back({f->psi[pair], f->n2 * sizeof(float2)});

@@ -119,6 +119,8 @@ struct el_flow {
     int prefetch_particles = 0;
     int sort_shift = 0;        // re-binning key: tiles of 2^sort_shift cells per side
     el_batch* batch = nullptr; // the batch this flow is a member of, if any
+    int fft_pool = -1, fft_slot = -1;  // its slot in one of the batch's FFT pools, if any
+    float2* nhat_cur = nullptr;        // N-hat while it lives in that slot (else nhat)
     cudaStream_t own_stream = nullptr;  // stream given at creation (restored on batch removal)
     int64_t since_sort = 0;
     int64_t launches = 0;
@@ -190,6 +192,10 @@ el_status kinematic_get_field(el_flow* f, int which, double* host_nn);  // omega
 void kinematic_diagnostics(const el_flow* f, double* e3);  // exact E, Z, P
 el_status fluid_refresh_planes(el_flow* f);       // physical planes of the current level
 el_status fluid_get_field(el_flow* f, int which, double* host_nn);
+
+// ---- flow descriptors (api.cu) ----------------------------------------------------
+const char* flow_desc_problem(const el_flow_desc* d);  // nullptr when the descriptor is valid
+int flow_planes(const el_flow_desc& d);                // spectral planes of the inverse FFT
 
 // ---- particles (particles.cu) ---------------------------------------------------
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,

@@ -28,7 +28,7 @@ SYMBOLS = ("el_workspace_bytes", "el_create_flow", "el_create_kinematic", "el_se
            "el_kernel_launches", "el_batch_workspace_bytes", "el_batch_create", "el_batch_add",
            "el_batch_remove", "el_batch_step", "el_batch_autotune", "el_batch_size",
            "el_batch_kernel_launches", "el_batch_last_error", "el_batch_destroy",
-           "el_dispersion_noalloc", "el_save_state", "el_load_state", "el_destroy_flow",
+           "el_batch_fft_pool_bytes", "el_batch_add_fft_pool", "el_dispersion_noalloc", "el_save_state", "el_load_state", "el_destroy_flow",
            "el_last_error")
 NOALLOC_MAX_PARTICLES = 262144
 
@@ -114,6 +114,10 @@ def load(path: str = LIB_PATH):
     lib.el_batch_last_error.argtypes = [P]
     lib.el_batch_last_error.restype = ctypes.c_char_p
     lib.el_batch_destroy.argtypes = [P]
+    lib.el_batch_fft_pool_bytes.argtypes = [ctypes.POINTER(el_flow_desc), I32]
+    lib.el_batch_fft_pool_bytes.restype = ctypes.c_size_t
+    lib.el_batch_add_fft_pool.argtypes = [P, ctypes.POINTER(el_flow_desc), I32, V, ctypes.c_size_t]
+    lib.el_batch_add_fft_pool.restype = ctypes.c_int
     for name in ("el_get_tuning", "el_set_tuning", "el_autotune", "el_batch_create",
                  "el_batch_add", "el_batch_remove", "el_batch_step", "el_batch_autotune",
                  "el_batch_destroy"):
@@ -362,10 +366,29 @@ class Batch:
             raise ElpathError(st, lib.el_last_error(None).decode())
         self._h = h
         self.members = []
+        self.pools = []
 
     def _check(self, st):
         if st != 0:
             raise ElpathError(st, self._lib.el_batch_last_error(self._h).decode())
+
+    def add_fft_pool(self, n, slots, interp=BILINEAR, bspline_prefilter=True, tracer_velocity=0):
+        """An FFT pool for `slots` members of grid n (and the plane count the
+        scheme / prefilter / tracer-velocity options imply); members added
+        afterwards take its slots.  Its device memory is held here until close."""
+        import torch
+        desc = make_desc(n, 0.0, 1.0, interp=interp, bspline_prefilter=bspline_prefilter,
+                         tracer_velocity=tracer_velocity)
+        nbytes = int(self._lib.el_batch_fft_pool_bytes(ctypes.byref(desc), int(slots)))
+        if nbytes == 0:
+            raise ElpathError(1, "invalid pool class or slot count")
+        mem = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.el_batch_add_fft_pool(self._h, ctypes.byref(desc), int(slots),
+                                                        ctypes.c_void_p(mem.data_ptr()),
+                                                        ctypes.c_size_t(nbytes)))
+        self.pools.append(mem)
+        return nbytes
 
     def add(self, flow):
         self._check(self._lib.el_batch_add(self._h, flow._h))
@@ -399,6 +422,7 @@ class Batch:
             self._lib.el_batch_destroy(h)
             self._h = None
             self.members = []
+            self.pools = []
 
     def __del__(self):
         try:
