@@ -403,8 +403,9 @@ def run_serving(dev, count=200, budget_gb=120.0, timeout=90.0):
     import torch
     from paper_2607_17836_b300 import serve
     reqs = inputs.served_requests(count=count)
+    pools = {128: 4, 256: 4, 512: 4, 1024: 4, 2048: 2}   # FFT-pool slots per grid size
     srv = serve.Server(hbm_budget=int(budget_gb * 2**30), max_members=64, tick_steps=50,
-                       device=dev)
+                       device=dev, fft_pool_slots=pools)
     t0 = time.perf_counter()
     results = srv.run(reqs, timeout=timeout)
     wall = time.perf_counter() - t0
@@ -415,7 +416,7 @@ def run_serving(dev, count=200, budget_gb=120.0, timeout=90.0):
             "completed": len(results), "submitted": count, "wall_s": wall,
             "latency": lat, "particle_steps_per_s": srv.particle_steps / wall,
             "requests_per_s": len(results) / wall, "peak_hbm_gb": srv.peak_used / 2**30,
-            "hbm_budget_gb": budget_gb}
+            "hbm_budget_gb": budget_gb, "fft_pool_slots": {str(n): k for n, k in pools.items()}}
 
 
 # Sec. 5.2 with the paper's 2 km domain mapped onto [0, 2 pi): lengths and

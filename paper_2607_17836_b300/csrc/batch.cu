@@ -154,8 +154,18 @@ struct FftPool {
     float* nl = nullptr;
     float2* nhat = nullptr;
     void* work = nullptr;
-    cufftHandle c2r = 0, r2c = 0;
+    size_t work_bytes = 0;
+    // plans over the first k slots, k = 1..slots (0: not made yet); members
+    // take the lowest free slot, and the transforms cover slots [0, k) with
+    // k one past the highest occupied slot
+    std::vector<cufftHandle> c2r, r2c;
     std::vector<el_flow*> member;  // occupant of each slot (nullptr: free)
+    int span() const {
+        int k = 0;
+        for (int i = 0; i < slots; i++)
+            if (member[i]) k = i + 1;
+        return k;
+    }
 };
 
 struct el_batch {
@@ -266,6 +276,8 @@ MemberDev member_of(const el_batch* b, el_flow* f) {
     return md;
 }
 
+void ensure_prefix_plans(el_batch* b, FftPool& p, int k);
+
 // Rebuild and upload the member tables, and size the persistent grids.
 el_status rebuild_tables(el_batch* b) {
     const int M = (int)b->members.size();
@@ -337,6 +349,7 @@ el_status rebuild_tables(el_batch* b) {
         BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rk_kernels[sc], rk_threads, 0));
         b->grid_rk[sc] = std::max(1, std::min(a.rk_tasks, std::max(1, occ) * b->sms));
     }
+    for (FftPool& p : b->pools) ensure_prefix_plans(b, p, p.span());
     b->tables_valid = true;
     return EL_OK;
 }
@@ -347,11 +360,11 @@ el_status fork_ffts(el_batch* b, cudaStream_t origin, bool c2r) {
     for (int k = 0; k < kSideStreams; k++) BT_CUDA(b, cudaStreamWaitEvent(b->side[k], b->fork_ev, 0));
     size_t branch = 0;
     for (FftPool& p : b->pools) {
-        if (std::find_if(p.member.begin(), p.member.end(), [](el_flow* f) { return f != nullptr; }) ==
-            p.member.end())
-            continue;
+        const int k = p.span();
+        if (k == 0) continue;
+        const int use = p.c2r[k] ? k : p.slots;  // a prefix plan, else the full one
         cudaStream_t s = b->side[branch++ % kSideStreams];
-        cufftHandle plan = c2r ? p.c2r : p.r2c;
+        cufftHandle plan = c2r ? p.c2r[use] : p.r2c[use];
         if (cufftSetStream(plan, s) != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cufftSetStream");
         cufftResult r = c2r ? cufftExecC2R(plan, reinterpret_cast<cufftComplex*>(p.spec), p.phys)
                             : cufftExecR2C(plan, p.nl, reinterpret_cast<cufftComplex*>(p.nhat));
@@ -438,10 +451,11 @@ el_status build_batch_graph(el_batch* b, int kind) {
         cufftSetStream(f->plan_c2r, b->stream);
         cufftSetStream(f->plan_r2c, b->stream);
     }
-    for (FftPool& p : b->pools) {
-        cufftSetStream(p.c2r, b->stream);
-        cufftSetStream(p.r2c, b->stream);
-    }
+    for (FftPool& p : b->pools)
+        for (int k = 1; k <= p.slots; k++) {
+            if (p.c2r[k]) cufftSetStream(p.c2r[k], b->stream);
+            if (p.r2c[k]) cufftSetStream(p.r2c[k], b->stream);
+        }
     if (s != EL_OK) {
         if (g) cudaGraphDestroy(g);
         return s;
@@ -536,6 +550,29 @@ el_status pool_leave(el_batch* b, el_flow* f) {
     return EL_OK;
 }
 
+// The plans over the first k slots of pool p, made (outside any capture)
+// when first needed; left unmade if they would need more work area than the
+// pool has (the full plan, sized with the pool, serves then).
+void ensure_prefix_plans(el_batch* b, FftPool& p, int k) {
+    if (k <= 0 || p.c2r[k]) return;
+    cufftHandle c2r = 0, r2c = 0;
+    size_t work = 0;
+    cufftResult r = pool_plans(p.n, p.planes, k, &c2r, &r2c, &work);
+    if (r == CUFFT_SUCCESS && work <= p.work_bytes) {
+        r = cufftSetWorkArea(c2r, p.work);
+        if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(r2c, p.work);
+        if (r == CUFFT_SUCCESS) r = cufftSetStream(c2r, b->stream);
+        if (r == CUFFT_SUCCESS) r = cufftSetStream(r2c, b->stream);
+        if (r == CUFFT_SUCCESS) {
+            p.c2r[k] = c2r;
+            p.r2c[k] = r2c;
+            return;
+        }
+    }
+    if (c2r) cufftDestroy(c2r);
+    if (r2c) cufftDestroy(r2c);
+}
+
 void invalidate(el_batch* b) {
     b->tables_valid = false;
     for (cudaGraphExec_t& g : b->graph) {
@@ -586,11 +623,12 @@ el_status el_batch_add_fft_pool(el_batch* b, const el_flow_desc* desc, int32_t s
     p.nmodes = (size_t)p.n * (p.n / 2 + 1);
     p.n2 = (size_t)p.n * p.n;
     size_t work = 0;
-    cufftResult r = pool_plans(p.n, p.planes, slots, &p.c2r, &p.r2c, &work);
+    cufftHandle full_c2r = 0, full_r2c = 0;
+    cufftResult r = pool_plans(p.n, p.planes, slots, &full_c2r, &full_r2c, &work);
     const PoolLayout l = pool_layout(p.n, p.planes, slots, work);
     if (r == CUFFT_SUCCESS && bytes < l.total) {
-        cufftDestroy(p.c2r);
-        cufftDestroy(p.r2c);
+        cufftDestroy(full_c2r);
+        cufftDestroy(full_r2c);
         return bfail(b, EL_ENOMEM, "pool memory has %zu bytes, needs %zu", bytes, l.total);
     }
     char* base = static_cast<char*>(dev_workspace);
@@ -599,22 +637,27 @@ el_status el_batch_add_fft_pool(el_batch* b, const el_flow_desc* desc, int32_t s
     p.nl = reinterpret_cast<float*>(base + l.nl);
     p.nhat = reinterpret_cast<float2*>(base + l.nhat);
     p.work = base + l.work;
-    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(p.c2r, p.work);
-    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(p.r2c, p.work);
-    if (r == CUFFT_SUCCESS) r = cufftSetStream(p.c2r, b->stream);
-    if (r == CUFFT_SUCCESS) r = cufftSetStream(p.r2c, b->stream);
+    p.work_bytes = work;
+    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(full_c2r, p.work);
+    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(full_r2c, p.work);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(full_c2r, b->stream);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(full_r2c, b->stream);
     if (r != CUFFT_SUCCESS) {
-        if (p.c2r) cufftDestroy(p.c2r);
-        if (p.r2c) cufftDestroy(p.r2c);
+        if (full_c2r) cufftDestroy(full_c2r);
+        if (full_r2c) cufftDestroy(full_r2c);
         return bfail(b, EL_ECUFFT, "pool plans failed (%d)", (int)r);
     }
-    // free slots hold zeros (their transforms run with the occupied ones)
+    // free slots inside the transformed span hold zeros until first used
     cudaError_t e = cudaMemsetAsync(base, 0, l.work, b->stream);
     if (e != cudaSuccess) {
-        cufftDestroy(p.c2r);
-        cufftDestroy(p.r2c);
+        cufftDestroy(full_c2r);
+        cufftDestroy(full_r2c);
         return bfail(b, EL_ECUDA, "pool clear: %s", cudaGetErrorString(e));
     }
+    p.c2r.assign((size_t)slots + 1, 0);
+    p.r2c.assign((size_t)slots + 1, 0);
+    p.c2r[slots] = full_c2r;
+    p.r2c[slots] = full_r2c;
     p.member.assign((size_t)slots, nullptr);
     b->pools.push_back(std::move(p));
     invalidate(b);
@@ -746,10 +789,11 @@ el_status el_batch_destroy(el_batch* b) {
     if (!b) return EL_EINVAL;
     if (b->stream || !b->members.empty()) cudaStreamSynchronize(b->stream);
     while (!b->members.empty()) el_batch_remove(b, b->members.back());
-    for (FftPool& p : b->pools) {
-        if (p.c2r) cufftDestroy(p.c2r);
-        if (p.r2c) cufftDestroy(p.r2c);
-    }
+    for (FftPool& p : b->pools)
+        for (int k = 1; k <= p.slots; k++) {
+            if (p.c2r[k]) cufftDestroy(p.c2r[k]);
+            if (p.r2c[k]) cufftDestroy(p.r2c[k]);
+        }
     for (cudaGraphExec_t g : b->graph)
         if (g) cudaGraphExecDestroy(g);
     for (int k = 0; k < kSideStreams; k++) {

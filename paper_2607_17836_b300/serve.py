@@ -91,6 +91,7 @@ class Server:
     device: str = "cuda"
     prep_workers: int = 8            # threads preparing arrived requests' host inputs
     prep_ahead: int = 16             # waiting requests (oldest first) whose inputs are prepared
+    fft_pool_slots: dict = None      # grid n -> FFT-pool slots (None: per-member transforms)
     results: list = field(default_factory=list)
 
     def __post_init__(self):
@@ -101,7 +102,12 @@ class Server:
         self.pool = ThreadPoolExecutor(max_workers=max(1, self.prep_workers))
         self.active: list[_Active] = []
         self.used = 0
-        self.peak_used = 0
+        # FFT pools (bilinear and Catmull-Rom requests share one class per
+        # grid size): their memory is held for the server's lifetime and
+        # counted against the budget
+        for n, slots in sorted((self.fft_pool_slots or {}).items()):
+            self.used += self.batch.add_fft_pool(int(n), int(slots))
+        self.peak_used = self.used
         self.particle_steps = 0
         self.t0 = time.perf_counter()
 

@@ -16,11 +16,20 @@ def small_stream(count=12):
                                   max_particles=2e4, steps=(10, 60))
 
 
-def test_served_results_equal_solo_runs_and_budget_holds():
+@pytest.mark.parametrize("pools", [None, {32: 2, 64: 2, 128: 2}], ids=["own_ffts", "fft_pools"])
+def test_served_results_equal_solo_runs_and_budget_holds(pools):
+    # with FFT pools, members of a grid size that find a free slot transform
+    # together (the pools' memory counts against the budget)
     reqs = small_stream()
     need = [elpath.workspace_bytes(serve.request_desc(r)) for r in reqs]
-    budget = int(2.5 * max(need))                  # forces queueing: only a few fit at once
-    srv = serve.Server(hbm_budget=budget, max_members=8, tick_steps=7, keep_positions=True)
+    pool_bytes = 0
+    if pools:
+        probe = elpath.Batch(1)
+        pool_bytes = sum(probe.add_fft_pool(n, k) for n, k in pools.items())
+        probe.close()
+    budget = int(2.5 * max(need)) + pool_bytes     # forces queueing: only a few fit at once
+    srv = serve.Server(hbm_budget=budget, max_members=8, tick_steps=7, keep_positions=True,
+                       fft_pool_slots=pools)
     results = srv.run(small_stream(), time_scale=1.0, timeout=300)
     srv.close()
     assert len(results) == len(reqs)
