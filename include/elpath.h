@@ -260,8 +260,9 @@ el_status el_batch_destroy(el_batch* batch);
  * until el_batch_destroy, at least el_batch_fft_pool_bytes(desc, slots)
  * bytes, 256-byte aligned (0: invalid desc or slots outside [1, 4096]).
  * A flow added with el_batch_add after the pool takes a free slot of a pool
- * of its class if there is one (else it transforms alone, as before); it
- * keeps the slot until it leaves.  The results equal the per-member path's up
+ * of its class if there is one, the lowest free one (else it transforms
+ * alone, as before); it keeps the slot until it leaves.  The batched calls
+ * cover slots 0 .. the highest occupied one.  The results equal the per-member path's up
  * to the rounding of cuFFT's batched kernels.  EL_ENOMEM when `bytes` is too
  * small; EL_ECUFFT when the plans cannot be made. */
 size_t el_batch_fft_pool_bytes(const el_flow_desc* desc, int32_t slots);
