@@ -1,5 +1,5 @@
 // Per-element bodies of the step kernels, shared by the single-flow kernels
-// (fluid.cu, particles.cu) and the batched kernels (batch.cu), so that a
+// (fluid.cu, rk4.cu) and the batched kernels (batch.cu), so that a
 // simulation advanced alone or inside a batch does the same arithmetic.
 #pragma once
 
