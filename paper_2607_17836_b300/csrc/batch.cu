@@ -97,12 +97,14 @@ __global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_co
     for (int t = blockIdx.x; t < b.nl_tasks; t += gridDim.x) {
         const int m = owner_of(b.nl_begin, b.nmembers, t);
         const MemberDev& md = b.members[m];
-        const size_t q = (size_t)(t - b.nl_begin[m]) * kBNlThreads + threadIdx.x;
+        const size_t i = (size_t)(t - b.nl_begin[m]) * kBNlThreads + threadIdx.x;
+        const size_t n2 = 4 * md.n4;
         const long long lv = md.step + 1 + ahead;  // the level this step produces
-        if (q < md.n4)
-            nonlinear_quad(md.phys4, md.nl4, md.snap[lv % 2], md.snap[(lv + 1) % 2], nullptr,
-                           md.n4, q, md.stencil_plane, md.psi_plane, md.psi[lv % 2],
-                           md.psi[(lv + 1) % 2], nullptr);
+        if (i < n2)
+            nonlinear_node(reinterpret_cast<const float*>(md.phys4), reinterpret_cast<float*>(md.nl4),
+                           md.snap[lv % 2], md.snap[(lv + 1) % 2], nullptr, n2, i,
+                           md.stencil_plane, md.psi_plane, md.psi[lv % 2], md.psi[(lv + 1) % 2],
+                           nullptr);
     }
 }
 
@@ -294,7 +296,7 @@ el_status rebuild_tables(el_batch* b) {
         b->h_members.push_back(member_of(b, f));
         b->h_spec_begin.push_back(b->h_spec_begin.back() + f->n * spec_chunks(f->n));
         b->h_nl_begin.push_back(b->h_nl_begin.back() +
-                                (int)((f->n2 / 4 + kBNlThreads - 1) / kBNlThreads));
+                                (int)((f->n2 + kBNlThreads - 1) / kBNlThreads));
     }
     for (int m = 0; m < M; m++) {
         el_flow* f = b->members[m];

@@ -37,13 +37,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectral(const __grid_constant
     if (i == 0) spectral_mode<ADVANCE>(a, a.n / 2, j);
 }
 
-// N = u wx + v wy at node i (Eq. 7) and node i's level pair (m-1, m) of the
-// new level m: `dst` = (level m-1 from the second half of `src`, level m), one
-// full 16-byte store.  At set-up (src == nullptr) level 0 fills both halves of
-// `dst` and of `other`, so no pair ever holds uninitialised values.  One node
-// per thread (scalar plane loads; the pair loads and stores contiguous across
-// the warp): 2.5 % shorter fluid steps at 1024^2 than four nodes per thread,
-// the arithmetic (that of the batched engine's nonlinear_quad) unchanged.
+// N and the level pair of the new level at every node (nonlinear_node).
 __global__ void k_nonlinear(const float* __restrict__ phys, float* __restrict__ nl,
                             const float4* __restrict__ src, float4* __restrict__ dst,
                             float4* __restrict__ other, size_t n2, int stencil_plane,
@@ -51,30 +45,8 @@ __global__ void k_nonlinear(const float* __restrict__ phys, float* __restrict__ 
                             float2* __restrict__ psi_dst, float2* __restrict__ psi_other) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n2) return;
-    float u = phys[i], v = phys[n2 + i];
-    const float wx = phys[2 * n2 + i], wy = phys[3 * n2 + i];
-    nl[i] = fmaf(u, wx, v * wy);
-    if (stencil_plane != 0) {
-        u = phys[4 * n2 + i];
-        v = phys[5 * n2 + i];
-    }
-    if (src) {
-        const float4 old = src[i];
-        dst[i] = make_float4(old.z, old.w, u, v);
-    } else {
-        const float4 both = make_float4(u, v, u, v);
-        dst[i] = both;
-        other[i] = both;
-    }
-    if (psi_plane >= 0) {
-        const float pk = phys[(size_t)psi_plane * n2 + i];
-        if (src) {
-            psi_dst[i] = make_float2(psi_src[i].y, pk);
-        } else {
-            psi_dst[i] = make_float2(pk, pk);
-            psi_other[i] = make_float2(pk, pk);
-        }
-    }
+    nonlinear_node(phys, nl, src, dst, other, n2, i, stencil_plane, psi_plane, psi_src, psi_dst,
+                   psi_other);
 }
 
 // Initial projection: mean removed, 2/3 rule (Sec. 3.1).
