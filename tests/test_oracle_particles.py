@@ -145,6 +145,14 @@ def test_cluster_index_of_uniform_points_is_near_zero():
     # so Var/mean - 1 = P (B-1)/B - 1
     x = np.full(1000, 0.01)
     assert abs(oracle.cluster_index(x, x) - (1000 * 4095 / 4096 - 1)) < 1e-9
+    # exactly k particles at every box centre: Var = 0, so the index is -1;
+    # shifting some by whole periods (2 pi m) must not move them between boxes
+    B, k = 64, 3
+    c = (np.arange(B) + 0.5) * (2 * np.pi / B)
+    X, Y = np.meshgrid(c, c)
+    xs = np.tile(X.ravel(), k) + 2 * np.pi * np.repeat([0, -3, 5], B * B)
+    ys = np.tile(Y.ravel(), k) + 2 * np.pi * np.repeat([2, 0, -1], B * B)
+    assert oracle.cluster_index(xs, ys) == pytest.approx(-1.0, abs=1e-12)
 
 
 @pytest.mark.parametrize("scheme,tol", [(oracle.CATMULL_ROM, 5e-5), (oracle.BSPLINE, 2e-6)])
