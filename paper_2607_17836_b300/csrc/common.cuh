@@ -197,10 +197,10 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn);
 const char* flow_desc_problem(const el_flow_desc* d);  // nullptr when the descriptor is valid
 int flow_planes(const el_flow_desc& d);                // spectral planes of the inverse FFT
 
-// ---- particles (particles.cu) ---------------------------------------------------
+// ---- particles (particles.cu; the RK4 step in rk4.cu) ----------------------------
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
                         const double* vxy);
-el_status particles_step_all(el_flow* f, int64_t step);  // K6, every species in one launch
+el_status particles_step_all(el_flow* f, int64_t step);  // K6 (rk4.cu), every species in one launch
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
 // msd x, msd y, cluster, <dx^4>, <dy^4> (the squared displacements' second moments)
 el_status particles_stats_into(el_flow* f, int s, double* out5);
