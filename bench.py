@@ -288,6 +288,32 @@ def cpu_oracle_rate(wl, scheme, budget_s=12.0, subsample=64, max_steps=40):
     return ps, steps / t_fluid, oracle.num_threads(), desc
 
 
+def cpu_oracle_config1():
+    """The FP64 oracle on the Taylor-Green case in full (64^2, 200 steps,
+    4096 tracers, bilinear): wall seconds and rates on this host's cores."""
+    import oracle
+    wl = inputs.taylor_green_64()
+    sp = wl.species[0]
+    t0 = time.perf_counter()
+    flow = oracle.Flow(wl.n, wl.nu, wl.dt, wl.omega0())
+    f = flow.fields(("u", "v"))
+    lvl = (f["u"], f["v"])
+    xy = inputs.uniform_positions(sp.count, sp.seed)
+    x, y = xy[:, 0].copy(), xy[:, 1].copy()
+    t_fluid = 0.0
+    for _ in range(wl.steps):
+        a = time.perf_counter()
+        flow.step(1)
+        f = flow.fields(("u", "v"))
+        t_fluid += time.perf_counter() - a
+        oracle.particles_rk4(0, wl.dt, 0.0, lvl[0], lvl[1], f["u"], f["v"], x, y)
+        lvl = (f["u"], f["v"])
+    wall = time.perf_counter() - t0
+    return {"workload": "taylor_green_64 in full: 64^2, 200 steps, 4096 tracers, bilinear",
+            "seconds": wall, "particle_steps_per_s": sp.count * wl.steps / wall,
+            "fluid_steps_per_s": wl.steps / t_fluid, "cores": oracle.num_threads()}
+
+
 def run_reference(args, wl, scheme, world, rank):
     if rank != 0:
         return
@@ -668,7 +694,8 @@ def run_ours(args, wl, scheme, world, rank, local):
     if not args.no_cpu_baseline:
         ps, fsps, cores, desc = cpu_oracle_rate(wl, scheme)
         line["cpu_baseline"] = {"value": ps, "unit": "particle-steps/s", "cores": cores,
-                                "kind": "oracle", "sample": desc, "fluid_steps_per_s": fsps}
+                                "kind": "oracle", "sample": desc, "fluid_steps_per_s": fsps,
+                                "config1_full": cpu_oracle_config1()}
     print(json.dumps(line), flush=True)
 
 

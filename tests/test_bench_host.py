@@ -4,6 +4,8 @@ byte counts follow from the stencil widths."""
 import os
 import shutil
 
+import pytest
+
 import bench
 
 
@@ -35,3 +37,10 @@ def test_gather_bytes():
     # level pair per node
     assert bench.GATHER_PLAIN == {0: 192, 1: 768, 2: 768}
     assert bench.GATHER_CACHED == {0: 64, 1: 256, 2: 256}
+
+
+def test_oracle_timing_of_the_taylor_green_case_in_full():
+    t = bench.cpu_oracle_config1()
+    assert t["seconds"] > 0 and t["cores"] >= 1
+    assert t["particle_steps_per_s"] == pytest.approx(4096 * 200 / t["seconds"])
+    assert t["fluid_steps_per_s"] > t["particle_steps_per_s"] / 4096
