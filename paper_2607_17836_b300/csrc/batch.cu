@@ -519,7 +519,8 @@ cufftResult pool_plans(int n, int planes, int slots, cufftHandle* c2r, cufftHand
 }
 
 // Put a joining member into a free slot of a pool of its class, if any;
-// its N-hat moves into the slot (stream-ordered on the batch stream).
+// its N-hat moves into the slot (stream-ordered on the batch stream).  On a
+// failed copy the member and the pool are left as they were.
 el_status pool_join(el_batch* b, el_flow* f) {
     for (size_t q = 0; q < b->pools.size(); q++) {
         FftPool& p = b->pools[q];
@@ -529,7 +530,7 @@ el_status pool_join(el_batch* b, el_flow* f) {
             float2* slot_nhat = p.nhat + (size_t)k * p.nmodes;
             BT_CUDA(b, cudaMemcpyAsync(slot_nhat, f->nhat, p.nmodes * sizeof(float2),
                                        cudaMemcpyDeviceToDevice, b->stream));
-            p.member[k] = f;
+            p.member[k] = f;  // after the copy was accepted
             f->fft_pool = (int)q;
             f->fft_slot = k;
             f->nhat_cur = slot_nhat;
@@ -719,6 +720,8 @@ el_status el_batch_add(el_batch* b, el_flow* f) {
     cudaGetDevice(&dev);
     if (dev != f->device) return bfail(b, EL_EINVAL, "flow lives on another device");
     BT_CUDA(b, cudaStreamSynchronize(f->stream));
+    // a pool slot first: if moving N-hat into it fails, nothing has changed
+    EL_TRY(pool_join(b, f));
     if (!b->members.empty() && b->members[0]->rk4_threads != f->rk4_threads)
         f->rk4_threads = b->members[0]->rk4_threads;
     f->own_stream = f->stream;
@@ -729,7 +732,7 @@ el_status el_batch_add(el_batch* b, el_flow* f) {
     f->batch = b;
     b->members.push_back(f);
     invalidate(b);
-    return pool_join(b, f);
+    return EL_OK;
 }
 
 el_status el_batch_remove(el_batch* b, el_flow* f) {

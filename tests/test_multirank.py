@@ -36,7 +36,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_aggregate_with_the_slowest_time():
     port = _free_port()
-    manager = mp.Manager()
+    manager = mp.get_context("spawn").Manager()  # no fork of a process that may run threads
     out = manager.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     for r in (0, 1):
