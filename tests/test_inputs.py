@@ -2,7 +2,9 @@
 decaying-turbulence field's shell spectrum is k^4 exp(-(k/k0)^2) up to
 random-phase noise, with no energy outside the 2/3 band and zero mean; the
 double shear layer's x-averaged vorticity is -du/dy of its tanh velocity
-profile; particle positions are uniform on the periodic square."""
+profile; particle positions are uniform on the periodic square; the served
+stream's arrivals are Poisson with the stated rate and its draws come from
+the stated sets and ranges, as do the ensemble members'."""
 import math
 
 import numpy as np
@@ -67,3 +69,34 @@ def test_positions_are_uniform_on_the_square():
     a, b = inputs.uniform_positions(1000, 9), inputs.uniform_positions(1000, 9)
     np.testing.assert_array_equal(a, b)                                  # seeded
     assert not np.array_equal(a, inputs.uniform_positions(1000, 10))
+
+
+def test_served_stream_recipe():
+    # Poisson arrivals at 20/s: exponential gaps of mean 1/20 (the mean of
+    # 2000 gaps within 5 standard errors); grids, schemes, Stokes numbers from
+    # their sets; particle counts log-uniform in [1e3, 1e7]; steps in range
+    reqs = inputs.served_requests(count=2000)
+    t = np.array([r.arrival for r in reqs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0)
+    assert abs(gaps.mean() - 0.05) < 5 * 0.05 / math.sqrt(len(gaps))
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1          # exponential: std = mean
+    assert {r.workload.n for r in reqs} == {128, 256, 512, 1024, 2048}
+    assert {r.scheme for r in reqs} == {0, 1}
+    assert {r.workload.species[0].st for r in reqs} == {0.0, 0.1, 1.0, 10.0}
+    lg = np.log10([r.workload.species[0].count for r in reqs])
+    assert lg.min() >= 3.0 - 1e-9 and lg.max() <= 7.0 + 1e-9
+    assert abs(lg.mean() - 5.0) < 5 * (4 / math.sqrt(12)) / math.sqrt(len(lg))
+    steps = np.array([r.workload.steps for r in reqs])
+    assert steps.min() >= 100 and steps.max() <= 2000
+    assert [r.rid for r in reqs] == list(range(2000))
+
+
+def test_ensemble_members_recipe():
+    ms = inputs.ensemble_members(64)
+    assert len(ms) == 64
+    assert {m.n for m in ms} <= {256, 512, 1024} and len({m.n for m in ms}) == 3
+    assert [m.ic_seed for m in ms] == [1000 + k for k in range(64)]     # per-member seeds
+    counts = np.array([m.species[0].count for m in ms])
+    assert counts.min() >= 10_000 and counts.max() <= 1_000_000
+    assert {m.species[0].st for m in ms} <= {0.0, 0.1, 1.0, 10.0}
