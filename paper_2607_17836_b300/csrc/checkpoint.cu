@@ -93,6 +93,59 @@ size_t image_bytes(const std::vector<Section>& s) {
     return b + sizeof(uint64_t);
 }
 
+// Every per-particle section of the image, checked on the host before any of
+// it reaches the device: a checksum proves the image intact, not valid, and
+// the device path indexes memory with these values (the re-binning sort bins
+// by cell, the readback scatters by id).  Cells must lie below n on both
+// axes and ids must be a permutation of [0, np); offsets must lie in [0, 1)
+// and velocities and x(0) be finite.  EL_CHECK_BOUNDS debug builds skip the
+// offset range test (offsets index nothing: the gathers wrap their indices),
+// so that their in-kernel invariant check can be exercised by an image.
+const char* particle_sections_problem(const unsigned char* in, size_t at, int n, const int64_t* np,
+                                      const double* st, int max_species) {
+    std::vector<unsigned char> seen;
+    for (int k = 0; k < max_species; k++) {
+        if (np[k] <= 0) continue;
+        const size_t m = (size_t)np[k];
+        const unsigned char* cell = in + at;
+        at += pad8(m * 4);
+        const unsigned char* off = in + at;
+        at += pad8(m * 8);
+        const unsigned char* vel = nullptr;
+        if (st[k] > 0.0) {
+            vel = in + at;
+            at += pad8(m * 8);
+        }
+        at += pad8(m * 8);  // image counts: any value is a valid periodic image
+        const unsigned char* id = in + at;
+        at += pad8(m * 4);
+        const unsigned char* x0 = in + at;
+        at += pad8(m * 16);
+        seen.assign(m, 0);
+        for (size_t p = 0; p < m; p++) {
+            uint32_t c, q;
+            float o[2], v[2];
+            double x[2];
+            std::memcpy(&c, cell + 4 * p, 4);
+            if ((c & 0xffffu) >= (uint32_t)n || (c >> 16) >= (uint32_t)n) return "a cell index is not below n";
+            std::memcpy(o, off + 8 * p, 8);
+            if (!(std::isfinite(o[0]) && std::isfinite(o[1]))) return "an in-cell offset is not finite";
+            if (!EL_CHECK_BOUNDS && !(o[0] >= 0.f && o[0] < 1.f && o[1] >= 0.f && o[1] < 1.f))
+                return "an in-cell offset is outside [0, 1)";
+            if (vel) {
+                std::memcpy(v, vel + 8 * p, 8);
+                if (!(std::isfinite(v[0]) && std::isfinite(v[1]))) return "a particle velocity is not finite";
+            }
+            std::memcpy(&q, id + 4 * p, 4);
+            if (q >= m || seen[q]) return "the particle ids are not a permutation of [0, np)";
+            seen[q] = 1;
+            std::memcpy(x, x0 + 16 * p, 16);
+            if (!(std::isfinite(x[0]) && std::isfinite(x[1]))) return "a reference position x(0) is not finite";
+        }
+    }
+    return nullptr;
+}
+
 bool same_flow(const CkptHeader& h, const el_flow* f) {
     const el_flow_desc &a = h.desc, &b = f->d;
     return a.n == b.n && a.interp == b.interp && std::memcmp(&a.nu, &b.nu, sizeof(double)) == 0 &&
@@ -178,6 +231,18 @@ el_status el_load_state(el_flow* f, const void* host_buf, size_t bytes) {
                         (long long)h.np[k]);
         if (h.np[k] > 0 && !(std::isfinite(h.st[k]) && h.st[k] >= 0.0))
             return fail(f, EL_EINVAL, "state image has a bad Stokes number");
+    }
+    // the image must hold exactly the sections its header declares (checked
+    // before any of them is read), and every particle's state must be valid
+    {
+        const std::vector<Section> want = sections(f, h.np, h.st, h.step);  // sizes only
+        if (image_bytes(want) != bytes)
+            return fail(f, EL_EINVAL, "state image is %zu bytes, its particle counts need %zu", bytes,
+                        image_bytes(want));
+        size_t at = pad8(sizeof h);
+        for (int q = 0; q < 5 + (f->psi_plane >= 0 ? 1 : 0); q++) at += pad8(want[q].bytes);
+        if (const char* why = particle_sections_problem(in, at, f->n, h.np, h.st, f->d.max_species))
+            return fail(f, EL_EINVAL, "state image refused: %s", why);
     }
     // room for every species, checked before anything changes
     if (!species_fit(f, h.np)) return fail(f, EL_EINVAL, "particle pool too small for the state image");

@@ -7,6 +7,7 @@ position and velocity, and the FP64 statistics.  Damaged or mismatched
 images are refused with the flow left as it was.
 """
 import ctypes
+import struct
 
 import numpy as np
 import pytest
@@ -155,3 +156,73 @@ def test_batch_members_save_but_do_not_load():
     batch.close()
     for f in (a, b, ref):
         f.close()
+
+
+def _fnv1a(data):
+    h = 1469598103934665603
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def test_invalid_particle_state_is_refused_before_any_upload():
+    # Images whose checksum is valid (recomputed after the edit) but whose
+    # particle state is not: cells that index past the grid, offsets outside
+    # [0, 1), non-finite velocities or x(0), ids that are not a permutation,
+    # counts that the image does not hold.  The library checks them on the
+    # host before anything reaches the device, so each is refused with
+    # EL_EINVAL and the flow keeps running exactly like its twin.
+    case = CASES[0]                       # n = 64: 3001 tracers, 2000 at St = 1
+    n = case[0]
+    g = make(case, 4)
+    g.step(6)
+    image = bytes(g.save_state())
+    twin = make(case, 4)
+    twin.step(6)
+    pad8 = lambda x: (x + 7) // 8 * 8
+    hdr = struct.unpack_from("<I", image, 12)[0]
+    nm = n * (n // 2 + 1)
+    at = pad8(hdr) + 4 * pad8(nm * 8) + pad8(n * n * 16)
+    sec = {}
+    for k, (m, st) in enumerate(case[3]):
+        for name, size in (("cell", 4), ("off", 8), ("vel", 8 if st > 0 else 0), ("img", 8),
+                           ("id", 4), ("x0", 16)):
+            if size:
+                sec[(k, name)] = at
+                at += pad8(m * size)
+    assert at + 8 == len(image)
+
+    def edited(*edits):
+        b = bytearray(image)
+        for fmt, where, value in edits:
+            struct.pack_into(fmt, b, where, value)
+        struct.pack_into("<Q", b, len(b) - 8, _fnv1a(bytes(b[:-8])))
+        return bytes(b)
+
+    cell5 = struct.unpack_from("<I", image, sec[(0, "cell")] + 4 * 5)[0]
+    id10 = struct.unpack_from("<I", image, sec[(0, "id")] + 4 * 10)[0]
+    np_at = 24 + ctypes.sizeof(elpath.el_flow_desc) + 16      # header: ... step, since_sort, np[]
+    assert struct.unpack_from("<q", image, np_at)[0] == case[3][0][0]
+    bad = {
+        "cell i = n": edited(("<I", sec[(0, "cell")] + 4 * 5, (cell5 & 0xFFFF0000) | n)),
+        "cell j >= n": edited(("<I", sec[(1, "cell")] + 4 * 3, (70 << 16) | 1)),
+        "offset 1.5": edited(("<f", sec[(0, "off")] + 8 * 7, 1.5)),
+        "offset -0.25": edited(("<f", sec[(1, "off")] + 8 * 2 + 4, -0.25)),
+        "offset NaN": edited(("<f", sec[(0, "off")], float("nan"))),
+        "velocity inf": edited(("<f", sec[(1, "vel")] + 8 * 3, float("inf"))),
+        "duplicate id": edited(("<I", sec[(0, "id")] + 4 * 9, id10)),
+        "id = np": edited(("<I", sec[(1, "id")], case[3][1][0])),
+        "x0 NaN": edited(("<d", sec[(1, "x0")] + 16 * 4 + 8, float("nan"))),
+        "count beyond the image": edited(("<q", np_at, case[3][0][0] + 1)),
+    }
+    for what, img in bad.items():
+        with pytest.raises(elpath.ElpathError) as e:
+            g.load_state(img)
+        assert e.value.status == 1, what
+    # the unedited image still loads (the offsets above were computed right)
+    g.load_state(edited())
+    g.step(10)
+    twin.step(10)
+    assert_bitwise(state(g, case), state(twin, case))
+    g.close()
+    twin.close()
