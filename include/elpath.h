@@ -276,17 +276,22 @@ el_status el_batch_add_fft_pool(el_batch* batch, const el_flow_desc* desc, int32
  * and cudaFree can synchronise the whole device) or an application whose
  * device memory is all reserved up front by another allocator.
  * d_xy, d_xy0: DEVICE arrays of 2*np doubles, unwrapped positions now and at
- * the reference time (as el_get_particles returns them).  d_out3: DEVICE
- * array of 3 doubles receiving <(x-x0)^2>, <(y-y0)^2> and the clustering
+ * the reference time (as el_get_particles returns them), each 16-byte
+ * aligned (read as (x, y) pairs).  d_out3: DEVICE array of 3 doubles, 8-byte
+ * aligned, receiving <(x-x0)^2>, <(y-y0)^2> and the clustering
  * index (Var(n)/mean(n) - 1 on a 64 x 64 box grid of the wrapped positions),
  * reduced in FP64 in the same fixed order as el_get_stats.
- * np must be <= EL_NOALLOC_MAX_PARTICLES, else EL_EINVAL.  Work is queued on
+ * np must be <= EL_NOALLOC_MAX_PARTICLES and the pointers aligned, else
+ * EL_EINVAL (np = 0 gives 0, 0, 0).  Work is queued on
  * cuda_stream and the call returns without waiting.  Scratch: one fixed
  * device array of about 4 MiB inside the library, present on every GPU that
  * loads it until the process exits, shared by all calls: calls whose work
  * overlaps on the GPU race.  The first call on a device looks up the array's
- * device address with that device current; make that first call before any
- * stream capture.  Errors: el_last_error(NULL). */
+ * device address with that device current and keeps it for the process;
+ * make that first call before any stream capture, and do not call this
+ * entry point after a cudaDeviceReset of that device (the reset unloads the
+ * library's device array, and the kept address would be stale).
+ * Errors: el_last_error(NULL). */
 #define EL_NOALLOC_MAX_PARTICLES 262144
 el_status el_dispersion_noalloc(const double* d_xy, const double* d_xy0, int64_t np,
                                 double* d_out3, void* cuda_stream);

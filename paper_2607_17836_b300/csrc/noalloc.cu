@@ -44,7 +44,8 @@ std::mutex g_scratch_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device (looked up on
-// the first call per device).
+// the first call per device and kept for the process: a cudaDeviceReset
+// unloads the array, so the entry point is not usable after one).
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -102,6 +103,11 @@ extern "C" el_status el_dispersion_noalloc(const double* d_xy, const double* d_x
                     (long long)np, (long long)kNoAllocMaxParticles, (long long)kNoAllocMaxParticles);
     if (!d_out3 || (np > 0 && (!d_xy || !d_xy0)))
         return fail(nullptr, EL_EINVAL, "el_dispersion_noalloc: NULL array");
+    // the kernels read positions as (x, y) pairs of 16 bytes and store doubles
+    if (np > 0 && (((uintptr_t)d_xy | (uintptr_t)d_xy0) & 15u))
+        return fail(nullptr, EL_EINVAL, "el_dispersion_noalloc: d_xy and d_xy0 must be 16-byte aligned");
+    if ((uintptr_t)d_out3 & 7u)
+        return fail(nullptr, EL_EINVAL, "el_dispersion_noalloc: d_out3 must be 8-byte aligned");
     void* base = nullptr;
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return noalloc_fail(EL_ECUDA, "scratch address", e);

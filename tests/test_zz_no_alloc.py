@@ -53,6 +53,47 @@ def test_noalloc_matches_get_stats_on_two_calls():
     g.close()
 
 
+def test_noalloc_empty_set_gives_zeros():
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    xy = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+    elpath.dispersion_noalloc(xy, xy, out=out)
+    torch.cuda.synchronize()
+    assert out.cpu().tolist() == [0.0, 0.0, 0.0]
+
+
+def test_noalloc_positions_whole_periods_away():
+    # Unwrapped positions several periods away from [0, 2 pi): the same
+    # displacement from the same x(0) shifted alike, so the mean-square
+    # displacement agrees to rounding, and the wrapped box counts (integers)
+    # are the same, so the clustering index is bit-identical.
+    g, counts, xys = _run_flow()
+    pos, _ = g.particles(0, counts[0])
+    g.close()
+    rng = np.random.default_rng(7)
+    shift = 2.0 * np.pi * rng.integers(-4, 5, size=(counts[0], 2)).astype(np.float64)
+    outs = []
+    for dx in (0.0, shift):
+        xy = torch.from_numpy(np.ascontiguousarray(pos + dx)).cuda()
+        xy0 = torch.from_numpy(np.ascontiguousarray(xys[0] + dx)).cuda()
+        out = torch.empty(3, dtype=torch.float64, device="cuda")
+        elpath.dispersion_noalloc(xy, xy0, out=out)
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+    np.testing.assert_allclose(outs[1][:2], outs[0][:2], rtol=1e-9)
+    assert outs[1][2] == outs[0][2]
+
+
+def test_noalloc_refuses_misaligned_positions():
+    # Refused on the host before any launch: the kernels read 16-byte pairs.
+    flat = torch.zeros(2 * 64 + 1, dtype=torch.float64, device="cuda")
+    xy = flat[1:].view(64, 2)
+    assert xy.data_ptr() % 16 == 8
+    with pytest.raises(elpath.ElpathError) as e:
+        elpath.dispersion_noalloc(xy, xy)
+    assert e.value.status == 1
+    assert "aligned" in str(e.value)
+
+
 def test_noalloc_rejects_more_particles_than_its_scratch():
     n_big = elpath.NOALLOC_MAX_PARTICLES + 1
     xy = torch.zeros((n_big, 2), dtype=torch.float64, device="cuda")
