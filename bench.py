@@ -10,9 +10,13 @@ production scheme).
                   [--impl ours|reference]
 
 Prints one JSON line.  `value` is particle-steps/s of the whole coupled step
-(fluid included), timed with CUDA events on the flow's stream, one event
-pair per step with an L2 flush (a 256 MiB write) before each step outside
-the event pair.  `--impl reference` times the FP64 CPU oracle instead.
+(fluid included), timed with CUDA events on the flow's stream around calls of
+10 steps (inside a call the fluid step of n+1 overlaps the particle step of
+n).  Each step touches more bytes than L2 holds (about 153 MiB at 1024^2
+with 4M particles against 126 MiB), and a 256 MiB write flushes L2 before
+every call, outside its event pair.  The solve latency (p50/p99) is taken
+over 200 single-step calls, each after an L2 flush.  `--impl reference`
+times the FP64 CPU oracle instead.
 Under torchrun (N > 1) each rank runs an independent replica (weak scaling;
 the path has no exchange step) and rank 0 prints the aggregate.
 """
@@ -39,11 +43,22 @@ from paper_2607_17836_b300 import inputs  # noqa: E402
 SCHEMES = {"bilinear": 0, "catmull_rom": 1, "bspline": 2}
 METRIC = "particle-steps/s (RK4+interp) & fluid steps/s at 1024^2; p50/p99 solve latency"
 SORT_EVERY = 20
-# Algorithmic bytes per particle-step of the RK4 kernel: state read + written
-# once (cell 4 B + offset 8 B, plus velocity 8 B for inertial particles).
-BYTES_TRACER = 2 * (4 + 8)
-BYTES_INERTIAL = 2 * (4 + 8 + 8)
+# Algorithmic bytes per particle-step of the RK4 kernel as the method's
+# state counts them: an 8-byte periodic image count, an 8-byte cell index,
+# an 8-byte offset pair and (inertial particles) an 8-byte velocity pair,
+# each read and written once; plus one read of the level pair (u, v at two
+# time levels, 16 N^2 bytes) per launch.
+BYTES_TRACER = 2 * (8 + 8 + 8)
+BYTES_INERTIAL = 2 * (8 + 8 + 8 + 8)
+FIELD_PAIR_BYTES_PER_NODE = 16
+# Compulsory bytes of this library's layout: the 4-byte packed cell and the
+# offset pair (and velocity pair) are read and written every step; the image
+# count is written only when a particle crosses the periodic boundary.
+COMPULSORY_TRACER = 2 * (4 + 8)
+COMPULSORY_INERTIAL = 2 * (4 + 8 + 8)
 FLUSH_BYTES = 256 << 20
+L2_BYTES = 126 << 20
+LATENCY_SAMPLES = 200
 # Snapshot bytes one particle-step gathers, per interpolation width W (W x W
 # nodes of (u, v) in FP32): the plain form fetches the nodes at each of its 6
 # snapshot evaluations (levels n and n+1 at stages 1 and 4, both at stages 2
@@ -240,52 +255,79 @@ def dist_setup():
 
 
 # ----------------------------------------------------------------------------------
+class OracleSample:
+    """The FP64 oracle as it stands, on a bounded sample of the workload: the
+    full-grid fluid solve plus every `subsample`-th particle of each species,
+    started as the GPU arm starts them (zero slip: an inertial particle takes
+    the interpolated fluid velocity at its start, from the interpolating
+    spline coefficients for the B-spline scheme).  Built once; each step()
+    times one coupled step (fluid step, then the particle step between the
+    two levels) and returns (fluid seconds, particle seconds)."""
+
+    def __init__(self, wl, scheme, subsample=64):
+        import oracle
+        self.oracle, self.wl, self.scheme, self.subsample = oracle, wl, scheme, subsample
+        self.flow = oracle.Flow(wl.n, wl.nu, wl.dt, wl.omega0())
+        f = self.flow.fields(("u", "v"))
+        self.level = (f["u"], f["v"])
+        su, sv = self._stencil(*self.level)
+        self.sets = []
+        for sp in wl.species:
+            xy = inputs.uniform_positions(sp.count, sp.seed)[::subsample]
+            x, y = xy[:, 0].copy(), xy[:, 1].copy()
+            vx = vy = None
+            if sp.st > 0:
+                vx, vy = oracle.interp(su, scheme, x, y), oracle.interp(sv, scheme, x, y)
+            self.sets.append((sp, x, y, vx, vy))
+        self.sampled = sum(len(s[1]) for s in self.sets)
+
+    def _stencil(self, u, v):
+        if self.scheme == 2:
+            return self.oracle.bspline_prefilter(u), self.oracle.bspline_prefilter(v)
+        return u, v
+
+    def step(self):
+        o = self.oracle
+        t0 = time.perf_counter()
+        self.flow.step(1)
+        f = self.flow.fields(("u", "v"))
+        un1, vn1 = f["u"], f["v"]
+        a, b = self._stencil(*self.level)
+        c, d = self._stencil(un1, vn1)
+        t1 = time.perf_counter()
+        for sp, x, y, vx, vy in self.sets:
+            o.particles_rk4(self.scheme, self.wl.dt, sp.st, a, b, c, d, x, y, vx, vy)
+        t2 = time.perf_counter()
+        self.level = (un1, vn1)
+        return t1 - t0, t2 - t1
+
+    def rate(self, t_fluid, t_part):
+        """Particle-steps/s of the full workload for one step that took
+        t_fluid + t_part (particle time scaled up by the subsample)."""
+        return self.wl.particles / (t_fluid + t_part * self.subsample)
+
+    def describe(self, steps):
+        return (f"{steps} coupled steps of the {self.wl.n}^2 fluid solve plus every "
+                f"{self.subsample}th particle of each species ({self.sampled} particles, zero slip "
+                f"as on the GPU); particle time scaled x{self.subsample} to the full "
+                f"{self.wl.particles} particles")
+
+
 def cpu_oracle_rate(wl, scheme, budget_s=12.0, subsample=64, max_steps=40):
-    """The FP64 oracle as it stands on this host's cores, on a bounded sample
-    of the workload: the full-grid fluid step plus every `subsample`-th
-    particle of each species; particle time is scaled back up to the full
-    counts.  Returns (particle-steps/s, fluid steps/s, cores, description)."""
+    """The oracle on a bounded sample (OracleSample), stepped until max_steps
+    or budget_s.  Returns (particle-steps/s, fluid steps/s, cores, description)."""
     import oracle
-    w0 = wl.omega0()
-    flow = oracle.Flow(wl.n, wl.nu, wl.dt, w0)
-    f = flow.fields(("u", "v"))
-    lvl = (f["u"], f["v"])
-    sets = []
-    for sp in wl.species:
-        xy = inputs.uniform_positions(sp.count, sp.seed)[::subsample]
-        x, y = xy[:, 0].copy(), xy[:, 1].copy()
-        vx = vy = None
-        if sp.st > 0:
-            vx = oracle.interp(lvl[0], scheme, x, y) if scheme != 2 else np.zeros_like(x)
-            vy = oracle.interp(lvl[1], scheme, x, y) if scheme != 2 else np.zeros_like(x)
-        sets.append((sp, x, y, vx, vy))
+    smp = OracleSample(wl, scheme, subsample)
     t_fluid = t_part = 0.0
     steps = 0
     t_start = time.perf_counter()
     while steps < max_steps and (time.perf_counter() - t_start) < budget_s:
-        t0 = time.perf_counter()
-        flow.step(1)
-        f = flow.fields(("u", "v"))
-        un1, vn1 = f["u"], f["v"]
-        if scheme == 2:
-            a, b = oracle.bspline_prefilter(lvl[0]), oracle.bspline_prefilter(lvl[1])
-            c, d = oracle.bspline_prefilter(un1), oracle.bspline_prefilter(vn1)
-        else:
-            a, b, c, d = lvl[0], lvl[1], un1, vn1
-        t1 = time.perf_counter()
-        for sp, x, y, vx, vy in sets:
-            oracle.particles_rk4(scheme, wl.dt, sp.st, a, b, c, d, x, y, vx, vy)
-        t2 = time.perf_counter()
-        lvl = (un1, vn1)
-        t_fluid += t1 - t0
-        t_part += t2 - t1
+        a, b = smp.step()
+        t_fluid += a
+        t_part += b
         steps += 1
-    per_step = t_fluid / steps + (t_part / steps) * subsample
-    ps = wl.particles / per_step
-    desc = (f"{steps} coupled steps of the {wl.n}^2 fluid solve plus every {subsample}th particle "
-            f"of each species ({sum(len(s[1]) for s in sets)} particles); particle time scaled "
-            f"x{subsample} to the full {wl.particles} particles")
-    return ps, steps / t_fluid, oracle.num_threads(), desc
+    ps = smp.rate(t_fluid / steps, t_part / steps)
+    return ps, steps / t_fluid, oracle.num_threads(), smp.describe(steps)
 
 
 def cpu_oracle_config1():
@@ -315,38 +357,81 @@ def cpu_oracle_config1():
 
 
 def run_reference(args, wl, scheme, world, rank):
+    """The reference arm: the FP64 oracle on the host cores, on the bounded
+    sample of OracleSample (set up once), W untimed coupled steps, then K
+    timed ones; value = the workload's particle-steps over the K steps' time."""
     if rank != 0:
         return
-    ps, fluid_sps, cores, desc = cpu_oracle_rate(wl, scheme, budget_s=8.0, max_steps=40)
-    # --steps K --warmup W: W + K bounded samples, each one coupled step.
     import oracle
-    rates = []
+    smp = OracleSample(wl, scheme)
     for _ in range(args.warmup):
-        cpu_oracle_rate(wl, scheme, budget_s=1.0, max_steps=1)
+        smp.step()
+    t_fluid = t_part = 0.0
     for _ in range(args.steps):
-        r, _, _, _ = cpu_oracle_rate(wl, scheme, budget_s=2.0, max_steps=2)
-        rates.append(r)
-    value = float(statistics.median(rates))
+        a, b = smp.step()
+        t_fluid += a
+        t_part += b
+    value = smp.rate(t_fluid / args.steps, t_part / args.steps)
+    cores = oracle.num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * wl.particles / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(wl, args.scheme),
-            "fluid_steps_per_s": fluid_sps,
+            "fluid_steps_per_s": args.steps / t_fluid,
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores,
-                             "kind": "oracle", "sample": desc},
+                             "kind": "oracle", "sample": smp.describe(args.steps)},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def step_working_set_bytes(wl):
+    """Distinct device bytes one coupled step touches: the particle state it
+    streams (cell + offset, + velocity for inertial particles), the spectral
+    half-planes (omega-hat high and low parts, AB2 history, N-hat and the four
+    derivative planes), the five physical planes (u, v, omega_x, omega_y, N)
+    and the two level pairs."""
+    n = wl.n
+    state = sum(s.count * (COMPULSORY_INERTIAL if s.st > 0 else COMPULSORY_TRACER) // 2
+                for s in wl.species)
+    return state + 8 * 8 * n * (n // 2 + 1) + 5 * 4 * n * n + 2 * 16 * n * n
+
+
 def config_of(wl, scheme_name):
+    ws = step_working_set_bytes(wl)
     return {"workload": wl.name, "n": wl.n, "nu": wl.nu, "dt": wl.dt,
             "species": [{"count": s.count, "st": s.st} for s in wl.species],
             "particles": wl.particles, "scheme": scheme_name, "sort_every": SORT_EVERY,
             "positions": "split precision: int32 image + cell index + fp32 offset",
-            "l2": "flushed (256 MiB write) before every call of 10 timed steps, outside the events",
+            "l2": (f"inputs larger than L2: each coupled step touches {ws / 2**20:.0f} MiB "
+                   f"(particle state + fluid planes + level pairs) against a {L2_BYTES >> 20} MiB "
+                   f"L2; a {FLUSH_BYTES >> 20} MiB write also flushes L2 before every call of "
+                   f"{CHUNK} timed steps, outside the events"),
             "parallelism": "replicas (one independent simulation per GPU)"}
+
+
+def roofline_point(species, n, launch_ms, peak, traffic=None):
+    """Roofline figures of one particle-step launch over `species` (list of
+    (count, st)) on an n^2 field, launch_ms long: the algorithmic bytes
+    (48 / 64 B per particle-step plus the field pair), this layout's
+    compulsory bytes (24 / 40 B plus the field pair) and, if known, the DRAM
+    bytes ncu measured for one launch."""
+    t = launch_ms * 1e-3
+    pair = FIELD_PAIR_BYTES_PER_NODE * n * n
+    alg = sum(c * (BYTES_INERTIAL if st > 0 else BYTES_TRACER) for c, st in species) + pair
+    comp = sum(c * (COMPULSORY_INERTIAL if st > 0 else COMPULSORY_TRACER) for c, st in species) + pair
+    out = {"launch_ms": launch_ms, "particle_steps_per_s": sum(c for c, _ in species) / t,
+           "achieved": alg / t / 1e9, "frac": alg / t / 1e9 / peak, "bytes_per_launch": alg,
+           "compulsory": {"bytes_per_launch": comp, "achieved": comp / t / 1e9,
+                          "frac": comp / t / 1e9 / peak},
+           "dram": None}
+    if traffic is not None:
+        out["dram"] = {"bytes_per_launch": traffic, "achieved": traffic / t / 1e9,
+                       "frac": traffic / t / 1e9 / peak,
+                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                                 "(committed profile of the current kernel source)"}
+    return out
 
 
 def run_ensemble(args, dev, members=64, steps=20):
@@ -422,10 +507,11 @@ def run_ensemble(args, dev, members=64, steps=20):
     return out
 
 
-def run_serving(dev, count=200, budget_gb=120.0, timeout=90.0):
-    """Config 5: Poisson arrivals (20 req/s), grids 128^2-2048^2, 1e3-1e7
-    particles, St in {0, 0.1, 1, 10}, bilinear or Catmull-Rom, 100-2000 steps;
-    the first `count` requests of the stream, HBM-footprint admission."""
+def run_serving(dev, count=200, rate=20.0, budget_gb=120.0, timeout=None):
+    """Config 5: the served stream (grids 128^2-2048^2, 1e3-1e7 particles,
+    St in {0, 0.1, 1, 10}, bilinear or Catmull-Rom, 100-2000 steps), its
+    first `count` requests, arriving as the configured 20/s Poisson stream
+    with its clock scaled to `rate` requests/s; HBM-footprint admission."""
     import torch
     from paper_2607_17836_b300 import serve
     reqs = inputs.served_requests(count=count)
@@ -433,14 +519,19 @@ def run_serving(dev, count=200, budget_gb=120.0, timeout=90.0):
     srv = serve.Server(hbm_budget=int(budget_gb * 2**30), max_members=64, tick_steps=50,
                        device=dev, fft_pool_slots=pools)
     t0 = time.perf_counter()
-    results = srv.run(reqs, timeout=timeout)
+    results = srv.run(reqs, time_scale=20.0 / rate, timeout=timeout)
     wall = time.perf_counter() - t0
     srv.close()
     torch.cuda.empty_cache()
     lat = serve.latency_summary(results)
-    return {"workload": f"first {count} requests of the served stream (Poisson 20/s)",
-            "completed": len(results), "submitted": count, "wall_s": wall,
-            "latency": lat, "particle_steps_per_s": srv.particle_steps / wall,
+    span = max(r.arrival for r in reqs)
+    work = sum(r.workload.particles * r.workload.steps for r in reqs)
+    return {"workload": f"first {count} of the 2000 requests of the served stream, Poisson "
+                        f"arrivals at {rate:g} requests/s (the 20/s stream's clock scaled)",
+            "requests": count, "arrival_rate_per_s": rate, "completed": len(results),
+            "arrivals_span_s": span, "wall_s": wall, "latency": lat,
+            "particle_steps_per_s": srv.particle_steps / wall,
+            "offered_particle_steps_per_s": work / span if span > 0 else None,
             "requests_per_s": len(results) / wall, "peak_hbm_gb": srv.peak_used / 2**30,
             "hbm_budget_gb": budget_gb, "fft_pool_slots": {str(n): k for n, k in pools.items()}}
 
@@ -568,20 +659,33 @@ def run_ours(args, wl, scheme, world, rank, local):
     torch.cuda.synchronize(dev)
     launches = flow.kernel_launches() - launches0
     chunk_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    step_ms = [t / c for t, c in zip(chunk_ms, chunks)]
     total_ms = max_over_ranks(float(sum(chunk_ms)), world, dev)
     if world > 1:
         dist.barrier()
 
+    # Solve latency of one coupled step: LATENCY_SAMPLES calls of one step
+    # each (fluid step, then particle step: nothing to overlap inside a call
+    # of one), every one preceded by an L2 flush outside its event pair.
+    lat_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(LATENCY_SAMPLES)]
+    with torch.cuda.stream(stream):
+        for k, (e0, e1) in enumerate(lat_ev):
+            flush.fill_((k + 1) & 0xFF)
+            e0.record(stream)
+            flow.step(1)
+            e1.record(stream)
+    stream.synchronize()
+    lat_ms = sorted(e0.elapsed_time(e1) for e0, e1 in lat_ev)
+
     # Per-stage times (direct launches with events between the stages).
-    prof = [flow.profile_step() for _ in range(min(args.steps, 20))]
+    prof = [flow.profile_step() for _ in range(20)]
     fluid_ms = statistics.mean(p["fluid"] for p in prof)
     part_ms = statistics.mean(p["particles"] for p in prof)
-    bytes_part = sum(s.count * (BYTES_INERTIAL if s.st > 0 else BYTES_TRACER) for s in wl.species)
     peak, peak_kind = measured_peaks()
-    achieved = bytes_part / (part_ms * 1e-3) / 1e9
     traffic_pps = recorded_traffic(args.scheme)
     traffic = traffic_pps * wl.particles if traffic_pps is not None else None
+    mix = [(s.count, s.st) for s in wl.species]
+    point4 = roofline_point(mix, wl.n, part_ms, peak, traffic)
 
     # The fluid solver alone as it runs inside el_step_coupled (captured
     # graphs): a flow with no particles, CUDA events around 500 steps.
@@ -597,9 +701,8 @@ def run_ours(args, wl, scheme, world, rank, local):
 
     # The roofline workload of the particle stage: 1024^2 with 16M inertial
     # particles at St = 1 in one species (same fluid, same scheme).
-    roof16 = None
+    point16 = None
     if not args.no_roofline16:
-        del flush
         big = 16_000_000
         g16 = elpath.Flow(wl.n, wl.nu, wl.dt, w0, interp=scheme, max_species=1,
                           max_particles=big, sort_every=SORT_EVERY, device=dev)
@@ -609,14 +712,14 @@ def run_ours(args, wl, scheme, world, rank, local):
             g16.step(1)
         pr = [g16.profile_step() for _ in range(10)]
         ms16 = statistics.mean(p["particles"] for p in pr)
-        ach16 = big * BYTES_INERTIAL / (ms16 * 1e-3) / 1e9
-        roof16 = {"workload": "1024^2 fluid, 16M inertial particles (St = 1), one species",
-                  "particle_stage_ms": ms16, "particle_steps_per_s": big / (ms16 * 1e-3),
-                  "achieved": ach16, "peak": peak, "unit": "GB/s", "frac": ach16 / peak,
-                  "bytes_per_particle_step": BYTES_INERTIAL}
+        t16 = recorded_profile(args.scheme).get("dram_bytes_per_particle_step_16M")
+        point16 = roofline_point([(big, 1.0)], wl.n, ms16, peak,
+                                 float(t16) * big if t16 is not None else None)
+        point16["workload"] = "1024^2 fluid, 16M inertial particles (St = 1), one species"
         g16.close()
         del g16
         torch.cuda.empty_cache()
+    del flush
 
     # End to end through the public API: particles from pinned host memory,
     # K coupled steps, statistics and every particle state back to pinned memory.
@@ -657,9 +760,17 @@ def run_ours(args, wl, scheme, world, rank, local):
               "l2_source": "ncu lts__throughput of the same kernel and workload "
                            "(profiles/k_rk4_<scheme>_traffic.txt), null if the kernel changed since"}
     value = aggregate_rate(wl.particles * args.steps, world, total_ms * 1e-3)
-    srt = sorted(step_ms)
-    p50 = srt[len(srt) // 2]
-    p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+    p50 = lat_ms[len(lat_ms) // 2]
+    p99 = lat_ms[min(len(lat_ms) - 1, int(math.ceil(0.99 * len(lat_ms))) - 1)]
+    roofline = {"bound": "hbm", "achieved": point4["achieved"], "peak": peak, "unit": "GB/s",
+                "frac": point4["frac"], "traffic": traffic,
+                "kernel": "k_rk4 (one launch: every species of one step)",
+                "peak_kind": peak_kind, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                "bytes_per_particle_step": {"tracer": BYTES_TRACER, "inertial": BYTES_INERTIAL,
+                                            "plus_per_launch": "16 N^2 (level pair)"},
+                "compulsory_bytes_per_particle_step": {"tracer": COMPULSORY_TRACER,
+                                                       "inertial": COMPULSORY_INERTIAL},
+                "at_4M_mix": point4, "at_16M_inertial": point16}
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -667,20 +778,16 @@ def run_ours(args, wl, scheme, world, rank, local):
             "fluid_steps_per_s": 1e3 / fluid_graph_ms,
             "fluid_steps_per_s_direct_launches": 1e3 / fluid_ms,
             "coupled_steps_per_s": 1e3 * args.steps / total_ms,
-            "latency_ms": {"p50": p50, "p99": p99,
-                           "what": "device time per coupled step, per call of up to 10 steps"},
+            "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat_ms), "min": lat_ms[0],
+                           "max": lat_ms[-1],
+                           "what": "device time of one coupled step called alone (fluid step, "
+                                   "then particle step), L2 flushed before each sample"},
             "stage_ms": {"fluid": fluid_ms, "particles": part_ms},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_rk4 (one launch: every species of one step)",
-                         "peak_kind": peak_kind,
-                         "bytes_per_particle_step": {"tracer": BYTES_TRACER,
-                                                     "inertial": BYTES_INERTIAL}},
+            "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "what": "set_particles from pinned host + K steps + stats + particles back"},
-            "l2_gather": gather,
-            "roofline_16M": roof16, "tuning": tuning,
+            "l2_gather": gather, "tuning": tuning,
             "gpu_launches": launches, "wall_s": t_wall,
             "clocks": clocks.summary(), "energy": st["energy"]}
     if not args.no_ensemble:
@@ -690,7 +797,11 @@ def run_ours(args, wl, scheme, world, rank, local):
     if not args.no_transport:
         line["transport"] = run_transport(wl)
     if not args.no_serving:
-        line["serving"] = run_serving(dev)
+        line["serving"] = run_serving(dev, count=args.serving_requests, rate=args.serving_rate)
+        line["serving_overload"] = run_serving(dev, count=200, rate=20.0)
+        line["serving_overload"]["note"] = ("the configured 20/s asks for about twice what one "
+                                            "GPU serves: queues grow, so its latency describes "
+                                            "a backlog, not the service")
     if not args.no_cpu_baseline:
         ps, fsps, cores, desc = cpu_oracle_rate(wl, scheme)
         line["cpu_baseline"] = {"value": ps, "unit": "particle-steps/s", "cores": cores,
@@ -713,6 +824,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-kinematic", action="store_true")
     ap.add_argument("--no-transport", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="requests of the served stream to run (its first N of 2000)")
+    ap.add_argument("--serving-rate", type=float, default=6.0,
+                    help="arrival rate (requests/s) of the sustained serving run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()

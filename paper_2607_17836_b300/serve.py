@@ -48,6 +48,16 @@ class Result:
     def latency(self) -> float:
         return self.finished - self.arrival
 
+    @property
+    def queue_wait(self) -> float:
+        """Arrival to admission: waiting for inputs, memory or a batch slot."""
+        return self.admitted - self.arrival
+
+    @property
+    def service(self) -> float:
+        """Admission to the result on the host: the steps in the shared batch."""
+        return self.finished - self.admitted
+
 
 @dataclass
 class _Active:
@@ -210,9 +220,17 @@ class Server:
 
 
 def latency_summary(results) -> dict:
+    """Time-to-result percentiles (linear interpolation), and the same for its
+    two parts: the queue wait (arrival to admission) and the service time
+    (admission to the result on the host)."""
     lat = np.array([r.latency for r in results])
     if lat.size == 0:
         return {"count": 0}
-    return {"count": int(lat.size), "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
-            "max_s": float(lat.max())}
+    out = {"count": int(lat.size), "p50_s": float(np.percentile(lat, 50)),
+           "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+           "max_s": float(lat.max())}
+    for name in ("queue_wait", "service"):
+        x = np.array([getattr(r, name) for r in results])
+        out[name] = {"p50_s": float(np.percentile(x, 50)), "p99_s": float(np.percentile(x, 99)),
+                     "mean_s": float(x.mean()), "max_s": float(x.max())}
+    return out

@@ -24,6 +24,20 @@ def test_latency_summary():
     assert serve.latency_summary([]) == {"count": 0}
 
 
+def test_latency_splits_into_queue_wait_and_service():
+    # request k waits k s for admission, then runs 2 s: wait p50 = 49.5,
+    # service 2 everywhere, and wait + service = time-to-result
+    res = [serve.Result(rid=k, arrival=5.0 * k, admitted=6.0 * k, finished=6.0 * k + 2.0, steps=1,
+                        particles=1, n=32, stats={}) for k in range(100)]
+    s = serve.latency_summary(res)
+    assert s["queue_wait"]["p50_s"] == pytest.approx(49.5)
+    assert s["queue_wait"]["max_s"] == pytest.approx(99.0)
+    assert s["service"]["p50_s"] == pytest.approx(2.0) and s["service"]["p99_s"] == pytest.approx(2.0)
+    assert s["p50_s"] == pytest.approx(51.5)
+    for r in res:
+        assert r.queue_wait + r.service == pytest.approx(r.latency)
+
+
 def test_request_descriptor_and_inputs():
     req = inputs.served_requests(count=5, seed=321)[3]
     d = serve.request_desc(req)
