@@ -730,11 +730,15 @@ def run_ours(args, wl, scheme, world, rank, local):
     t0 = time.perf_counter()
     for k, s in enumerate(wl.species):
         flow.set_particles(k, pinned_in[k].numpy(), s.st)
+    t1 = time.perf_counter()
     flow.step(args.steps)
-    st = flow.stats()
+    st = flow.stats()                 # waits for the steps
+    t2 = time.perf_counter()
     for k, s in enumerate(wl.species):
         flow.particles_into(k, pinned_xy[k].numpy(), pinned_v[k].numpy() if s.st > 0 else None)
     e2e_s = time.perf_counter() - t0
+    e2e_phases = {"upload_ms": 1e3 * (t1 - t0), "steps_and_stats_ms": 1e3 * (t2 - t1),
+                  "readback_ms": 1e3 * (time.perf_counter() - t2)}
     h2d = sum(xy.nbytes for xy in xys)
     d2h = sum(s.count * 16 * (2 if s.st > 0 else 1) for s in wl.species)
     e2e_value = aggregate_rate(wl.particles * args.steps, world, max_over_ranks(e2e_s, world, dev))
@@ -786,7 +790,8 @@ def run_ours(args, wl, scheme, world, rank, local):
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                    "what": "set_particles from pinned host + K steps + stats + particles back"},
+                    "what": "set_particles from pinned host + K steps + stats + particles back",
+                    "phases": e2e_phases},
             "l2_gather": gather, "tuning": tuning,
             "gpu_launches": launches, "wall_s": t_wall,
             "clocks": clocks.summary(), "energy": st["energy"]}
@@ -810,6 +815,31 @@ def run_ours(args, wl, scheme, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_launch(args, wl, scheme):
+    """A fixed launch of k_rk4 for ncu: the bench workload ("mix": 4 species
+    x 1M) or the roofline point ("16M": 16M inertial particles at St = 1),
+    1024^2, 128-thread blocks, re-binning every 20 steps in single cells,
+    the stencil gather of --gather (default: automatic); 21 steps (re-binned at step 20), then three
+    steps with per-stage CUDA events.  `ncu -k regex:k_rk4 -s 21 -c 1`
+    captures the first of those three particle launches."""
+    from paper_2607_17836_b300 import elpath
+    if args.profile_launch == "16M":
+        species = [(16_000_000, 1.0, 99)]
+    else:
+        species = [(s.count, s.st, s.seed) for s in wl.species]
+    g = elpath.Flow(wl.n, wl.nu, wl.dt, wl.omega0(), interp=scheme, max_species=len(species),
+                    max_particles=sum(c for c, _, _ in species), sort_every=SORT_EVERY)
+    for k, (c, st, seed) in enumerate(species):
+        g.set_particles(k, inputs.uniform_positions(c, seed), st)
+    gather = {"auto": elpath.GATHER_AUTO, "registers": elpath.GATHER_REGISTERS,
+              "shared": elpath.GATHER_SHARED}[args.gather]
+    g.set_tuning(128, SORT_EVERY, 0, gather)
+    g.step(21)
+    for _ in range(3):
+        print(json.dumps(g.profile_step()), flush=True)
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -828,6 +858,10 @@ def main():
                     help="requests of the served stream to run (its first N of 2000)")
     ap.add_argument("--serving-rate", type=float, default=6.0,
                     help="arrival rate (requests/s) of the sustained serving run")
+    ap.add_argument("--profile-launch", choices=["mix", "16M"], default=None,
+                    help="only a fixed k_rk4 launch for ncu (see run_profile_launch)")
+    ap.add_argument("--gather", choices=["auto", "registers", "shared"], default="auto",
+                    help="stencil gather of the cubic schemes in --profile-launch")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -837,6 +871,11 @@ def main():
         import torch.distributed as dist
         backend = "nccl" if args.impl == "ours" else "gloo"
         dist.init_process_group(backend)
+    if args.profile_launch:
+        import torch
+        torch.cuda.set_device(local)
+        run_profile_launch(args, wl, scheme)
+        return
     try:
         if args.impl == "reference":
             run_reference(args, wl, scheme, world, rank)

@@ -201,14 +201,24 @@ typedef struct {
     int32_t rk4_threads;  /* threads per block of the particle step: multiple of 32, 64..512 */
     int32_t sort_every;   /* re-bin every k steps (0 = never)                                  */
     int32_t sort_shift;   /* re-binning key = tile of 2^shift x 2^shift cells (0..4)           */
+    int32_t gather;       /* cubic schemes' stencil gather: EL_GATHER_* (bilinear ignores it)  */
     double ms_per_step;   /* filled by the autotuners: measured time per step of the choice   */
 } el_tuning;
+
+/* Stencil gather of the cubic schemes (Eqs. 18-22), same results either way:
+ * EL_GATHER_REGISTERS: each thread keeps its particle's 16 level-pair nodes in
+ * registers; EL_GATHER_SHARED: the 32 particles of a warp share one patch of
+ * nodes in shared memory (pays when many particles share a cell);
+ * EL_GATHER_AUTO (the default): the shared patch when some species holds at
+ * least 2 particles per cell on average, else registers. */
+enum { EL_GATHER_AUTO = 0, EL_GATHER_REGISTERS = 1, EL_GATHER_SHARED = 2 };
 
 el_status el_get_tuning(const el_flow* flow, el_tuning* out);
 el_status el_set_tuning(el_flow* flow, const el_tuning* tuning);
 
 /* Autotuner.  Picks the particle step's block size (fastest of {128, 256,
- * 512} over trial_steps steps, each right after a re-binning), the
+ * 512} over trial_steps steps, each right after a re-binning, for each
+ * stencil gather with the cubic schemes), the
  * re-binning tile (fastest of 1, 2, 4 cells per side, counting its cost)
  * and the cadence from a measured model: the step time grows about linearly
  * as particles drift out of cell order, t(k) = t0 + a k, so with re-binning

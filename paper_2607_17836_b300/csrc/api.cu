@@ -489,6 +489,8 @@ static el_status create_flow(const el_flow_desc* desc, const double* omega0, con
     }
     el_status s = kin ? kinematic_level(f, 0, true) : fluid_init(f, omega0);
     if (s != EL_OK) return bail(s);
+    s = rk4_prepare(f);
+    if (s != EL_OK) return bail(s);
     e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) {
         fail(f, EL_ECUDA, "create: %s", cudaGetErrorString(e));
@@ -541,8 +543,14 @@ el_status el_set_particles(el_flow* f, int32_t species, int64_t np, double st, c
         f->pool_used = kept_used;
     }
     if (placed != EL_OK) return placed;
-    drop_graphs(f);
-    batch_member_changed(f->batch);
+    // The captured step graphs read the species table on the device; what
+    // they bake in is each species' block range and the gather choice, both
+    // set by the particle counts, so new particles in the same numbers keep
+    // them (no re-capture on the next step).
+    if (kept.np != np) {
+        drop_graphs(f);
+        batch_member_changed(f->batch);
+    }
     if (f->d.sort_every > 0) f->since_sort = f->d.sort_every;  // bin the new particles first
     return EL_OK;
 }
@@ -692,6 +700,7 @@ el_status el_get_tuning(const el_flow* f, el_tuning* out) {
     out->rk4_threads = f->rk4_threads;
     out->sort_every = f->d.sort_every;
     out->sort_shift = f->sort_shift;
+    out->gather = f->gather;
     out->ms_per_step = 0.0;
     return EL_OK;
 }
@@ -703,7 +712,10 @@ el_status el_set_tuning(el_flow* f, const el_tuning* t) {
     if (t->sort_every < 0) return fail(f, EL_EINVAL, "sort_every must be >= 0");
     if (t->sort_shift < 0 || t->sort_shift > 4 || (1 << t->sort_shift) > f->n / 4)
         return fail(f, EL_EINVAL, "sort_shift out of range");
+    if (t->gather < EL_GATHER_AUTO || t->gather > EL_GATHER_SHARED)
+        return fail(f, EL_EINVAL, "gather must be EL_GATHER_AUTO, _REGISTERS or _SHARED");
     f->rk4_threads = t->rk4_threads;
+    f->gather = t->gather;
     f->d.sort_every = t->sort_every;
     f->sort_shift = t->sort_shift;
     drop_graphs(f);
@@ -725,7 +737,8 @@ el_status el_autotune(el_flow* f, int32_t trial_steps, el_tuning* best) {
         f->since_sort = 0;
         return EL_OK;
     };
-    return autotune_model(step, apply, sort_all, f->stream, start, trial_steps, best, f->n);
+    const bool cubic = f->d.interp == EL_CATMULL_ROM || f->d.interp == EL_BSPLINE;
+    return autotune_model(step, apply, sort_all, f->stream, start, trial_steps, best, f->n, cubic);
 }
 
 el_status el_destroy_flow(el_flow* f) {

@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_co
 
 // One kernel per interpolation scheme (each with its own register budget);
 // the entries of the other schemes are skipped.
-template <int SCHEME>
+// SHARED: the warp-shared stencil patch of the cubic schemes (as k_rk4).
+template <int SCHEME, bool SHARED>
 __global__ void __launch_bounds__(512, SCHEME == 0 ? 3 : 1) k_batch_rk4(const __grid_constant__ BatchArgs b) {
     for (int t = blockIdx.x; t < b.rk_tasks; t += gridDim.x) {
         const int e = owner_of(b.rk_begin, b.nentries, t);
@@ -118,6 +119,19 @@ __global__ void __launch_bounds__(512, SCHEME == 0 ? 3 : 1) k_batch_rk4(const __
         if (md.scheme != SCHEME) continue;
         const SpeciesDev& sd = *b.rk_sp[e];
         const int p = (t - b.rk_begin[e]) * (int)blockDim.x + (int)threadIdx.x;
+        if constexpr (SHARED) {
+            // warp-shared stencils (as in the single-flow kernel): every
+            // lane of the warp takes part; the branches are block-uniform
+            extern __shared__ float2 el_patch[];
+            const bool active = p < sd.np;
+            if (md.psi_plane >= 0 && !sd.inertial) {
+                if (active) rk4_psi_tracer<SCHEME>(md.psi[md.step % 2], md.n, md.log2n, md.h, sd, p);
+                continue;
+            }
+            rk4_particle_coop<SCHEME>(md.snap[md.step % 2], md.n, md.log2n, md.dt, md.h, sd, p,
+                                      active, el_patch + (threadIdx.x >> 5) * (3 * kPatchCap));
+            continue;
+        }
         if (p >= sd.np) continue;
         if (md.psi_plane >= 0)
             rk4_particle<SCHEME, true>(md.snap[md.step % 2], md.psi[md.step % 2], md.n, md.log2n,
@@ -189,6 +203,7 @@ struct el_batch {
     BatchArgs args{};
     int grid_spec = 0, grid_nl = 0, grid_rk[3] = {0, 0, 0};
     bool scheme_used[3] = {false, false, false};
+    bool rk_shared[3] = {false, false, false};  // warp-shared stencil patch per scheme
     bool tables_valid = false;
     // one coupled step of every member in three captured forms (fluid of
     // step s, particles of s alongside fluid of s + 1, particles of the last
@@ -344,11 +359,26 @@ el_status rebuild_tables(el_batch* b) {
     b->grid_spec = std::max(1, std::min(a.spec_tasks, occ * b->sms));
     BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_nonlinear, kBNlThreads, 0));
     b->grid_nl = std::max(1, std::min(a.nl_tasks, occ * b->sms));
-    void (*rk_kernels[3])(BatchArgs) = {k_batch_rk4<0>, k_batch_rk4<1>, k_batch_rk4<2>};
+    void (*rk_kernels[3][2])(BatchArgs) = {{k_batch_rk4<0, false>, k_batch_rk4<0, false>},
+                                           {k_batch_rk4<1, false>, k_batch_rk4<1, true>},
+                                           {k_batch_rk4<2, false>, k_batch_rk4<2, true>}};
+    const int gather = b->members.empty() ? EL_GATHER_AUTO : b->members[0]->gather;
     for (int sc = 0; sc < 3; sc++) {
         b->scheme_used[sc] = false;
-        for (el_flow* f : b->members) b->scheme_used[sc] = b->scheme_used[sc] || f->d.interp == sc;
-        BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rk_kernels[sc], rk_threads, 0));
+        double density = 0.0;  // particles per cell of the densest species of the scheme
+        for (el_flow* f : b->members) {
+            if (f->d.interp != sc) continue;
+            b->scheme_used[sc] = true;
+            for (int s = 0; s < f->d.max_species; s++)
+                density = std::max(density, (double)f->sp[s].np / (double)f->n2);
+        }
+        b->rk_shared[sc] = rk4_shared_gather(sc, gather, density);
+        const size_t smem = rk4_patch_bytes(b->rk_shared[sc], rk_threads);
+        auto kern = rk_kernels[sc][b->rk_shared[sc] ? 1 : 0];
+        if (smem > 0)
+            BT_CUDA(b, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)rk4_patch_bytes(true, 512)));
+        BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, rk_threads, smem));
         b->grid_rk[sc] = std::max(1, std::min(a.rk_tasks, std::max(1, occ) * b->sms));
     }
     for (FftPool& p : b->pools) ensure_prefix_plans(b, p, p.span());
@@ -407,9 +437,16 @@ el_status enqueue_particles(el_batch* b) {
     const BatchArgs& a = b->args;
     if (a.rk_tasks > 0) {
         int threads = b->members.empty() ? 256 : b->members[0]->rk4_threads;
-        if (b->scheme_used[0]) k_batch_rk4<0><<<b->grid_rk[0], threads, 0, b->stream>>>(a);
-        if (b->scheme_used[1]) k_batch_rk4<1><<<b->grid_rk[1], threads, 0, b->stream>>>(a);
-        if (b->scheme_used[2]) k_batch_rk4<2><<<b->grid_rk[2], threads, 0, b->stream>>>(a);
+        const size_t smem = rk4_patch_bytes(true, threads);
+        if (b->scheme_used[0]) k_batch_rk4<0, false><<<b->grid_rk[0], threads, 0, b->stream>>>(a);
+        if (b->scheme_used[1]) {
+            if (b->rk_shared[1]) k_batch_rk4<1, true><<<b->grid_rk[1], threads, smem, b->stream>>>(a);
+            else k_batch_rk4<1, false><<<b->grid_rk[1], threads, 0, b->stream>>>(a);
+        }
+        if (b->scheme_used[2]) {
+            if (b->rk_shared[2]) k_batch_rk4<2, true><<<b->grid_rk[2], threads, smem, b->stream>>>(a);
+            else k_batch_rk4<2, false><<<b->grid_rk[2], threads, 0, b->stream>>>(a);
+        }
         b->launches += (int)b->scheme_used[0] + (int)b->scheme_used[1] + (int)b->scheme_used[2];
     }
     return EL_OK;
@@ -724,6 +761,7 @@ el_status el_batch_add(el_batch* b, el_flow* f) {
     EL_TRY(pool_join(b, f));
     if (!b->members.empty() && b->members[0]->rk4_threads != f->rk4_threads)
         f->rk4_threads = b->members[0]->rk4_threads;
+    if (!b->members.empty()) f->gather = b->members[0]->gather;  // one setting per batch
     f->own_stream = f->stream;
     f->stream = b->stream;
     cufftSetStream(f->plan_c2r, b->stream);
@@ -820,6 +858,7 @@ namespace {
 el_status batch_apply(el_batch* b, const el_tuning& t) {
     for (el_flow* f : b->members) {
         f->rk4_threads = t.rk4_threads;
+        f->gather = t.gather;
         f->d.sort_every = t.sort_every;
         f->sort_shift = std::min(t.sort_shift, std::max(0, f->log2n - 2));
     }
@@ -835,9 +874,13 @@ extern "C" el_status el_batch_autotune(el_batch* b, int32_t trial_steps, el_tuni
     if (trial_steps < 1) return bfail(b, EL_EINVAL, "trial_steps must be >= 1");
     if (b->members.empty()) return bfail(b, EL_ESTATE, "empty batch");
     el_flow* f0 = b->members[0];
-    el_tuning start{f0->rk4_threads, f0->d.sort_every, f0->sort_shift, 0.0};
+    el_tuning start{f0->rk4_threads, f0->d.sort_every, f0->sort_shift, f0->gather, 0.0};
     int nmin = f0->n;
-    for (el_flow* f : b->members) nmin = std::min(nmin, f->n);
+    bool cubic = false;
+    for (el_flow* f : b->members) {
+        nmin = std::min(nmin, f->n);
+        cubic = cubic || f->d.interp == EL_CATMULL_ROM || f->d.interp == EL_BSPLINE;
+    }
     auto step = [b](int n) { return el_batch_step(b, n); };
     auto apply = [b](el_tuning t) { return batch_apply(b, t); };
     auto sort_all = [b]() -> el_status {
@@ -847,5 +890,5 @@ extern "C" el_status el_batch_autotune(el_batch* b, int32_t trial_steps, el_tuni
         }
         return EL_OK;
     };
-    return autotune_model(step, apply, sort_all, b->stream, start, trial_steps, best_out, nmin);
+    return autotune_model(step, apply, sort_all, b->stream, start, trial_steps, best_out, nmin, cubic);
 }

@@ -115,7 +115,8 @@ struct el_flow {
 
     int64_t step = 0;          // coupled steps taken
     int rk4_threads = 256;     // threads per block of the particle step (tunable)
-    int prefetch_threads = 0;  // block size the cached prefetch distance was computed for
+    int gather = EL_GATHER_AUTO;  // cubic schemes' stencil gather (tunable)
+    int prefetch_threads = 0;  // block size (and gather, + 1024) the cached prefetch distance is for
     int prefetch_particles = 0;
     int sort_shift = 0;        // re-binning key: tiles of 2^sort_shift cells per side
     el_batch* batch = nullptr; // the batch this flow is a member of, if any
@@ -201,6 +202,11 @@ int flow_planes(const el_flow_desc& d);                // spectral planes of the
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
                         const double* vxy);
 el_status particles_step_all(el_flow* f, int64_t step);  // K6 (rk4.cu), every species in one launch
+// K6 with the warp-shared stencil patch?  For scheme `interp` under setting
+// `gather`, with `density` = the largest particles-per-cell of a species (rk4.cu).
+bool rk4_shared_gather(int interp, int gather, double density);
+size_t rk4_patch_bytes(bool shared, int threads);  // dynamic shared memory of a K6 block (rk4.cu)
+el_status rk4_prepare(el_flow* f);                 // K6 launch attributes, at flow creation (rk4.cu)
 el_status particles_get(el_flow* f, int s, double* xy, double* vxy);
 // msd x, msd y, cluster, <dx^4>, <dy^4> (the squared displacements' second moments)
 el_status particles_stats_into(el_flow* f, int s, double* out5);

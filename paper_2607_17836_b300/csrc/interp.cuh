@@ -242,6 +242,135 @@ struct Stencil {
     }
 };
 
+// Warp-shared stencils of the cubic schemes (Eqs. 18-22).  After re-binning
+// the 32 particles of a warp sit in a few neighbouring cells, so their 4 x 4
+// stencils overlap: the warp loads the union of them once (one node per lane
+// per pass) into its own region of shared memory, and every stage of every
+// lane reads its 16 nodes from there.  Nothing is held in registers between
+// stages, which leaves room for more resident warps than a per-thread register
+// copy of the 16 level pairs (64 registers) would.
+//
+// The patch covers the warp's cells plus one cell on every side, so a stage
+// that moves one cell away (the common crossing) still finds its stencil; a
+// stage further away, or a warp whose cells spread over more than kPatchCap
+// nodes, gathers from the level pair in global memory instead.  Each node is
+// stored three times, as the value each stage time reads: level n (stage 1),
+// the SUM of the two levels (stages 2 and 3, times 1/2 after the sum over the
+// stencil) and level n+1 (stage 4); the values and the order of the
+// arithmetic are the register cache's, so both give the same bits.
+constexpr int kPatchCap = 192;  // nodes of one warp's patch
+
+template <int SCHEME>
+struct PatchStencil {
+    const float2* lv;    // the warp's patch: [0, cap) level n, [cap, 2 cap) sum, [2 cap, 3 cap) level n+1
+    int w;               // patch width (nodes per row)
+    int base;            // patch index of the first node of the particle's own cell's stencil
+    bool patch;          // the patch holds the warp's stencils
+    const float4* snap;  // the level pair (for stencils outside the patch)
+    int n, ci, cj;       // grid size, the particle's cell
+
+    __device__ __forceinline__ void to_mid() {}
+
+    template <int THETA>
+    __device__ __forceinline__ float2 first_stage(float2 o) const {
+        return eval<THETA>(0, 0, o);
+    }
+
+    template <int THETA>
+    __device__ __forceinline__ float2 at(const float4* __restrict__, int, int, int, float2 l) const {
+        const float flx = floorf(l.x), fly = floorf(l.y);
+        return eval<THETA>((int)flx, (int)fly, fsub2(l, make_float2(flx, fly)));
+    }
+
+    // Value of the node at THETA (0: level n, 1: the level sum, 2: level n+1)
+    // from its level pair.
+    template <int THETA>
+    __device__ __forceinline__ static float2 pick(float4 t) {
+        return THETA == 0 ? make_float2(t.x, t.y)
+                          : (THETA == 2 ? make_float2(t.z, t.w)
+                                        : __fadd2_rn(make_float2(t.x, t.y), make_float2(t.z, t.w)));
+    }
+
+    // The stencil of cell (ci + fi, cj + fj) at offsets s, THETA as in Stencil::eval.
+    template <int THETA>
+    __device__ __forceinline__ float2 eval(int fi, int fj, float2 s) const {
+        float2 wt[4];
+        cubic_weights2<SCHEME>(s, wt);
+        float2 r = make_float2(0.f, 0.f);
+        if (patch && (unsigned)(fi + 1) <= 2u && (unsigned)(fj + 1) <= 2u) {
+            const float2* q = lv + THETA * kPatchCap + base + fj * w + fi;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const float2* qr = q + b * w;
+                float2 row = __fmul2_rn(pair(wt[0].x), qr[0]);
+#pragma unroll
+                for (int a = 1; a < 4; a++) row = __ffma2_rn(pair(wt[a].x), qr[a], row);
+                r = __ffma2_rn(pair(wt[b].y), row, r);
+            }
+        } else {
+            const int m = n - 1;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const float4* rp = snap + ((cj + fj - 1 + b) & m) * n;
+                float2 row = __fmul2_rn(pair(wt[0].x), pick<THETA>(node_ld(rp, (ci + fi - 1) & m)));
+#pragma unroll
+                for (int a = 1; a < 4; a++)
+                    row = __ffma2_rn(pair(wt[a].x), pick<THETA>(node_ld(rp, (ci + fi - 1 + a) & m)), row);
+                r = __ffma2_rn(pair(wt[b].y), row, r);
+            }
+        }
+        if (THETA == 1) r = __fmul2_rn(r, pair(0.5f));
+        return r;
+    }
+};
+
+// Set up the warp's patch: every lane of the warp calls this (inactive lanes
+// too, with active = false); at least one lane is active.  The cells are
+// taken relative to the first active lane's, as signed distances modulo n
+// (any representative works: node indices wrap), and the patch spans the
+// warp's cells plus one cell each side, plus the stencil's reach (one node
+// before the cell, two after).  `region` is the warp's 3 * kPatchCap float2
+// of shared memory; the previous contents may still be read by lanes of an
+// earlier particle, so the warp synchronises before overwriting them.
+template <int SCHEME>
+__device__ __forceinline__ void patch_setup(PatchStencil<SCHEME>& st, float2* __restrict__ region,
+                                            const float4* __restrict__ snap, int n, int ci, int cj,
+                                            bool active, unsigned act) {
+    const unsigned full = 0xffffffffu;
+    const int src = __ffs(act) - 1;
+    const int ri = __shfl_sync(full, ci, src), rj = __shfl_sync(full, cj, src);
+    const int m = n - 1, half = n >> 1;
+    const int di = active ? ((ci - ri + half) & m) - half : 0;
+    const int dj = active ? ((cj - rj + half) & m) - half : 0;
+    const int imin = __reduce_min_sync(full, di), imax = __reduce_max_sync(full, di);
+    const int jmin = __reduce_min_sync(full, dj), jmax = __reduce_max_sync(full, dj);
+    const int w = imax - imin + 6, h = jmax - jmin + 6;
+    st.lv = region;
+    st.w = w;
+    st.base = (dj - jmin + 1) * w + (di - imin + 1);
+    st.patch = w * h <= kPatchCap;  // the same on every lane
+    st.snap = snap;
+    st.n = n;
+    st.ci = ci;
+    st.cj = cj;
+    __syncwarp();
+    if (st.patch) {
+        const int oi = ri + imin - 2, oj = rj + jmin - 2;
+        // row of patch index k: floor((k + 1/2) / w), exact in FP32 here
+        // (k < kPatchCap, so the quotient is >= 1/(2 kPatchCap) from an integer)
+        const float inv_w = 1.0f / (float)w;
+        for (int k = (int)(threadIdx.x & 31); k < w * h; k += 32) {
+            const int r = (int)(((float)k + 0.5f) * inv_w);
+            const int c = k - r * w;
+            const float4 t = node_ld(snap, ((oj + r) & m) * n + ((oi + c) & m));
+            region[k] = make_float2(t.x, t.y);
+            region[kPatchCap + k] = __fadd2_rn(make_float2(t.x, t.y), make_float2(t.z, t.w));
+            region[2 * kPatchCap + k] = make_float2(t.z, t.w);
+        }
+        __syncwarp();
+    }
+}
+
 // EL_ANALYTIC: the kinematic field itself at the particle (no grid, no
 // stencil); THETA selects the stage time.  The integer part of k x in grid
 // units is reduced modulo n exactly before the phase is formed.

@@ -6,6 +6,8 @@
 #include "common.cuh"
 #include "stages.cuh"
 
+#include <algorithm>
+
 namespace el {
 namespace {
 
@@ -19,11 +21,24 @@ constexpr int kRK4MaxThreads = 512;
 #ifndef EL_RK4_CUBIC_MIN_BLOCKS
 #define EL_RK4_CUBIC_MIN_BLOCKS 1
 #endif
-// The cubic kernels' register cap: 96 (4-8 B of spills) fits 5 blocks of 128
-// threads per SM against 4 at their natural 120, and measured 8-10 % faster at
-// 1024^2 (4 and 16 particles per cell); 80 spills 250 B and is slower.
+// The cubic kernels' register caps.  Register-cached stencils: 96 (4-8 B of
+// spills) fits 5 blocks of 128 threads per SM against 4 at their natural 120,
+// 8-10 % faster at 1024^2 (4 and 16 particles per cell); 80 spills 250 B and
+// is slower.  Warp-shared stencils (PatchStencil: nothing large stays in
+// registers): 56, measured against 48 and 64 at 16 particles per cell.
 #ifndef EL_RK4_CUBIC_MAXNREG
 #define EL_RK4_CUBIC_MAXNREG 96
+#endif
+#ifndef EL_RK4_SHARED_MAXNREG
+#define EL_RK4_SHARED_MAXNREG 56
+#endif
+// EL_GATHER_AUTO takes the warp-shared patch from this many particles per
+// cell (of the densest species) on.  Measured (Catmull-Rom, St = 1): 1 per
+// cell (1024^2, 1M a species) registers 0.110 ms, shared 0.175 ms; 4 per
+// cell (2048^2, 16M) 0.434 / 0.383 ms; 16 per cell (1024^2, 16M) 0.395 /
+// 0.344 ms.
+#ifndef EL_RK4_SHARED_DENSITY
+#define EL_RK4_SHARED_DENSITY 2.0
 #endif
 #ifndef EL_RK4_PREFETCH_WAVES
 #define EL_RK4_PREFETCH_WAVES 1.0
@@ -77,17 +92,22 @@ __device__ __forceinline__ int species_of(const unsigned (&begin)[kMaxSpecies], 
 // block per run of particles: at the register cap that gives 75 % occupancy
 // a grid-stride loop over runs measured 15-18 % slower (more spills, and a
 // block no longer retires between runs).
-template <int SCHEME, bool PSI>
+//
+// SHARED (cubic schemes only): the warp-shared stencil patch (PatchStencil)
+// instead of each thread's register copy of its cell's stencil; the same
+// arithmetic on the same values, so the same bits.
+template <int SCHEME, bool PSI, bool SHARED>
 __global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_MIN_BLOCKS : EL_RK4_CUBIC_MIN_BLOCKS)
-    __maxnreg__(SCHEME == 1 || SCHEME == 2 ? EL_RK4_CUBIC_MAXNREG : 128) k_rk4(const __grid_constant__ RK4Args a) {
+    __maxnreg__(SHARED ? EL_RK4_SHARED_MAXNREG : (SCHEME == 1 || SCHEME == 2 ? EL_RK4_CUBIC_MAXNREG : 128))
+    k_rk4(const __grid_constant__ RK4Args a) {
     const int s = species_of(a.block_begin, blockIdx.x);
     const SpeciesDev& sd = a.table[s];
     const int first = (int)(blockIdx.x - a.block_begin[s]) * (int)blockDim.x;
     prefetch_state(sd, first, a.prefetch);
     const int p = first + (int)threadIdx.x;
-    if (p >= sd.np) return;
+    const bool active = p < sd.np;
 #if EL_CHECK_BOUNDS
-    {
+    if (active) {
         const uint32_t c = sd.cell[sd.cur][p];
         const float2 o = sd.off[sd.cur][p];
         const bool bad = (c & 0xffffu) >= (uint32_t)a.n || (c >> 16) >= (uint32_t)a.n ||
@@ -98,37 +118,92 @@ __global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_
         }
     }
 #endif
-    rk4_particle<SCHEME, PSI>(a.snap, a.psi, a.n, a.log2n, a.dt, a.h, sd, p, &a.kin);
+    if constexpr (SHARED) {
+        // warp-shared stencils: every lane of the warp takes part
+        static_assert(SCHEME == 1 || SCHEME == 2, "the shared patch serves the cubic schemes");
+        extern __shared__ float2 el_patch[];
+        if (PSI && !sd.inertial) {  // the streamfunction path (the same for the whole block)
+            if (active) rk4_psi_tracer<SCHEME>(a.psi, a.n, a.log2n, a.h, sd, p);
+            return;
+        }
+        rk4_particle_coop<SCHEME>(a.snap, a.n, a.log2n, a.dt, a.h, sd, p, active,
+                                  el_patch + (threadIdx.x >> 5) * (3 * kPatchCap));
+    } else {
+        if (!active) return;
+        rk4_particle<SCHEME, PSI>(a.snap, a.psi, a.n, a.log2n, a.dt, a.h, sd, p, &a.kin);
+    }
 }
 }  // namespace
 
-// Resident blocks of k_rk4 on the whole GPU at the flow's block size.
+bool rk4_shared_gather(int interp, int gather, double density) {
+    if (interp != EL_CATMULL_ROM && interp != EL_BSPLINE) return false;
+    return gather == EL_GATHER_SHARED || (gather == EL_GATHER_AUTO && density >= EL_RK4_SHARED_DENSITY);
+}
+
+// Dynamic shared memory of a particle-step block of `threads` threads: the
+// warps' stencil patches with the shared gather, none otherwise.
+size_t rk4_patch_bytes(bool shared, int threads) {
+    return shared ? (size_t)(threads / 32) * 3 * kPatchCap * sizeof(float2) : 0;
+}
+
+// Allow the shared-gather kernels the dynamic shared memory of 512-thread
+// blocks (above the 48 KiB default) on the current device.
 template <int SCHEME, bool PSI>
+static cudaError_t rk4_allow_smem() {
+    return cudaFuncSetAttribute(k_rk4<SCHEME, PSI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rk4_patch_bytes(true, kRK4MaxThreads));
+}
+
+// Launch attributes of the flow's particle kernels, set when the flow is
+// created (outside any stream capture) on its device.
+el_status rk4_prepare(el_flow* f) {
+    if (f->d.interp == EL_CATMULL_ROM) {
+        EL_CUDA_OK(f, (rk4_allow_smem<1, false>()));
+        EL_CUDA_OK(f, (rk4_allow_smem<1, true>()));
+    } else if (f->d.interp == EL_BSPLINE) {
+        EL_CUDA_OK(f, (rk4_allow_smem<2, false>()));
+        EL_CUDA_OK(f, (rk4_allow_smem<2, true>()));
+    }
+    return EL_OK;
+}
+
+// Resident blocks of k_rk4 on the whole GPU at the flow's block size.
+template <int SCHEME, bool PSI, bool SHARED>
 static int rk4_wave_blocks(int threads) {
     int per_sm = 0, dev = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rk4<SCHEME, PSI>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rk4<SCHEME, PSI, SHARED>, threads,
+                                                  rk4_patch_bytes(SHARED, threads));
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return per_sm * sms;
 }
 
-// The prefetch distance of k_rk4 in particles, cached per block size:
-// EL_RK4_PREFETCH_WAVES resident waves (SMs x resident blocks), a whole number
-// of blocks.  Measured at 1024^2: 0.5, 1 and 2 waves time alike, 4-5 % faster
-// than no prefetch for every scheme and particle count.
-static int rk4_prefetch_distance(el_flow* f) {
+// The prefetch distance of k_rk4 in particles, cached per block size and
+// gather: EL_RK4_PREFETCH_WAVES resident waves (SMs x resident blocks), a
+// whole number of blocks.  Measured at 1024^2: 0.5, 1 and 2 waves time alike,
+// 4-5 % faster than no prefetch for every scheme and particle count.
+static int rk4_prefetch_distance(el_flow* f, bool shared) {
     const int T = f->rk4_threads;
-    if (f->prefetch_threads == T) return f->prefetch_particles;
+    const int key = T + (shared ? 1024 : 0);
+    if (f->prefetch_threads == key) return f->prefetch_particles;
     int wave = 0;
     const bool psi = f->psi_plane >= 0;
     switch (f->d.interp) {
-        case EL_BILINEAR: wave = psi ? rk4_wave_blocks<0, true>(T) : rk4_wave_blocks<0, false>(T); break;
-        case EL_CATMULL_ROM: wave = psi ? rk4_wave_blocks<1, true>(T) : rk4_wave_blocks<1, false>(T); break;
-        case EL_BSPLINE: wave = psi ? rk4_wave_blocks<2, true>(T) : rk4_wave_blocks<2, false>(T); break;
-        default: wave = rk4_wave_blocks<3, false>(T); break;
+        case EL_BILINEAR:
+            wave = psi ? rk4_wave_blocks<0, true, false>(T) : rk4_wave_blocks<0, false, false>(T);
+            break;
+        case EL_CATMULL_ROM:
+            wave = shared ? (psi ? rk4_wave_blocks<1, true, true>(T) : rk4_wave_blocks<1, false, true>(T))
+                          : (psi ? rk4_wave_blocks<1, true, false>(T) : rk4_wave_blocks<1, false, false>(T));
+            break;
+        case EL_BSPLINE:
+            wave = shared ? (psi ? rk4_wave_blocks<2, true, true>(T) : rk4_wave_blocks<2, false, true>(T))
+                          : (psi ? rk4_wave_blocks<2, true, false>(T) : rk4_wave_blocks<2, false, false>(T));
+            break;
+        default: wave = rk4_wave_blocks<3, false, false>(T); break;
     }
     f->prefetch_particles = (int)((double)wave * EL_RK4_PREFETCH_WAVES + 0.5) * T;
-    f->prefetch_threads = T;
+    f->prefetch_threads = key;
     return f->prefetch_particles;
 }
 
@@ -145,7 +220,11 @@ el_status particles_step_all(el_flow* f, int64_t step) {
     a.log2n = f->log2n;
     a.dt = (float)f->d.dt;
     a.h = (float)(f->d.dt * (double)f->n / kTwoPi);
-    a.prefetch = rk4_prefetch_distance(f);
+    double density = 0.0;  // particles per cell of the densest species
+    for (int s = 0; s < f->d.max_species; s++)
+        density = std::max(density, (double)f->sp[s].np / (double)f->n2);
+    const bool shared = rk4_shared_gather(f->d.interp, f->gather, density);
+    a.prefetch = rk4_prefetch_distance(f, shared);
     unsigned blocks = 0;
     int ns = 0;
     for (int s = 0; s < f->d.max_species; s++) {
@@ -160,20 +239,30 @@ el_status particles_step_all(el_flow* f, int64_t step) {
     // slots past max_species are never selected
     for (int s = f->d.max_species; s < kMaxSpecies; s++) a.block_begin[s] = 0xffffffffu;
     const int T = f->rk4_threads;
+    const size_t smem = rk4_patch_bytes(shared, T);
+    cudaStream_t st = f->stream;
+    const bool psi = f->psi_plane >= 0;
     if (f->d.interp == EL_ANALYTIC) {
         a.kin = kinematic_stage_args(f, step);
-        k_rk4<3, false><<<blocks, T, 0, f->stream>>>(a);
-    } else if (f->psi_plane < 0) {
-        switch (f->d.interp) {
-            case EL_BILINEAR: k_rk4<0, false><<<blocks, T, 0, f->stream>>>(a); break;
-            case EL_CATMULL_ROM: k_rk4<1, false><<<blocks, T, 0, f->stream>>>(a); break;
-            default: k_rk4<2, false><<<blocks, T, 0, f->stream>>>(a); break;
+        k_rk4<3, false, false><<<blocks, T, 0, st>>>(a);
+    } else if (f->d.interp == EL_BILINEAR) {
+        if (psi) k_rk4<0, true, false><<<blocks, T, 0, st>>>(a);
+        else k_rk4<0, false, false><<<blocks, T, 0, st>>>(a);
+    } else if (f->d.interp == EL_CATMULL_ROM) {
+        if (shared) {
+            if (psi) k_rk4<1, true, true><<<blocks, T, smem, st>>>(a);
+            else k_rk4<1, false, true><<<blocks, T, smem, st>>>(a);
+        } else {
+            if (psi) k_rk4<1, true, false><<<blocks, T, 0, st>>>(a);
+            else k_rk4<1, false, false><<<blocks, T, 0, st>>>(a);
         }
     } else {
-        switch (f->d.interp) {
-            case EL_BILINEAR: k_rk4<0, true><<<blocks, T, 0, f->stream>>>(a); break;
-            case EL_CATMULL_ROM: k_rk4<1, true><<<blocks, T, 0, f->stream>>>(a); break;
-            default: k_rk4<2, true><<<blocks, T, 0, f->stream>>>(a); break;
+        if (shared) {
+            if (psi) k_rk4<2, true, true><<<blocks, T, smem, st>>>(a);
+            else k_rk4<2, false, true><<<blocks, T, smem, st>>>(a);
+        } else {
+            if (psi) k_rk4<2, true, false><<<blocks, T, 0, st>>>(a);
+            else k_rk4<2, false, false><<<blocks, T, 0, st>>>(a);
         }
     }
     EL_LAUNCHED(f);

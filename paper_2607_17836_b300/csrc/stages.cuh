@@ -224,12 +224,16 @@ __device__ __forceinline__ void rk4_load_state(const SpeciesDev& sd, int p, Part
 // each node without blending.  All (x, y) and (u, v) arithmetic is on float
 // pairs (one paired FP32 instruction per two lanes of work).  h = dt * n /
 // (2 pi): grid units per unit velocity.  Writes the new state.
-template <int SCHEME>
-__device__ __forceinline__ void rk4_finish(const float4* __restrict__ snap, int n, int log2n, float dt,
-                                           float h, const SpeciesDev& sd, ParticleRK4<SCHEME>& q) {
-    const int cur = sd.cur, p = q.p, ci = q.ci, cj = q.cj;
-    const float2 o = q.o;
-    Stencil<SCHEME>& st = q.st;
+//
+// G supplies the fluid velocity at the stages: first_stage<THETA>(o) in the
+// particle's own cell, to_mid() after it, at<THETA>(snap, n, ci, cj, l) at
+// grid-unit position l relative to cell (ci, cj) (Stencil: a register cache
+// of one cell's nodes; PatchStencil: a warp's shared-memory patch).
+template <class G>
+__device__ __forceinline__ void rk4_update(const float4* __restrict__ snap, int n, int log2n, float dt,
+                                           float h, const SpeciesDev& sd, int p, int ci, int cj,
+                                           float2 o, float2 vel, G& st) {
+    const int cur = sd.cur;
     const float2 h2 = make_float2(0.5f * h, 0.5f * h), h1 = make_float2(h, h);
     const float2 two = make_float2(2.0f, 2.0f);
     float2 np2;
@@ -248,7 +252,7 @@ __device__ __forceinline__ void rk4_finish(const float4* __restrict__ snap, int 
         // v_s = v + c_s dt a_{s-1}, a_s = (u(x_s, t_s) - v_s) / St (Eq. 13).
         const float2 ist = make_float2(sd.inv_st, sd.inv_st);
         const float2 d2 = make_float2(0.5f * dt, 0.5f * dt), d1 = make_float2(dt, dt);
-        const float2 v = q.v;
+        const float2 v = vel;
         float2 u1 = st.template first_stage<0>(o);
         st.to_mid();
         float2 a1 = __fmul2_rn(fsub2(u1, v), ist);
@@ -278,6 +282,12 @@ __device__ __forceinline__ void rk4_finish(const float4* __restrict__ snap, int 
         int2 m = imgp[p];
         imgp[p] = make_int2(m.x + dix, m.y + diy);
     }
+}
+
+template <int SCHEME>
+__device__ __forceinline__ void rk4_finish(const float4* __restrict__ snap, int n, int log2n, float dt,
+                                           float h, const SpeciesDev& sd, ParticleRK4<SCHEME>& q) {
+    rk4_update(snap, n, log2n, dt, h, sd, q.p, q.ci, q.cj, q.o, q.v, q.st);
 }
 
 // Tracers driven by the streamfunction (tracer_velocity = 1, Eq. 11): the
@@ -312,6 +322,32 @@ __device__ __forceinline__ void rk4_psi_tracer(const float2* __restrict__ psi, i
         int2 m = imgp[p];
         imgp[p] = make_int2(m.x + dix, m.y + diy);
     }
+}
+
+// One RK4 step of particle p of species sd for the cubic schemes, with the
+// warp's stencils shared through shared memory (PatchStencil).  Every lane of
+// the warp calls this; lanes with active = false (past the species' end) only
+// help load the patch.  `region`: the warp's 3 * kPatchCap float2 of shared
+// memory.
+template <int SCHEME>
+__device__ __forceinline__ void rk4_particle_coop(const float4* __restrict__ snap, int n, int log2n,
+                                                  float dt, float h, const SpeciesDev& sd, int p,
+                                                  bool active, float2* __restrict__ region) {
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (act == 0) return;  // the same on every lane
+    int ci = 0, cj = 0;
+    float2 o = make_float2(0.f, 0.f), v = o;
+    if (active) {
+        const int cur = sd.cur;
+        const uint32_t c = EL_STATE_LD(sd.cell[cur] + p);
+        ci = (int)(c & 0xffffu);
+        cj = (int)(c >> 16);
+        o = EL_STATE_LD(sd.off[cur] + p);
+        if (sd.inertial) v = EL_STATE_LD(sd.vel[cur] + p);
+    }
+    PatchStencil<SCHEME> st;
+    patch_setup(st, region, snap, n, ci, cj, active, act);
+    if (active) rk4_update(snap, n, log2n, dt, h, sd, p, ci, cj, o, v, st);
 }
 
 // One RK4 step of particle p of species sd between levels n and n+1 (the

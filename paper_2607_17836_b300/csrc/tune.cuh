@@ -58,7 +58,8 @@ el_status time_call(Fn fn, cudaStream_t stream, double* ms) {
 // The autotuner (shared by single flows and batches).  None of its choices
 // changes any result, so its trial windows are ordinary steps.
 //  1. block size of the particle step: the fastest of {128, 256, 512} over
-//     `trial` steps, each started right after a re-binning;
+//     `trial` steps, each started right after a re-binning, and with the
+//     cubic schemes (`cubic`) for each stencil gather (registers, shared);
 //  2. re-binning tile: the fastest of {1, 2, 4} cells per side, counting the
 //     re-binning cost spread over 40 steps;
 //  3. re-binning cadence from a measured model: particles drift out of cell
@@ -68,21 +69,26 @@ el_status time_call(Fn fn, cudaStream_t stream, double* ms) {
 //     timed right after a re-binning and W steps later, c directly.
 template <class StepFn, class ApplyFn, class SortFn>
 el_status autotune_model(StepFn step, ApplyFn apply, SortFn sort_all, cudaStream_t stream,
-                         el_tuning start, int trial, el_tuning* best_out, int n) {
+                         el_tuning start, int trial, el_tuning* best_out, int n, bool cubic) {
     char why[128] = {0};
     el_tuning best = start;
     best.sort_every = 0;  // the trials below place their own re-binnings
     double best_ms = 1e30;
-    for (int th : {128, 256, 512}) {
-        el_tuning t = best;
-        t.rk4_threads = th;
-        EL_TRY(apply(t));
-        EL_TRY(sort_all());
-        double ms = 0.0;
-        EL_TRY(time_steps(step, stream, trial, &ms, why));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = t;
+    const el_tuning base = best;
+    for (int g : {EL_GATHER_REGISTERS, EL_GATHER_SHARED}) {
+        if (!cubic && g != EL_GATHER_REGISTERS) continue;
+        for (int th : {128, 256, 512}) {
+            el_tuning t = base;
+            t.rk4_threads = th;
+            t.gather = cubic ? g : base.gather;
+            EL_TRY(apply(t));
+            EL_TRY(sort_all());
+            double ms = 0.0;
+            EL_TRY(time_steps(step, stream, trial, &ms, why));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
         }
     }
     double best_cost = 1e30, sort_ms = 0.0;

@@ -49,7 +49,11 @@ class el_flow_desc(ctypes.Structure):
 
 class el_tuning(ctypes.Structure):
     _fields_ = [("rk4_threads", ctypes.c_int32), ("sort_every", ctypes.c_int32),
-                ("sort_shift", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
+                ("sort_shift", ctypes.c_int32), ("gather", ctypes.c_int32),
+                ("ms_per_step", ctypes.c_double)]
+
+
+GATHER_AUTO, GATHER_REGISTERS, GATHER_SHARED = 0, 1, 2
 
 
 class el_kinematic(ctypes.Structure):
@@ -314,10 +318,10 @@ class Flow:
         t = el_tuning()
         self._check(self._lib.el_get_tuning(self._h, ctypes.byref(t)))
         return {"rk4_threads": t.rk4_threads, "sort_every": t.sort_every,
-                "sort_shift": t.sort_shift}
+                "sort_shift": t.sort_shift, "gather": t.gather}
 
-    def set_tuning(self, rk4_threads=256, sort_every=20, sort_shift=0):
-        t = el_tuning(int(rk4_threads), int(sort_every), int(sort_shift), 0.0)
+    def set_tuning(self, rk4_threads=256, sort_every=20, sort_shift=0, gather=GATHER_AUTO):
+        t = el_tuning(int(rk4_threads), int(sort_every), int(sort_shift), int(gather), 0.0)
         self._check(self._lib.el_set_tuning(self._h, ctypes.byref(t)))
 
     def autotune(self, trial_steps=10) -> dict:
@@ -325,7 +329,8 @@ class Flow:
         t = el_tuning()
         self._check(self._lib.el_autotune(self._h, int(trial_steps), ctypes.byref(t)))
         return {"rk4_threads": t.rk4_threads, "sort_every": t.sort_every,
-                "sort_shift": t.sort_shift, "ms_per_step": t.ms_per_step}
+                "sort_shift": t.sort_shift, "gather": t.gather,
+                "ms_per_step": t.ms_per_step}
 
     def save_state(self) -> bytes:
         """el_save_state: the flow's complete state at its current step."""
@@ -405,7 +410,8 @@ class Batch:
         t = el_tuning()
         self._check(self._lib.el_batch_autotune(self._h, int(trial_steps), ctypes.byref(t)))
         return {"rk4_threads": t.rk4_threads, "sort_every": t.sort_every,
-                "sort_shift": t.sort_shift, "ms_per_step": t.ms_per_step}
+                "sort_shift": t.sort_shift, "gather": t.gather,
+                "ms_per_step": t.ms_per_step}
 
     def size(self) -> int:
         return int(self._lib.el_batch_size(self._h))

@@ -49,13 +49,13 @@ def test_stable_runs_report_finite_statistics():
     g.close()
 
 
-def run(case_threads, interp, sort_every):
+def run(case_threads, interp, sort_every, gather=elpath.GATHER_AUTO):
     n = 128
     g = elpath.Flow(n, 1e-4, 5e-4, inputs.decaying_turbulence(n, 12), interp=interp,
                     max_species=2, max_particles=6000, sort_every=sort_every)
     g.set_particles(0, inputs.uniform_positions(3000, 1), 0.0)
     g.set_particles(1, inputs.uniform_positions(3000, 2), 1.0)
-    g.set_tuning(case_threads, sort_every, 0)
+    g.set_tuning(case_threads, sort_every, 0, gather)
     g.step(150)
     s = g.stats()
     out = [g.field(0)] + list(g.particles(0, 3000)) + list(g.particles(1, 3000))
@@ -71,9 +71,15 @@ def test_reruns_are_bitwise_identical(interp):
     a = run(256, interp, 10)
     b = run(256, interp, 10)
     c = run(128, interp, 17)          # another block size and re-binning cadence
-    for x, y, z in zip(a, b, c):
+    # the two stencil gathers of the cubic schemes (register copy, warp-shared
+    # patch in shared memory): the same arithmetic on the same values
+    d = run(512, interp, 10, elpath.GATHER_REGISTERS)
+    e = run(128, interp, 0, elpath.GATHER_SHARED)
+    for x, y, z, u, v in zip(a, b, c, d, e):
         np.testing.assert_array_equal(x, y)
         np.testing.assert_array_equal(x, z)
+        np.testing.assert_array_equal(x, u)
+        np.testing.assert_array_equal(x, v)
 
 
 def test_non_finite_host_inputs_are_refused_and_leave_the_flow_unchanged():
