@@ -25,3 +25,11 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_sessionfinish(session, exitstatus):
+    # the achieved-error table of the GPU parity tests, when both are set
+    log, table = os.environ.get("EL_PARITY_LOG"), os.environ.get("EL_PARITY_TABLE")
+    if log and table and os.path.exists(log):
+        from parity import write_table
+        write_table(log, table)

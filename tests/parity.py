@@ -1,6 +1,9 @@
 """Shared helpers for the GPU-vs-oracle parity tests (test code only)."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 import oracle
@@ -13,6 +16,49 @@ GATHER_RTOL = 2e-6        # interpolated velocity: max |err| / max |u|
 OMEGA_RTOL = 1e-5         # vorticity L-inf after 100 steps: max |err| / max |omega|
 POS_ATOL = 1e-5 * TWO_PI  # particle positions after 200 steps
 STATS_RTOL = 1e-2         # long chaotic runs: dispersion and clustering
+
+
+SCHEME_NAMES = {0: "bilinear", 1: "Catmull-Rom", 2: "B-spline"}
+
+
+def record(workload, scheme, quantity, value, bound):
+    """Append an achieved error (and the bound the test asserts, or None for
+    a figure that is reported but not asserted) as one JSON line to the file
+    named by EL_PARITY_LOG, when that is set."""
+    path = os.environ.get("EL_PARITY_LOG")
+    if not path:
+        return
+    name = SCHEME_NAMES.get(scheme, scheme) if scheme is not None else "-"
+    with open(path, "a") as fh:
+        fh.write(json.dumps({"workload": workload, "scheme": name, "quantity": quantity,
+                             "value": float(value),
+                             "bound": None if bound is None else float(bound)}) + "\n")
+
+
+def write_table(log_path, out_path):
+    """Render the recorded errors as a markdown table (worst value per
+    workload, scheme and quantity)."""
+    rows = {}
+    with open(log_path) as fh:
+        for line in fh:
+            r = json.loads(line)
+            key = (r["workload"], r["scheme"], r["quantity"])
+            if key not in rows or r["value"] > rows[key]["value"]:
+                rows[key] = r
+    lines = ["# Achieved errors of the CUDA path against the FP64 oracle",
+             "",
+             "Written by the GPU parity tests (tests/conftest.py, EL_PARITY_LOG and",
+             "EL_PARITY_TABLE): the worst value each test measured, beside the bound it asserts.",
+             "",
+             "| workload | scheme | quantity | achieved | bound |",
+             "|---|---|---|---|---|"]
+    for key in sorted(rows):
+        r = rows[key]
+        bound = "reported" if r["bound"] is None else f"{r['bound']:.3g}"
+        lines.append(f"| {r['workload']} | {r['scheme']} | {r['quantity']} | {r['value']:.3g} | "
+                     f"{bound} |")
+    with open(out_path, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
 
 
 def rel_linf(a, b):

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from paper_2607_17836_b300 import elpath, inputs
-from parity import OMEGA_RTOL, POS_ATOL, OracleRun, rel_linf
+from parity import OMEGA_RTOL, POS_ATOL, OracleRun, record, rel_linf
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -41,8 +41,11 @@ def test_decaying_turbulence_1024_all_schemes():
         g.step(100)
     o.step(100)
     w_ref = o.flow.fields(("w",))["w"]
-    for g in flows:
-        assert rel_linf(g.field(0), w_ref) < OMEGA_RTOL
+    name = "decaying turbulence 1024^2, 4 x 1M"
+    for scheme, g in enumerate(flows):
+        werr = rel_linf(g.field(0), w_ref)
+        record(name, scheme, "omega L-inf rel., 100 steps", werr, OMEGA_RTOL)
+        assert werr < OMEGA_RTOL
     for g in flows:
         g.step(100)
     o.step(100)
@@ -51,9 +54,12 @@ def test_decaying_turbulence_1024_all_schemes():
             pos, vel = g.particles(k, s.count)
             ref = o.positions(4 * scheme + k)
             err = np.max(np.abs(pos[::stride] - ref))
+            record(name, scheme, "max position error, 200 steps (every 244th)", err, POS_ATOL)
             assert err < POS_ATOL, (scheme, k, err)
             if s.st > 0:
-                assert np.max(np.abs(vel[::stride] - o.velocities(4 * scheme + k))) < 1e-4
+                verr = np.max(np.abs(vel[::stride] - o.velocities(4 * scheme + k)))
+                record(name, scheme, "max velocity error, 200 steps (every 244th)", verr, 1e-4)
+                assert verr < 1e-4
         st = g.stats()
         assert st["finite"]
         g.close()
@@ -69,12 +75,19 @@ def test_kelvin_helmholtz_2048_16M():
     g.set_particles(0, xy, sp.st)
     o = OracleRun(wl.n, wl.nu, wl.dt, w0)
     o.add(1, sp.st, xy[::64])
+    name = "shear layer 2048^2, 16M at St = 1"
     g.step(100)
     o.step(100)
-    assert rel_linf(g.field(0), o.flow.fields(("w",))["w"]) < OMEGA_RTOL
+    werr = rel_linf(g.field(0), o.flow.fields(("w",))["w"])
+    record(name, 1, "omega L-inf rel., 100 steps", werr, OMEGA_RTOL)
+    assert werr < OMEGA_RTOL
     g.step(100)
     o.step(100)
     pos, vel = g.particles(0, sp.count)
-    assert np.max(np.abs(pos[::64] - o.positions(0))) < POS_ATOL
-    assert np.max(np.abs(vel[::64] - o.velocities(0))) < 1e-4
+    perr = np.max(np.abs(pos[::64] - o.positions(0)))
+    verr = np.max(np.abs(vel[::64] - o.velocities(0)))
+    record(name, 1, "max position error, 200 steps (every 64th)", perr, POS_ATOL)
+    record(name, 1, "max velocity error, 200 steps (every 64th)", verr, 1e-4)
+    assert perr < POS_ATOL
+    assert verr < 1e-4
     g.close()

@@ -14,7 +14,7 @@ import pytest
 import oracle
 from paper_2607_17836_b300 import elpath, inputs
 from parity import (GATHER_RTOL, OMEGA_RTOL, POS_ATOL, STATS_RTOL, TWO_PI, OracleRun, decaying,
-                    gpu_flow, oracle_stencil, rel_linf)
+                    gpu_flow, oracle_stencil, record, rel_linf)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -33,10 +33,16 @@ def test_taylor_green_64_tracers_config():
     X, Y = inputs.grid(wl.n)
     exact = 2 * math.exp(-2 * wl.nu * wl.dt * wl.steps) * np.sin(X) * np.sin(Y)
     w = g.field(0)
+    wl_name = "Taylor-Green 64^2, 4096 tracers"
+    record(wl_name, 0, "omega L-inf rel. vs closed form, 200 steps", rel_linf(w, exact), 2e-6)
     assert rel_linf(w, exact) < 2e-6   # FP32 storage: ~steps^0.5 * 2^-24 unbiased
-    assert rel_linf(w, o.flow.fields(("w",))["w"]) < OMEGA_RTOL
+    werr = rel_linf(w, o.flow.fields(("w",))["w"])
+    record(wl_name, 0, "omega L-inf rel., 200 steps", werr, OMEGA_RTOL)
+    assert werr < OMEGA_RTOL
     pos, _ = g.particles(0, 4096)
-    assert np.max(np.abs(pos - o.positions(0))) < POS_ATOL
+    perr = np.max(np.abs(pos - o.positions(0)))
+    record(wl_name, 0, "max position error, 200 steps", perr, POS_ATOL)
+    assert perr < POS_ATOL
     st = g.stats()
     assert abs(st["energy"] - 0.25 * math.exp(-4 * wl.nu * wl.dt * wl.steps)) < 1e-6
     psi0 = np.sin(xy[:, 0]) * np.sin(xy[:, 1])
@@ -53,6 +59,9 @@ def test_vorticity_parity_128(mode):
         g.step(steps)
         o.step(steps)
         of = o.fields(("u", "v", "w"))
+        if steps == 90:
+            record(f"decaying 128^2, AB2 mode {mode}", None, "omega L-inf rel., 100 steps",
+                   rel_linf(g.field(0), of["w"]), OMEGA_RTOL)
         assert rel_linf(g.field(0), of["w"]) < OMEGA_RTOL
         assert rel_linf(g.field(1), of["u"]) < OMEGA_RTOL
         assert rel_linf(g.field(2), of["v"]) < OMEGA_RTOL
@@ -86,7 +95,10 @@ def test_gather_parity(scheme, prefilter):
             b = oracle.interp(cur[comp], scheme, pts[:, 0], pts[:, 1])
             ref.append((1 - theta) * a + theta * b)
         ref = np.stack(ref, axis=1)
-        assert np.max(np.abs(uv - ref)) / np.max(np.abs(ref)) < GATHER_RTOL, theta
+        gerr = np.max(np.abs(uv - ref)) / np.max(np.abs(ref))
+        record("gather, 64^2 field, 20011 points" + ("" if prefilter else " (raw B-spline)"), scheme,
+               "interpolated velocity rel. error", gerr, GATHER_RTOL)
+        assert gerr < GATHER_RTOL, theta
     if scheme == 2 and prefilter:
         # the GPU's spectral prefilter vs the oracle's cyclic tridiagonal solve
         u = g.field(1)
@@ -117,7 +129,10 @@ def test_coupled_particles_parity_128(scheme):
     o.step(200)
     for s in range(4):
         pos, vel = g.particles(s, counts[s])
-        assert np.max(np.abs(pos - o.positions(s))) < POS_ATOL, s
+        perr = np.max(np.abs(pos - o.positions(s)))
+        record("decaying 128^2, 4 species (1-12345 particles)", scheme,
+               "max position error, 200 steps", perr, POS_ATOL)
+        assert perr < POS_ATOL, s
         if sts[s] > 0:
             assert np.max(np.abs(vel - o.velocities(s))) < 1e-4, s
 
@@ -295,4 +310,7 @@ def test_streamfunction_tracers_parity(scheme):
     o.step(200)
     for s in range(2):
         pos, _ = g.particles(s, 4000)
-        assert np.max(np.abs(pos - o.positions(s))) < POS_ATOL, s
+        perr = np.max(np.abs(pos - o.positions(s)))
+        record("streamfunction tracers (Eq. 11) + inertial, 128^2", scheme,
+               "max position error, 200 steps", perr, POS_ATOL)
+        assert perr < POS_ATOL, s
