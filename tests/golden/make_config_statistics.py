@@ -12,7 +12,7 @@ chaotic runs are compared with (dispersion and clustering within 1 %):
     FP64 fluid solve (the fluid depends on neither the particles nor the
     scheme); zero-slip start, as the library does;
   * double shear layer, 2048^2, 4000 steps (nu = 5e-5, dt = 2.5e-4): every
-    64th of the 16M inertial particles at St = 1 (262,144), Catmull-Rom.
+    64th of the 16M inertial particles at St = 1 (250,000), Catmull-Rom.
 
 At each checkpoint step the file records, per scheme and species, the
 per-axis mean-square displacement (Sec. 5.5) and the clustering index of the

@@ -6,7 +6,7 @@ oracle integrates just the sampled ones in the same fluid).
     of St = 0.1, 1, 10, each of the three schemes: vorticity after 100 steps,
     sampled positions and velocities after 200 steps;
   * 2048^2 double shear layer, 16M inertial particles at St = 1, Catmull-Rom:
-    vorticity after 100 steps, every 64th particle (262,144 of them) after
+    vorticity after 100 steps, every 64th particle (250,000 of them) after
     200 steps (about 0.8 s of oracle work per step on the host).
 """
 import numpy as np

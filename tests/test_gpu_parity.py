@@ -158,6 +158,38 @@ def test_periodic_crossing_and_unwrapping():
         assert np.max(np.abs(pos[:, 0] - xy[:, 0])) > 2 * TWO_PI   # wrapped at least twice
 
 
+def test_new_particles_mid_run_keep_or_rebuild_the_step_graphs():
+    # Particles set again in the same numbers keep the flow's captured step
+    # graphs (they read the particle state through the device species table);
+    # other numbers rebuild them.  Either way the new particles then follow
+    # the oracle's trajectories from the level they were set at.
+    n, nu, dt = 64, 1e-3, 1e-3
+    w0 = decaying(n, seed=21, k0=6.0)
+    g = gpu_flow(n, nu, dt, w0, interp=1, max_species=2, max_particles=6000, sort_every=7)
+    o = OracleRun(n, nu, dt, w0)
+    first = inputs.uniform_positions(3000, seed=22)
+    g.set_particles(0, first, 0.0)
+    g.set_particles(1, first, 1.0)
+    g.step(30)
+    o.step(30)
+    for count, seed in ((3000, 23), (1234, 24)):     # the same numbers, then others
+        xy = inputs.uniform_positions(count, seed)
+        g.set_particles(0, xy, 0.0)
+        g.set_particles(1, xy, 1.0)
+        k0 = len(o.sets)
+        o.add(1, 0.0, xy)
+        o.add(1, 1.0, xy)
+        g.step(25)
+        o.step(25)
+        for s in range(2):
+            pos, _ = g.particles(s, count)
+            perr = np.max(np.abs(pos - o.positions(k0 + s)))
+            record("particles set again mid-run, 64^2", 1, "max position error, 25 steps", perr,
+                   POS_ATOL)
+            assert perr < POS_ATOL, (count, s, perr)
+    g.close()
+
+
 def test_empty_and_single_species_and_sort_invariance():
     n, nu, dt = 64, 1e-3, 1e-3
     w0 = decaying(n, seed=10, k0=6.0)
@@ -251,6 +283,10 @@ def test_argument_errors():
         g.set_particles(0, bad, 0.0)
     with pytest.raises(elpath.ElpathError):
         g.set_particles(0, xy[:5], -1.0)
+    with pytest.raises(elpath.ElpathError) as e:
+        g.set_tuning(128, 20, 0, 3)          # no such stencil gather
+    assert e.value.status == 1
+    assert g.tuning()["gather"] == elpath.GATHER_AUTO
     # a failed call leaves the flow usable
     g.set_particles(0, xy[:5], 0.0)
     g.step(2)
