@@ -140,6 +140,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
     char* ey = take(n * 8);
     char* px = take(nh * 4);
     char* py = take(n * 4);
+    char* twiddle = take(n * 8);
     char* table = take(sizeof(SpeciesDev) * kMaxSpecies);
     char* check = take(4 * sizeof(uint32_t));
     char* bad_input = take(sizeof(unsigned long long));
@@ -171,6 +172,7 @@ size_t carve(const el_flow_desc& d, size_t fft_bytes, el_flow* f, char* base) {
         f->ey = (float2*)ey;
         f->pre_x = (float*)px;
         f->pre_y = (float*)py;
+        f->twiddle = (float2*)twiddle;
         f->table = (SpeciesDev*)table;
         f->check = (uint32_t*)check;
         f->bad_input = (unsigned long long*)bad_input;
@@ -481,6 +483,23 @@ static el_status create_flow(const el_flow_desc* desc, const double* omega0, con
     if (e != cudaSuccess) {
         fail(f, EL_ECUDA, "table upload: %s", cudaGetErrorString(e));
         return bail(EL_ECUDA);
+    }
+    std::vector<float2> tw;
+    if (fused_fluid_supported(f)) {
+        // exp(-2 pi i m / n) in FP64, rounded once
+        tw.resize((size_t)f->n);
+        for (int m = 0; m < f->n; m++) {
+            const double t = kTwoPi * (double)m / (double)f->n;
+            tw[m] = make_float2((float)std::cos(t), (float)-std::sin(t));
+        }
+        e = cudaMemcpyAsync(f->twiddle, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice, f->stream);
+        if (e != cudaSuccess) {
+            fail(f, EL_ECUDA, "twiddle upload: %s", cudaGetErrorString(e));
+            return bail(EL_ECUDA);
+        }
+        el_status fs = fused_fluid_prepare(f);
+        if (fs != EL_OK) return bail(fs);
+        f->fused = true;
     }
     e = cudaMemsetAsync(f->check, 0, 4 * sizeof(uint32_t), f->stream);
     if (e != cudaSuccess) {

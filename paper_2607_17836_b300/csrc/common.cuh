@@ -93,6 +93,8 @@ struct el_flow {
     double* stage64 = nullptr;  // n^2 doubles: host <-> device field staging
     float2* ex = nullptr;     // exp(-nu kx^2 dt) as (hi, lo) floats, kx = 0..n/2
     float2* ey = nullptr;     // exp(-nu ky^2 dt) as (hi, lo) floats, row index 0..n-1
+    float2* twiddle = nullptr;  // exp(-2 pi i m / n), m < n (the fused 1024^2 step's transforms)
+    bool fused = false;         // the fluid step runs the fused kernels (fused_fluid.cu)
     float* pre_x = nullptr;   // spline prefilter 3/(2 + cos(k dx)) per kx
     float* pre_y = nullptr;   // ... per row index
     el::SpeciesDev* table = nullptr;  // device copy of h_table
@@ -182,6 +184,7 @@ el_status fail(el_flow* f, el_status s, const char* fmt, ...);
     } while (0)
 
 // ---- fluid (fluid.cu) -------------------------------------------------------
+struct SpecArgs;
 el_status fluid_init(el_flow* f, const double* omega0_host);
 el_status fluid_step(el_flow* f, int64_t step);   // K5+K1, C2R, K3, R2C
 el_status fluid_diagnostics(el_flow* f);          // E, Z, P -> red_out[0..2]
@@ -193,6 +196,10 @@ el_status kinematic_get_field(el_flow* f, int which, double* host_nn);  // omega
 void kinematic_diagnostics(const el_flow* f, double* e3);  // exact E, Z, P
 el_status fluid_refresh_planes(el_flow* f);       // physical planes of the current level
 el_status fluid_get_field(el_flow* f, int which, double* host_nn);
+// ---- the fused 1024^2 fluid step (fused_fluid.cu) -----------------------------------
+bool fused_fluid_supported(const el_flow* f);
+el_status fused_fluid_prepare(el_flow* f);
+el_status fluid_step_fused(el_flow* f, const SpecArgs& a, int64_t step);
 
 // ---- flow descriptors (api.cu) ----------------------------------------------------
 const char* flow_desc_problem(const el_flow_desc* d);  // nullptr when the descriptor is valid

@@ -212,6 +212,7 @@ el_status fluid_init(el_flow* f, const double* omega0_host) {
 el_status fluid_step(el_flow* f, int64_t step) {
     NvtxRange range("fluid_step");
     if (f->kinematic) return kinematic_level(f, step + 1, false);
+    if (f->fused) return fluid_step_fused(f, spec_args(f, step == 0), step);
     k_spectral<true><<<spec_grid(f), kSpecThreads, 0, f->stream>>>(spec_args(f, step == 0));
     EL_LAUNCHED(f);
     return finish_rhs(f, step + 1, false);
@@ -247,7 +248,9 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn) {
         EL_TRY(fft_exec_c2r(f, f->plan_c2r1, f->aux_spec, f->aux_phys));
         k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(f->aux_phys, out, f->n2, 1, 0);
     } else if (which == 1 || which == 2) {
-        // physical planes 0/1 hold u, v of the current level
+        // physical planes 0/1 hold u, v of the current level (the fused step
+        // does not write them: rebuild them from omega-hat first)
+        if (f->fused) EL_TRY(fluid_refresh_planes(f));
         k_f2d<<<blocks_for((int64_t)f->n2, T), T, 0, f->stream>>>(f->phys + (which - 1) * f->n2,
                                                                    out, f->n2, 1, 0);
     } else {

@@ -62,80 +62,135 @@ struct SpecArgs {
 //   w <- E w - dt (3/2 E N - 1/2 E^2 H), H <- N.
 // mode 1 (Eq. 10 as printed): R = -N - nu k^2 w; w <- w + dt (3/2 R - 1/2 H), H <- R.
 // The first step is forward Euler in either mode.
-template <bool ADVANCE>
-__device__ __forceinline__ void spectral_mode(const SpecArgs& a, int i, int j) {
-    const int n = a.n;
-    const size_t q = (size_t)j * a.nh + i;
-    const int kx = i, ky = wavenumber_row(j, n);
-    const bool keep = kept(kx, ky, n);
+// What the AB2 update of one mode reads.
+struct ModeIn {
+    float2 w, N, wl, H, ea, eb;
+};
+
+// The loads of the AB2 update of mode (i, j) (row-major index q), all issued
+// together.
+__device__ __forceinline__ ModeIn load_mode(const SpecArgs& a, int i, int j, size_t q) {
     const float2* __restrict__ nhat = a.nhat;
     const float2* __restrict__ hist_in = a.hist;
     const float2* __restrict__ lo_in = a.what_lo;
-    // every load first, so they are all in flight together
-    float2 w = a.what[q];
-    float2 N = make_float2(0.f, 0.f), wl = N, H = N, ea = N, eb = N;
-    if (ADVANCE) {
-        N = nhat[q];
-        wl = lo_in[q];
-        if (!a.first) H = hist_in[q];
-        if (a.mode == 0) {
-            ea = a.ex[i];
-            eb = a.ey[j];
-        }
-        if (!keep) N = make_float2(0.f, 0.f);
-        const float dt = a.dt;
-        float2 inc, hi, lo, hist_out;
-        if (a.mode == 0) {
-            float Eh = ea.x * eb.x;  // E = Eh + El (two-product of the hi parts)
-            float El = fmaf(ea.x, eb.x, -Eh) + fmaf(ea.x, eb.y, ea.y * eb.x);
-            float E2 = Eh * Eh;
-            float c1 = a.first ? dt : 1.5f * dt, c2 = a.first ? 0.f : 0.5f * dt * E2;
-            float px = Eh * w.x, py = Eh * w.y;
-            hi = make_float2(px, py);
-            lo = make_float2(fmaf(Eh, w.x, -px) + fmaf(El, w.x, Eh * wl.x),
-                             fmaf(Eh, w.y, -py) + fmaf(El, w.y, Eh * wl.y));
-            inc = make_float2(fmaf(c2, H.x, -c1 * Eh * N.x), fmaf(c2, H.y, -c1 * Eh * N.y));
-            hist_out = N;
-        } else {
-            float nuk2 = a.nu * (float)(kx * kx + ky * ky);
-            float2 R = make_float2(-N.x - nuk2 * w.x, -N.y - nuk2 * w.y);
-            inc = a.first ? make_float2(dt * R.x, dt * R.y)
-                          : make_float2(dt * (1.5f * R.x - 0.5f * H.x), dt * (1.5f * R.y - 0.5f * H.y));
-            hi = w;
-            lo = wl;
-            hist_out = R;
-        }
-        float sx, exx, sy, eyy;
-        two_sum(hi.x, lo.x + inc.x, sx, exx);
-        two_sum(hi.y, lo.y + inc.y, sy, eyy);
-        w = make_float2(sx, sy);
-        a.hist[q] = hist_out;
-        a.what[q] = w;
-        a.what_lo[q] = make_float2(exx, eyy);
+    ModeIn in;
+    in.w = a.what[q];
+    in.N = nhat[q];
+    in.wl = lo_in[q];
+    in.H = make_float2(0.f, 0.f);
+    in.ea = in.H;
+    in.eb = in.H;
+    if (!a.first) in.H = hist_in[q];
+    if (a.mode == 0) {
+        in.ea = a.ex[i];
+        in.eb = a.ey[j];
     }
+    return in;
+}
+
+// The AB2 update of mode (i, j) from its loaded inputs: writes the new
+// omega-hat (both parts) and history, returns the new high part.
+__device__ __forceinline__ float2 advance_loaded(const SpecArgs& a, int i, int j, size_t q, const ModeIn& in) {
+    const int n = a.n;
+    const int kx = i, ky = wavenumber_row(j, n);
+    const bool keep = kept(kx, ky, n);
+    float2 w = in.w, N = in.N;
+    const float2 wl = in.wl, H = in.H, ea = in.ea, eb = in.eb;
+    if (!keep) N = make_float2(0.f, 0.f);
+    const float dt = a.dt;
+    float2 inc, hi, lo, hist_out;
+    if (a.mode == 0) {
+        float Eh = ea.x * eb.x;  // E = Eh + El (two-product of the hi parts)
+        float El = fmaf(ea.x, eb.x, -Eh) + fmaf(ea.x, eb.y, ea.y * eb.x);
+        float E2 = Eh * Eh;
+        float c1 = a.first ? dt : 1.5f * dt, c2 = a.first ? 0.f : 0.5f * dt * E2;
+        float px = Eh * w.x, py = Eh * w.y;
+        hi = make_float2(px, py);
+        lo = make_float2(fmaf(Eh, w.x, -px) + fmaf(El, w.x, Eh * wl.x),
+                         fmaf(Eh, w.y, -py) + fmaf(El, w.y, Eh * wl.y));
+        inc = make_float2(fmaf(c2, H.x, -c1 * Eh * N.x), fmaf(c2, H.y, -c1 * Eh * N.y));
+        hist_out = N;
+    } else {
+        float nuk2 = a.nu * (float)(kx * kx + ky * ky);
+        float2 R = make_float2(-N.x - nuk2 * w.x, -N.y - nuk2 * w.y);
+        inc = a.first ? make_float2(dt * R.x, dt * R.y)
+                      : make_float2(dt * (1.5f * R.x - 0.5f * H.x), dt * (1.5f * R.y - 0.5f * H.y));
+        hi = w;
+        lo = wl;
+        hist_out = R;
+    }
+    float sx, exx, sy, eyy;
+    two_sum(hi.x, lo.x + inc.x, sx, exx);
+    two_sum(hi.y, lo.y + inc.y, sy, eyy);
+    w = make_float2(sx, sy);
+    a.hist[q] = hist_out;
+    a.what[q] = w;
+    a.what_lo[q] = make_float2(exx, eyy);
+    return w;
+}
+
+// The AB2 update of mode (i, j) (row-major index q), reading N-hat, the low
+// part and the history and writing the new omega-hat (both parts) and
+// history; returns the new high part.
+__device__ __forceinline__ float2 advance_mode(const SpecArgs& a, int i, int j, size_t q) {
+    return advance_loaded(a, i, j, q, load_mode(a, i, j, q));
+}
+
+// Plane `p` of the spectral planes of omega-hat w (high part) at mode (i, j):
+// 0 u-hat = i ky psi-hat, 1 v-hat = -i kx psi-hat (Eqs. 5, 6; psi-hat = w/k^2,
+// psi-hat(0) = 0), 2 i kx w, 3 i ky w (Eq. 4), then with the spline prefilter
+// 4, 5 = u-hat, v-hat times the prefilter factor pre_x[i] pre_y[j], and
+// psi_plane = psi-hat (times the same factor with the prefilter), all scaled
+// by 1/n^2 (the inverse transform's normalisation).
+__device__ __forceinline__ float2 plane_value(const SpecArgs& a, int p, int i, int j, float2 w) {
+    const int n = a.n;
+    const int kx = i, ky = wavenumber_row(j, n);
     const float dkx = (i == n / 2) ? 0.f : (float)kx;  // Nyquist: zero derivative
     const float dky = (j == n / 2) ? 0.f : (float)ky;
     const float k2 = (float)(kx * kx + ky * ky);
     w.x *= a.scale;
     w.y *= a.scale;
-    const float ik2 = k2 > 0.f ? 1.f / k2 : 0.f;  // psi-hat(0) = 0 (Eq. 5)
+    if (p == 2) return make_float2(-dkx * w.y, dkx * w.x);
+    if (p == 3) return make_float2(-dky * w.y, dky * w.x);
+    const float ik2 = k2 > 0.f ? 1.f / k2 : 0.f;
     const float2 psi = make_float2(w.x * ik2, w.y * ik2);
-    const float2 uh = make_float2(-dky * psi.y, dky * psi.x);  // u-hat = i ky psi-hat
-    const float2 vh = make_float2(dkx * psi.y, -dkx * psi.x);  // v-hat = -i kx psi-hat
+    const float pf = (a.spline && p >= 4) ? a.pre_x[i] * a.pre_y[j] : 1.0f;
+    if (p == a.psi_plane) return make_float2(psi.x * pf, psi.y * pf);
+    if (p == 0 || p == 4) {
+        const float2 uh = make_float2(-dky * psi.y, dky * psi.x);
+        return p == 0 ? uh : make_float2(uh.x * pf, uh.y * pf);
+    }
+    const float2 vh = make_float2(dkx * psi.y, -dkx * psi.x);
+    return p == 1 ? vh : make_float2(vh.x * pf, vh.y * pf);
+}
+
+// AB2 update (when ADVANCE) and the spectral velocity / gradient planes of
+// the resulting omega-hat.
+//
+// omega-hat is held as an unevaluated sum w_hi + w_lo of two floats: one
+// float would round the small per-step change (the viscous decay is only
+// nu k^2 dt of w) the same way step after step and drift by up to half an
+// ulp per step; the pair keeps about 44 bits.  Only w_hi feeds the planes.
+// mode 0 (integrating factor): E = exp(-nu k^2 dt) = ex[kx] * ey[ky] (the 1-D
+//   factors computed on the host in FP64, held as float pairs);
+//   w <- E w - dt (3/2 E N - 1/2 E^2 H), H <- N.
+// mode 1 (Eq. 10 as printed): R = -N - nu k^2 w; w <- w + dt (3/2 R - 1/2 H), H <- R.
+// The first step is forward Euler in either mode.
+template <bool ADVANCE>
+__device__ __forceinline__ void spectral_mode(const SpecArgs& a, int i, int j) {
+    const size_t q = (size_t)j * a.nh + i;
+    const float2 w = ADVANCE ? advance_mode(a, i, j, q) : a.what[q];
     const size_t m = a.nmodes;
     float2* __restrict__ spec = a.spec;
-    spec[q] = uh;
-    spec[m + q] = vh;
-    spec[2 * m + q] = make_float2(-dkx * w.y, dkx * w.x);  // i kx omega-hat
-    spec[3 * m + q] = make_float2(-dky * w.y, dky * w.x);  // i ky omega-hat
-    // Interpolating cubic-spline coefficients: (c_{i-1} + 4 c_i + c_{i+1})/6 = f_i
-    // is diagonal in Fourier space with factor (2 + cos k dx)/3 per axis.
-    const float pf = a.spline ? a.pre_x[i] * a.pre_y[j] : 1.0f;
+    spec[q] = plane_value(a, 0, i, j, w);
+    spec[m + q] = plane_value(a, 1, i, j, w);
+    spec[2 * m + q] = plane_value(a, 2, i, j, w);
+    spec[3 * m + q] = plane_value(a, 3, i, j, w);
     if (a.spline) {
-        spec[4 * m + q] = make_float2(uh.x * pf, uh.y * pf);
-        spec[5 * m + q] = make_float2(vh.x * pf, vh.y * pf);
+        spec[4 * m + q] = plane_value(a, 4, i, j, w);
+        spec[5 * m + q] = plane_value(a, 5, i, j, w);
     }
-    if (a.psi_plane >= 0) spec[(size_t)a.psi_plane * m + q] = make_float2(psi.x * pf, psi.y * pf);
+    if (a.psi_plane >= 0) spec[(size_t)a.psi_plane * m + q] = plane_value(a, a.psi_plane, i, j, w);
 }
 
 // N = u wx + v wy at node i (Eq. 7), and node i's level pair (m-1, m) of the
