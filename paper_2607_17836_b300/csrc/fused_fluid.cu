@@ -253,6 +253,61 @@ __device__ __forceinline__ void stage_rows(float2* __restrict__ buf, const float
     if (p1 >= 0) stage_plane(buf + kRowWarps * kRowPitch, G, p1, y0);
 }
 
+// The same staging of planes p0 and p1 split in two: the loads into
+// registers (issued early, in flight while the warp transforms), then the
+// stores into the staging buffer (once every warp is done reading it).
+struct Staged {
+    float2 t[2][kStagePasses];
+};
+__device__ __forceinline__ void stage_load(Staged& st, const float2* __restrict__ G, int p0, int p1, int y0) {
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int p = q == 0 ? p0 : p1;
+#pragma unroll
+        for (int k = 0; k < kStagePasses; k++) {
+            const int e = threadIdx.x + k * kRowWarps * 32;
+            if (e < kStageElems) st.t[q][k] = G[((size_t)p * kFKCP + (e >> 2)) * kFN + y0 + (e & 3)];
+        }
+    }
+}
+__device__ __forceinline__ void stage_store(const Staged& st, float2* __restrict__ buf) {
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+#pragma unroll
+        for (int k = 0; k < kStagePasses; k++) {
+            const int e = threadIdx.x + k * kRowWarps * 32;
+            if (e < kStageElems) buf[(q * kRowWarps + (e & 3)) * kRowPitch + (e >> 2)] = st.t[q][k];
+        }
+    }
+}
+
+// dst[x] = (src[x].z, src[x].w, new[x]) for the row's 1024 nodes (lane +
+// 32 i holds new value v[i]): the read-modify-write of the level pair in
+// batches of 8 loads per lane, the next batch's loads issued before the
+// current batch is stored.
+__device__ __forceinline__ void write_pair_row(const float4* __restrict__ src, float4* __restrict__ dst,
+                                               const float2 (&v)[32], int lane) {
+    float4 cur[8], nxt[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) cur[k] = src[lane + 32 * k];
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        if (b < 3) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) nxt[k] = src[lane + 32 * (8 * (b + 1) + k)];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int i = 8 * b + k;
+            dst[lane + 32 * i] = make_float4(cur[k].z, cur[k].w, v[i].x, v[i].y);
+        }
+        if (b < 3) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) cur[k] = nxt[k];
+        }
+    }
+}
+
 // The complex row sequence z[k] = A[k] + i B[k] of two real planes (staged
 // in `buf` for this warp's row), for register k = lane + 32 i: kept columns,
 // their mirror images (Hermitian symmetry of a real plane's spectrum) for
@@ -295,14 +350,16 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_fused_rows(const __grid_cons
     const int y0 = blockIdx.x * kRowWarps, y = y0 + warp;
     load_twiddles<kRowWarps * 32>(tw2, r.tw);
     stage_rows(buf, r.G, 2, 3, y0);
+    Staged next;
+    stage_load(next, r.G, 0, 1, y0);  // in flight during the first transform
     __syncthreads();
     float2 v[32];
     row_pair(v, mine0, mine1, lane);  // wx + i wy
-    __syncthreads();
-    stage_rows(buf, r.G, 0, 1, y0);
     fft1024<1>(v, tb, tw2, lane);
 #pragma unroll
     for (int i = 0; i < 32; i++) hold[32 * i + lane] = v[i];
+    __syncthreads();
+    stage_store(next, buf);
     __syncthreads();
     row_pair(v, mine0, mine1, lane);  // u + i v
     fft1024<1>(v, tb, tw2, lane);
@@ -319,13 +376,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_fused_rows(const __grid_cons
         row_pair(v, mine0, mine1, lane);
         fft1024<1>(v, tb, tw2, lane);
     }
-    const float4* __restrict__ src = r.src + (size_t)y * kFN;
-    float4* __restrict__ dst = r.dst + (size_t)y * kFN;
-#pragma unroll
-    for (int i = 0; i < 32; i++) {
-        const float4 old = src[lane + 32 * i];
-        dst[lane + 32 * i] = make_float4(old.z, old.w, v[i].x, v[i].y);
-    }
+    write_pair_row(r.src + (size_t)y * kFN, r.dst + (size_t)y * kFN, v, lane);
     if (P == 5 || P == 7) {  // the streamfunction stencil field
         __syncthreads();
         stage_rows(buf, r.G, r.psi_plane, -1, y0);
