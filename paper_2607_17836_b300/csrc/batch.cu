@@ -12,6 +12,11 @@
 //                     one launch per interpolation scheme present
 //   k_batch_advance                                        per-member step counters
 //
+// Members on the 1024^2 grid whose fluid step is the fused one (fused_fluid.cu)
+// take no part in the spectral, cuFFT and nonlinear stages: the fused
+// kernels advance all of them at once (one launch of each of the four per
+// plane count present, the member in the grid's last dimension).
+//
 // The per-element arithmetic is the single-flow kernels' (stages.cuh), so a
 // member's results do not depend on what else is in the batch.  Each member
 // keeps its own step counter on the device (members join and leave at any
@@ -196,10 +201,14 @@ struct el_batch {
     int* d_rk_begin = nullptr;
     int* d_rk_member = nullptr;
     const SpeciesDev** d_rk_sp = nullptr;
+    FusedMember* d_fused = nullptr;
     // host copies (kept alive while their upload may be pending)
     std::vector<MemberDev> h_members;
     std::vector<int> h_spec_begin, h_nl_begin, h_rk_begin, h_rk_member;
     std::vector<const SpeciesDev*> h_rk_sp;
+    std::vector<FusedMember> h_fused;  // grouped by plane count 4..7
+    int fused_begin[5] = {};           // records of plane count 4 + k: [fused_begin[k], fused_begin[k + 1])
+    const float2* fused_twiddle = nullptr;
     BatchArgs args{};
     int grid_spec = 0, grid_nl = 0, grid_rk[3] = {0, 0, 0};
     bool scheme_used[3] = {false, false, false};
@@ -241,7 +250,8 @@ el_status bfail(el_batch* b, el_status s, const char* fmt, ...) {
 size_t table_bytes(int max_members) {
     size_t m = (size_t)max_members, e = m * kMaxSpecies;
     return align_up(m * sizeof(MemberDev)) + 2 * align_up((m + 1) * sizeof(int)) +
-           2 * align_up((e + 1) * sizeof(int)) + align_up(e * sizeof(void*));
+           2 * align_up((e + 1) * sizeof(int)) + align_up(e * sizeof(void*)) +
+           align_up(m * sizeof(FusedMember));
 }
 
 MemberDev member_of(const el_batch* b, el_flow* f) {
@@ -309,10 +319,38 @@ el_status rebuild_tables(el_batch* b) {
         el_flow* f = b->members[m];
         rk_threads = f->rk4_threads;  // one block size for the whole batch
         b->h_members.push_back(member_of(b, f));
-        b->h_spec_begin.push_back(b->h_spec_begin.back() + f->n * spec_chunks(f->n));
+        const bool own = !f->fused;  // the spectral and nonlinear stages' members
+        b->h_spec_begin.push_back(b->h_spec_begin.back() + (own ? f->n * spec_chunks(f->n) : 0));
         b->h_nl_begin.push_back(b->h_nl_begin.back() +
-                                (int)((f->n2 + kBNlThreads - 1) / kBNlThreads));
+                                (own ? (int)((f->n2 + kBNlThreads - 1) / kBNlThreads) : 0));
     }
+    // the fused members' records, grouped by plane count
+    b->h_fused.clear();
+    b->fused_twiddle = nullptr;
+    for (int planes = 4; planes <= 7; planes++) {
+        b->fused_begin[planes - 4] = (int)b->h_fused.size();
+        for (int m = 0; m < M; m++) {
+            el_flow* f = b->members[m];
+            if (!f->fused || f->nplanes != planes) continue;
+            FusedMember fm{};
+            fm.spec = b->h_members[m].spec;
+            fm.S = f->spec;
+            fm.G = reinterpret_cast<float2*>(f->phys);
+            fm.H = reinterpret_cast<float2*>(f->nl);
+            fm.nhat = f->nhat;
+            for (int k = 0; k < 2; k++) {
+                fm.snap[k] = f->snap[k];
+                fm.psi[k] = f->psi[k];
+            }
+            fm.step = &b->d_members[m].step;
+            fm.psi_plane = f->psi_plane;
+            b->h_fused.push_back(fm);
+            b->fused_twiddle = f->twiddle;  // the same table in every 1024^2 flow
+        }
+        if (b->h_fused.size() > (size_t)b->fused_begin[planes - 4])
+            BT_CUDA(b, fused_fluid_batch_prepare(planes));
+    }
+    b->fused_begin[4] = (int)b->h_fused.size();
     for (int m = 0; m < M; m++) {
         el_flow* f = b->members[m];
         if (f->rk4_threads != rk_threads)
@@ -345,6 +383,9 @@ el_status rebuild_tables(el_batch* b) {
         BT_CUDA(b, cudaMemcpyAsync(b->d_nl_begin, b->h_nl_begin.data(), sizeof(int) * (M + 1),
                                    cudaMemcpyHostToDevice, b->stream));
     }
+    if (!b->h_fused.empty())
+        BT_CUDA(b, cudaMemcpyAsync(b->d_fused, b->h_fused.data(), sizeof(FusedMember) * b->h_fused.size(),
+                                   cudaMemcpyHostToDevice, b->stream));
     if (a.nentries > 0) {
         BT_CUDA(b, cudaMemcpyAsync(b->d_rk_begin, b->h_rk_begin.data(),
                                    sizeof(int) * (a.nentries + 1), cudaMemcpyHostToDevice, b->stream));
@@ -404,7 +445,7 @@ el_status fork_ffts(el_batch* b, cudaStream_t origin, bool c2r) {
     }
     for (size_t m = 0; m < b->members.size(); m++) {
         el_flow* f = b->members[m];
-        if (f->fft_pool >= 0) continue;
+        if (f->fft_pool >= 0 || f->fused) continue;
         cudaStream_t s = b->side[branch++ % kSideStreams];
         cufftHandle plan = c2r ? f->plan_c2r : f->plan_r2c;
         if (cufftSetStream(plan, s) != CUFFT_SUCCESS) return bfail(b, EL_ECUFFT, "cufftSetStream");
@@ -419,10 +460,18 @@ el_status fork_ffts(el_batch* b, cudaStream_t origin, bool c2r) {
     return EL_OK;
 }
 
-// The fluid step (every member) on stream s: spectral stage, C2R, nonlinear
-// stage and level pair, R2C.
+// The fluid step (every member) on stream s: the fused members' kernels,
+// then for the others the spectral stage, C2R, nonlinear stage and level
+// pair, R2C.
 el_status enqueue_fluid(el_batch* b, cudaStream_t s, int ahead) {
     const BatchArgs& a = b->args;
+    for (int k = 0; k < 4; k++) {
+        const int count = b->fused_begin[k + 1] - b->fused_begin[k];
+        if (count == 0) continue;
+        BT_CUDA(b, fused_fluid_batch(s, b->d_fused + b->fused_begin[k], count, 4 + k, ahead,
+                                     b->fused_twiddle));
+        b->launches += 4;
+    }
     k_batch_spectral<<<b->grid_spec, kBSpecThreads, 0, s>>>(a, ahead);
     b->launches++;
     EL_TRY(fork_ffts(b, s, true));
@@ -559,6 +608,7 @@ cufftResult pool_plans(int n, int planes, int slots, cufftHandle* c2r, cufftHand
 // its N-hat moves into the slot (stream-ordered on the batch stream).  On a
 // failed copy the member and the pool are left as they were.
 el_status pool_join(el_batch* b, el_flow* f) {
+    if (f->fused) return EL_OK;  // its transforms are the fused kernels'
     for (size_t q = 0; q < b->pools.size(); q++) {
         FftPool& p = b->pools[q];
         if (p.n != f->n || p.planes != f->nplanes) continue;
@@ -727,6 +777,7 @@ el_status el_batch_create(int32_t max_members, void* dev_workspace, size_t bytes
     b->d_rk_begin = (int*)take((e + 1) * sizeof(int));
     b->d_rk_member = (int*)take((e + 1) * sizeof(int));
     b->d_rk_sp = (const SpeciesDev**)take(e * sizeof(void*));
+    b->d_fused = (FusedMember*)take(m * sizeof(FusedMember));
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);

@@ -200,6 +200,12 @@ el_status fluid_get_field(el_flow* f, int which, double* host_nn);
 bool fused_fluid_supported(const el_flow* f);
 el_status fused_fluid_prepare(el_flow* f);
 el_status fluid_step_fused(el_flow* f, const SpecArgs& a, int64_t step);
+struct FusedMember;
+// The fused step of `count` batched flows with `planes` inverse-transform
+// planes (device records d_members), each at its step counter + `ahead`.
+cudaError_t fused_fluid_batch(cudaStream_t s, const FusedMember* d_members, int count, int planes,
+                              int ahead, const float2* twiddle);
+cudaError_t fused_fluid_batch_prepare(int planes);
 
 // ---- flow descriptors (api.cu) ----------------------------------------------------
 const char* flow_desc_problem(const el_flow_desc* d);  // nullptr when the descriptor is valid

@@ -148,14 +148,76 @@ __device__ __forceinline__ bool row_is_kept(int j) { return j < kFKC || j >= kFN
 
 constexpr int kTile = 32;  // KA's tiles: 32 kept rows x 32 columns
 
+// The arguments of one flow's fused step (RowArgs: those of k_fused_rows).
+struct RowArgs {
+    const float2* G;        // [P][kFKCP][kFN] planes after the column transforms
+    float2* H;              // [kFKCP][kFN] N after the row transform (kept columns)
+    const float2* tw;       // exp(-2 pi i m / 1024), m < 1024
+    const float4* src;      // level pair (m-2, m-1)
+    float4* dst;            // level pair (m-1, m)
+    const float2* psi_src;  // streamfunction pairs, or nullptr
+    float2* psi_dst;
+    int psi_plane;
+};
+
+// Where a launch's flows come from.  OneFlow: one flow, every argument
+// computed on the host (in the kernels' parameter space).  Members: batched
+// flows (device records, one per grid slice: blockIdx.z of KA, blockIdx.y of
+// the others), the step-dependent arguments derived from each member's step
+// counter + `ahead`, as the batched spectral and nonlinear kernels do.
+struct OneFlow {
+    SpecArgs a;
+    RowArgs r;
+    float2* S;
+    float2* G;
+    float2* nhat;
+    __device__ __forceinline__ const SpecArgs& spec(int) const { return a; }
+    __device__ __forceinline__ float2* planes_s(int) const { return S; }
+    __device__ __forceinline__ float2* planes_g(int) const { return G; }
+    __device__ __forceinline__ const RowArgs& rows(int) const { return r; }
+    __device__ __forceinline__ const float2* h(int) const { return r.H; }
+    __device__ __forceinline__ float2* nhat_out(int) const { return nhat; }
+};
+
+struct Members {
+    const FusedMember* m;
+    const float2* tw;
+    int ahead;
+    __device__ __forceinline__ long long step(int k) const { return *m[k].step + ahead; }
+    __device__ __forceinline__ SpecArgs spec(int k) const {
+        SpecArgs a = m[k].spec;
+        a.first = step(k) == 0;
+        return a;
+    }
+    __device__ __forceinline__ float2* planes_s(int k) const { return m[k].S; }
+    __device__ __forceinline__ float2* planes_g(int k) const { return m[k].G; }
+    __device__ __forceinline__ RowArgs rows(int k) const {
+        const FusedMember& f = m[k];
+        const long long lv = step(k) + 1;  // the level this step produces
+        RowArgs r;
+        r.G = f.G;
+        r.H = f.H;
+        r.tw = tw;
+        r.src = f.snap[lv % 2];        // pair (lv-2, lv-1)
+        r.dst = f.snap[(lv + 1) % 2];  // pair (lv-1, lv)
+        r.psi_src = f.psi_plane >= 0 ? f.psi[lv % 2] : nullptr;
+        r.psi_dst = f.psi_plane >= 0 ? f.psi[(lv + 1) % 2] : nullptr;
+        r.psi_plane = f.psi_plane;
+        return r;
+    }
+    __device__ __forceinline__ const float2* h(int k) const { return m[k].H; }
+    __device__ __forceinline__ float2* nhat_out(int k) const { return m[k].nhat; }
+};
+
 // KA: the AB2 update of a 32 x 32 tile of kept modes (rows r0.., columns
 // kx0..), read and written in the row-major state (32 consecutive kx per
 // warp), then each spectral plane of the new omega-hat written transposed,
 // S[p][kx][j], through a shared-memory tile (32 consecutive j per warp).
-// Block: 32 x 8 threads.
-template <int P>
-__global__ void __launch_bounds__(256) k_fused_advance(const __grid_constant__ SpecArgs a,
-                                                       float2* __restrict__ S) {
+// Block: 32 x 8 threads; blockIdx.z: the flow.
+template <int P, class Src>
+__global__ void __launch_bounds__(256) k_fused_advance(const __grid_constant__ Src src) {
+    const auto& a = src.spec(blockIdx.z);
+    float2* __restrict__ S = src.planes_s(blockIdx.z);
     __shared__ float2 tile[kTile][kTile + 1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int kx0 = blockIdx.x * kTile, r0 = blockIdx.y * kTile;
@@ -189,11 +251,12 @@ __global__ void __launch_bounds__(256) k_fused_advance(const __grid_constant__ S
 
 // KB: the inverse transform along y of plane p, column kx (warp p of block
 // kx): S[p][kx][j] for the kept rows (zero elsewhere, never read) into
-// G[p][kx][y].  Block: P warps.
-template <int P>
-__global__ void __launch_bounds__(P * 32) k_fused_columns(const float2* __restrict__ S,
-                                                          const float2* __restrict__ tw,
-                                                          float2* __restrict__ G) {
+// G[p][kx][y].  Block: P warps; blockIdx.y: the flow.
+template <int P, class Src>
+__global__ void __launch_bounds__(P * 32) k_fused_columns(const __grid_constant__ Src src,
+                                                          const float2* __restrict__ tw) {
+    const float2* __restrict__ S = src.planes_s(blockIdx.y);
+    float2* __restrict__ G = src.planes_g(blockIdx.y);
     extern __shared__ float2 sm[];
     float2* tw2 = sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -212,16 +275,6 @@ __global__ void __launch_bounds__(P * 32) k_fused_columns(const float2* __restri
     for (int i = 0; i < 32; i++) G[col + lane + 32 * i] = v[i];
 }
 
-struct RowArgs {
-    const float2* G;        // [P][kFKCP][kFN] planes after the column transforms
-    float2* H;              // [kFKCP][kFN] N after the row transform (kept columns)
-    const float2* tw;       // exp(-2 pi i m / 1024), m < 1024
-    const float4* src;      // level pair (m-2, m-1)
-    float4* dst;            // level pair (m-1, m)
-    const float2* psi_src;  // streamfunction pairs, or nullptr
-    float2* psi_dst;
-    int psi_plane;
-};
 
 constexpr int kRowPitch = kFKCP;  // float2 per staged row of a plane in KC
 
@@ -336,9 +389,10 @@ __device__ __forceinline__ void row_pair(float2 (&v)[32], const float2* __restri
 // transforms along x, two real planes per complex transform, the nonlinear
 // term N = u wx + v wy (Eq. 7), the level pair (and streamfunction pair),
 // and the forward transform of N along x into H[kx][y] (kept columns,
-// written in 32-byte runs through the staging buffer).
-template <int P>
-__global__ void __launch_bounds__(kRowWarps * 32) k_fused_rows(const __grid_constant__ RowArgs r) {
+// written in 32-byte runs through the staging buffer).  blockIdx.y: the flow.
+template <int P, class Src>
+__global__ void __launch_bounds__(kRowWarps * 32) k_fused_rows(const __grid_constant__ Src src) {
+    const auto& r = src.rows(blockIdx.y);
     extern __shared__ float2 sm[];
     float2* tw2 = sm;
     float2* buf = sm + 1024;  // 2 planes x kRowWarps rows x kRowPitch
@@ -406,10 +460,13 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_fused_rows(const __grid_cons
 
 // KD: N-hat of the kept modes of columns kx0 .. kx0 + kNhatWarps - 1 (one per
 // warp) from H (forward transform along y), written to the row-major N-hat
-// in 32-byte runs through a shared-memory staging buffer.
-__global__ void __launch_bounds__(kNhatWarps * 32) k_fused_nhat(const float2* __restrict__ tw,
-                                                               const float2* __restrict__ H,
-                                                               float2* __restrict__ nhat, int nh) {
+// in 32-byte runs through a shared-memory staging buffer.  blockIdx.y: the flow.
+template <class Src>
+__global__ void __launch_bounds__(kNhatWarps * 32) k_fused_nhat(const __grid_constant__ Src src,
+                                                               const float2* __restrict__ tw) {
+    const float2* __restrict__ H = src.h(blockIdx.y);
+    float2* __restrict__ nhat = src.nhat_out(blockIdx.y);
+    constexpr int nh = kFN / 2 + 1;
     extern __shared__ float2 sm[];
     float2* tw2 = sm;
     float2* out = sm + 1024;  // [kFKR][kNhatWarps]
@@ -443,29 +500,48 @@ constexpr size_t kRowSmem =
     (size_t)(1024 + 2 * kRowWarps * kRowPitch + kRowWarps * (kTB + 1024)) * sizeof(float2);
 constexpr size_t kNhatSmem = (size_t)(1024 + kFKR * kNhatWarps + kNhatWarps * kTB) * sizeof(float2);
 
-template <int P>
+template <int P, class Src>
 cudaError_t allow_smem() {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_columns<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_fused_columns<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kColSmem(P));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_fused_rows<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kRowSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fused_nhat<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kNhatSmem);
     return e;
 }
 
-template <int P>
-el_status launch(el_flow* f, const SpecArgs& a, const RowArgs& r, float2* S, float2* G) {
-    const dim3 tiles((kFKC + kTile - 1) / kTile, (kFKR + kTile - 1) / kTile);
-    k_fused_advance<P><<<tiles, 256, 0, f->stream>>>(a, S);
-    EL_LAUNCHED(f);
-    k_fused_columns<P><<<kFKC, P * 32, kColSmem(P), f->stream>>>(S, f->twiddle, G);
-    EL_LAUNCHED(f);
-    k_fused_rows<P><<<kFN / kRowWarps, kRowWarps * 32, kRowSmem, f->stream>>>(r);
-    EL_LAUNCHED(f);
-    k_fused_nhat<<<(kFKC + kNhatWarps - 1) / kNhatWarps, kNhatWarps * 32, kNhatSmem, f->stream>>>(
-        f->twiddle, r.H, f->nhat, f->nh);
-    EL_LAUNCHED(f);
-    return EL_OK;
+template <class Src>
+cudaError_t allow_smem(int planes) {
+    switch (planes) {
+        case 4: return allow_smem<4, Src>();
+        case 5: return allow_smem<5, Src>();
+        case 6: return allow_smem<6, Src>();
+        default: return allow_smem<7, Src>();
+    }
+}
+
+// The four kernels for `count` flows of P planes (the grid's member slice).
+template <int P, class Src>
+void launch(const Src& src, int count, const float2* tw, cudaStream_t st) {
+    const dim3 tiles((kFKC + kTile - 1) / kTile, (kFKR + kTile - 1) / kTile, count);
+    k_fused_advance<P, Src><<<tiles, 256, 0, st>>>(src);
+    k_fused_columns<P, Src><<<dim3(kFKC, count), P * 32, kColSmem(P), st>>>(src, tw);
+    k_fused_rows<P, Src><<<dim3(kFN / kRowWarps, count), kRowWarps * 32, kRowSmem, st>>>(src);
+    k_fused_nhat<Src><<<dim3((kFKC + kNhatWarps - 1) / kNhatWarps, count), kNhatWarps * 32, kNhatSmem, st>>>(
+        src, tw);
+}
+
+template <class Src>
+void launch(int planes, const Src& src, int count, const float2* tw, cudaStream_t st) {
+    switch (planes) {
+        case 4: launch<4>(src, count, tw, st); break;
+        case 5: launch<5>(src, count, tw, st); break;
+        case 6: launch<6>(src, count, tw, st); break;
+        default: launch<7>(src, count, tw, st); break;
+    }
 }
 
 }  // namespace
@@ -481,16 +557,7 @@ bool fused_fluid_supported(const el_flow* f) {
 // Launch attributes (dynamic shared memory above 48 KiB), at flow creation,
 // outside any stream capture.
 el_status fused_fluid_prepare(el_flow* f) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_nhat, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kNhatSmem);
-    if (e == cudaSuccess) {
-        switch (f->nplanes) {
-            case 4: e = allow_smem<4>(); break;
-            case 5: e = allow_smem<5>(); break;
-            case 6: e = allow_smem<6>(); break;
-            default: e = allow_smem<7>(); break;
-        }
-    }
+    const cudaError_t e = allow_smem<OneFlow>(f->nplanes);
     if (e != cudaSuccess) return fail(f, EL_ECUDA, "fused fluid step attributes: %s", cudaGetErrorString(e));
     return EL_OK;
 }
@@ -501,10 +568,13 @@ el_status fluid_step_fused(el_flow* f, const SpecArgs& a, int64_t step) {
     // S (the planes before the column transforms) in the spectral planes'
     // buffer, G (after them) in the physical planes' buffer, H in the
     // nonlinear term's: none of them holds state between steps
-    float2* S = f->spec;
-    float2* G = reinterpret_cast<float2*>(f->phys);
-    RowArgs r{};
-    r.G = G;
+    OneFlow o{};
+    o.a = a;
+    o.S = f->spec;
+    o.G = reinterpret_cast<float2*>(f->phys);
+    o.nhat = f->nhat;
+    RowArgs& r = o.r;
+    r.G = o.G;
     r.H = reinterpret_cast<float2*>(f->nl);
     r.tw = f->twiddle;
     r.src = f->snap[m % 2];        // pair (m-2, m-1): level m-1 in its second half
@@ -512,12 +582,21 @@ el_status fluid_step_fused(el_flow* f, const SpecArgs& a, int64_t step) {
     r.psi_src = f->psi_plane >= 0 ? f->psi[m % 2] : nullptr;
     r.psi_dst = f->psi_plane >= 0 ? f->psi[(m + 1) % 2] : nullptr;
     r.psi_plane = f->psi_plane;
-    switch (f->nplanes) {
-        case 4: return launch<4>(f, a, r, S, G);
-        case 5: return launch<5>(f, a, r, S, G);
-        case 6: return launch<6>(f, a, r, S, G);
-        default: return launch<7>(f, a, r, S, G);
-    }
+    launch(f->nplanes, o, 1, f->twiddle, f->stream);
+    f->launches += 4;
+    EL_CUDA_OK(f, cudaGetLastError());
+    return EL_OK;
+}
+
+// Launch attributes of the batched kernels for `planes`, outside any capture.
+cudaError_t fused_fluid_batch_prepare(int planes) { return allow_smem<Members>(planes); }
+
+cudaError_t fused_fluid_batch(cudaStream_t s, const FusedMember* d_members, int count, int planes,
+                              int ahead, const float2* twiddle) {
+    if (count <= 0) return cudaSuccess;
+    Members src{d_members, twiddle, ahead};
+    launch(planes, src, count, twiddle, s);
+    return cudaGetLastError();
 }
 
 }  // namespace el

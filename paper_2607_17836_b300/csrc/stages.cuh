@@ -50,6 +50,21 @@ struct SpecArgs {
     float scale, dt, nu;
 };
 
+// One batched flow's fused 1024^2 fluid step (fused_fluid.cu), device-resident:
+// everything but what depends on the step number, which the kernels derive
+// from the member's step counter on the device.
+struct FusedMember {
+    SpecArgs spec;            // its `first` is set on the device
+    float2* S;                // planes before the column transforms
+    float2* G;                // after them
+    float2* H;                // N after the row transforms
+    float2* nhat;             // N-hat (read by the AB2 update, then written)
+    float4* snap[2];          // level pairs: snap[k % 2] = levels (k, k+1)
+    float2* psi[2];           // streamfunction pairs, or nullptr
+    const long long* step;    // the member's step counter
+    int psi_plane;
+};
+
 // AB2 update (when ADVANCE) and the spectral velocity / gradient planes of
 // the resulting omega-hat.
 //
@@ -111,10 +126,15 @@ __device__ __forceinline__ float2 advance_loaded(const SpecArgs& a, int i, int j
         inc = make_float2(fmaf(c2, H.x, -c1 * Eh * N.x), fmaf(c2, H.y, -c1 * Eh * N.y));
         hist_out = N;
     } else {
-        float nuk2 = a.nu * (float)(kx * kx + ky * ky);
-        float2 R = make_float2(-N.x - nuk2 * w.x, -N.y - nuk2 * w.y);
-        inc = a.first ? make_float2(dt * R.x, dt * R.y)
-                      : make_float2(dt * (1.5f * R.x - 0.5f * H.x), dt * (1.5f * R.y - 0.5f * H.y));
+        // Eq. 10 with every rounding written out (fmaf where one rounding is
+        // meant, __fmul_rn where a product rounds by itself): nothing is left
+        // for the compiler to contract, so every kernel that inlines this
+        // update (one flow or a batch) rounds it the same way
+        const float nuk2 = __fmul_rn(a.nu, (float)(kx * kx + ky * ky));
+        const float2 R = make_float2(fmaf(-nuk2, w.x, -N.x), fmaf(-nuk2, w.y, -N.y));
+        inc = a.first ? make_float2(__fmul_rn(dt, R.x), __fmul_rn(dt, R.y))
+                      : make_float2(__fmul_rn(dt, fmaf(1.5f, R.x, __fmul_rn(-0.5f, H.x))),
+                                    __fmul_rn(dt, fmaf(1.5f, R.y, __fmul_rn(-0.5f, H.y))));
         hi = w;
         lo = wl;
         hist_out = R;

@@ -113,3 +113,62 @@ def test_autotune_changes_no_result():
     bbest = batch.autotune(trial_steps=4)
     assert bbest["ms_per_step"] > 0
     batch.close()
+
+
+FUSED_CASES = [  # (interp, bspline_prefilter, tracer_velocity, ab2_mode): planes 4, 4, 6, 5, 7
+    (0, 1, 0, 0),
+    (1, 1, 0, 1),
+    (2, 1, 0, 0),
+    (0, 1, 1, 0),
+    (2, 1, 1, 1),
+]
+
+
+def make_fused(case, seed):
+    interp, pre, tv, mode = case
+    g = elpath.Flow(1024, 1e-4, 5e-4, inputs.decaying_turbulence(1024, seed), interp=interp,
+                    bspline_prefilter=pre, tracer_velocity=tv, ab2_mode=mode, max_species=2,
+                    max_particles=6000, sort_every=7)
+    g.set_particles(0, inputs.uniform_positions(3000, seed + 1), 0.0)
+    g.set_particles(1, inputs.uniform_positions(3000, seed + 2), 1.0)
+    return g
+
+
+def test_fused_1024_members_equal_their_solo_runs_bit_for_bit():
+    # 1024^2 members take the fused fluid step in the batch too (one launch of
+    # each fused kernel per plane count, every member in it): the same
+    # kernels' arithmetic as alone, so the same bits, whatever the plane
+    # count, the AB2 form or the step each member joined at (members at odd
+    # and even steps share a launch).  A 256^2 member steps beside them.
+    head = [0, 3, 1, 4, 2]  # steps alone before joining
+    steps = 12
+    refs = []
+    for m, case in enumerate(FUSED_CASES):
+        g = make_fused(case, 40 + 5 * m)
+        g.step(head[m] + steps)
+        refs.append((g.field(0), g.particles(0, 3000)[0], g.particles(1, 3000)))
+        g.close()
+    small = make(SPECS[3], 9)
+    small_ref = make(SPECS[3], 9)
+    small_ref.step(steps)
+    batch = elpath.Batch(8)
+    flows = []
+    for m, case in enumerate(FUSED_CASES):
+        g = make_fused(case, 40 + 5 * m)
+        g.step(head[m])
+        flows.append(g)
+        batch.add(g)
+    batch.add(small)
+    batch.step(steps)
+    for g, (w, p0, (p1, v1)) in zip(flows, refs):
+        np.testing.assert_array_equal(g.field(0), w)
+        np.testing.assert_array_equal(g.particles(0, 3000)[0], p0)
+        q1, u1 = g.particles(1, 3000)
+        np.testing.assert_array_equal(q1, p1)
+        np.testing.assert_array_equal(u1, v1)
+    assert_same(state(small, SPECS[3]), state(small_ref, SPECS[3]))
+    for g in flows + [small]:
+        batch.remove(g)
+        g.close()
+    small_ref.close()
+    batch.close()
