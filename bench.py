@@ -887,6 +887,38 @@ def run_profile_launch(args, wl, scheme):
     g.close()
 
 
+def run_profile_ensemble(args):
+    """A fixed run of the 64-member ensemble for ncu: the batch as the bench
+    builds it (one FFT pool per cuFFT grid size, no autotuning), 3 steps, then
+    2 more.  Its steps run inside the NVTX range el_batch_step, so
+    `ncu --nvtx --nvtx-include "el_batch_step/"` captures only their kernels."""
+    import torch
+    from paper_2607_17836_b300 import elpath
+    wls = inputs.ensemble_members(64)
+    batch = elpath.Batch(64)
+    for n in (256, 512):
+        k = sum(1 for w in wls if w.n == n)
+        if k:
+            batch.add_fft_pool(n, k)
+    flows = []
+    for wl in wls:
+        sp = wl.species[0]
+        g = elpath.Flow(wl.n, wl.nu, wl.dt, wl.omega0(), interp=0, max_species=1,
+                        max_particles=sp.count, sort_every=SORT_EVERY)
+        g.set_particles(0, inputs.uniform_positions(sp.count, sp.seed), sp.st)
+        batch.add(g)
+        flows.append(g)
+    batch.step(3)
+    batch.synchronize()
+    batch.step(2)
+    batch.synchronize()
+    print(json.dumps({"members": len(flows), "steps": 5,
+                      "sizes": {str(n): sum(1 for w in wls if w.n == n) for n in (256, 512, 1024)}}))
+    batch.close()
+    for g in flows:
+        g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -907,8 +939,9 @@ def main():
                     help="arrival rate (requests/s) of the sustained serving run")
     ap.add_argument("--overload-requests", type=int, default=200,
                     help="requests of the served stream run at its configured 20/s")
-    ap.add_argument("--profile-launch", choices=["mix", "16M"], default=None,
-                    help="only a fixed k_rk4 launch for ncu (see run_profile_launch)")
+    ap.add_argument("--profile-launch", choices=["mix", "16M", "ensemble"], default=None,
+                    help="only a fixed k_rk4 launch for ncu (see run_profile_launch), or the "
+                         "64-member ensemble's batched steps (run_profile_ensemble)")
     ap.add_argument("--gather", choices=["auto", "registers", "shared"], default="auto",
                     help="stencil gather of the cubic schemes in --profile-launch")
     args = ap.parse_args()
@@ -923,7 +956,10 @@ def main():
     if args.profile_launch:
         import torch
         torch.cuda.set_device(local)
-        run_profile_launch(args, wl, scheme)
+        if args.profile_launch == "ensemble":
+            run_profile_ensemble(args)
+        else:
+            run_profile_launch(args, wl, scheme)
         return
     try:
         if args.impl == "reference":

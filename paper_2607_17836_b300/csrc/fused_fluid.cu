@@ -1,6 +1,7 @@
-// The pseudospectral step (Sec. 3.1, Eqs. 4-10) on a 1024^2 grid as three
+// The pseudospectral step (Sec. 3.1, Eqs. 4-10) on a 1024^2 grid as four
 // kernels of our own instead of the pointwise kernels around cuFFT's 2-D
-// transforms.  Only the modes the 2/3 rule keeps are ever nonzero (the
+// transforms, for one flow or for every 1024^2 member of a batch at once
+// (the member in the grid's last dimension; OneFlow / Members below).  Only the modes the 2/3 rule keeps are ever nonzero (the
 // initial field is projected, N-hat is masked every step), so every
 // transform is pruned to them: 342 of the 513 columns kx, 683 of the 1024
 // rows ky.
