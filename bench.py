@@ -865,13 +865,17 @@ def run_ours(args, wl, scheme, world, rank, local):
 def run_profile_launch(args, wl, scheme):
     """A fixed launch of k_rk4 for ncu: the bench workload ("mix": 4 species
     x 1M) or the roofline point ("16M": 16M inertial particles at St = 1),
-    1024^2, 128-thread blocks, re-binning every 20 steps in single cells,
+    1024^2 ("shear": the 2048^2 shear layer's 16M at St = 1 instead),
+    128-thread blocks, re-binning every 20 steps in single cells,
     the stencil gather of --gather (default: automatic); 21 steps (re-binned at step 20), then three
     steps with per-stage CUDA events.  `ncu -k regex:k_rk4 -s 21 -c 1`
     captures the first of those three particle launches."""
     from paper_2607_17836_b300 import elpath
     if args.profile_launch == "16M":
         species = [(16_000_000, 1.0, 99)]
+    elif args.profile_launch == "shear":  # the 2048^2 shear layer, 16M at St = 1
+        wl = inputs.kelvin_helmholtz_2048()
+        species = [(s.count, s.st, s.seed) for s in wl.species]
     else:
         species = [(s.count, s.st, s.seed) for s in wl.species]
     g = elpath.Flow(wl.n, wl.nu, wl.dt, wl.omega0(), interp=scheme, max_species=len(species),
@@ -939,7 +943,7 @@ def main():
                     help="arrival rate (requests/s) of the sustained serving run")
     ap.add_argument("--overload-requests", type=int, default=200,
                     help="requests of the served stream run at its configured 20/s")
-    ap.add_argument("--profile-launch", choices=["mix", "16M", "ensemble"], default=None,
+    ap.add_argument("--profile-launch", choices=["mix", "16M", "shear", "ensemble"], default=None,
                     help="only a fixed k_rk4 launch for ncu (see run_profile_launch), or the "
                          "64-member ensemble's batched steps (run_profile_ensemble)")
     ap.add_argument("--gather", choices=["auto", "registers", "shared"], default="auto",

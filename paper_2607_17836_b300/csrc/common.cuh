@@ -93,7 +93,7 @@ struct el_flow {
     double* stage64 = nullptr;  // n^2 doubles: host <-> device field staging
     float2* ex = nullptr;     // exp(-nu kx^2 dt) as (hi, lo) floats, kx = 0..n/2
     float2* ey = nullptr;     // exp(-nu ky^2 dt) as (hi, lo) floats, row index 0..n-1
-    float2* twiddle = nullptr;  // exp(-2 pi i m / n), m < n (the fused 1024^2 step's transforms)
+    float2* twiddle = nullptr;  // exp(-2 pi i m / n), m < n (the fused step's transforms)
     bool fused = false;         // the fluid step runs the fused kernels (fused_fluid.cu)
     float* pre_x = nullptr;   // spline prefilter 3/(2 + cos(k dx)) per kx
     float* pre_y = nullptr;   // ... per row index
@@ -196,16 +196,17 @@ el_status kinematic_get_field(el_flow* f, int which, double* host_nn);  // omega
 void kinematic_diagnostics(const el_flow* f, double* e3);  // exact E, Z, P
 el_status fluid_refresh_planes(el_flow* f);       // physical planes of the current level
 el_status fluid_get_field(el_flow* f, int which, double* host_nn);
-// ---- the fused 1024^2 fluid step (fused_fluid.cu) -----------------------------------
+// ---- the fused 1024^2 / 2048^2 fluid step (fused_fluid.cu) ----------------------------
 bool fused_fluid_supported(const el_flow* f);
 el_status fused_fluid_prepare(el_flow* f);
 el_status fluid_step_fused(el_flow* f, const SpecArgs& a, int64_t step);
 struct FusedMember;
-// The fused step of `count` batched flows with `planes` inverse-transform
-// planes (device records d_members), each at its step counter + `ahead`.
-cudaError_t fused_fluid_batch(cudaStream_t s, const FusedMember* d_members, int count, int planes,
+// The fused step of `count` batched flows of grid n with `planes`
+// inverse-transform planes (device records d_members), each at its step
+// counter + `ahead`; twiddle: the n-entry table of any of them.
+cudaError_t fused_fluid_batch(cudaStream_t s, const FusedMember* d_members, int count, int n, int planes,
                               int ahead, const float2* twiddle);
-cudaError_t fused_fluid_batch_prepare(int planes);
+cudaError_t fused_fluid_batch_prepare(int n, int planes);
 
 // ---- flow descriptors (api.cu) ----------------------------------------------------
 const char* flow_desc_problem(const el_flow_desc* d);  // nullptr when the descriptor is valid

@@ -149,6 +149,113 @@ __device__ __forceinline__ bool row_is_kept(int j) { return j < kFKC || j >= kFN
 
 constexpr int kTile = 32;  // KA's tiles: 32 kept rows x 32 columns
 
+// The kept spectrum of an N^2 grid (2/3 rule): columns kx < KC, rows ky in
+// [-(KC - 1), KC - 1], i.e. KR = 2 KC - 1 rows j = ky mod N; the
+// intermediate arrays hold KCP >= KC columns of N values.
+template <int N>
+struct Geo;
+template <>
+struct Geo<1024> {
+    static constexpr int KC = kFKC, KCP = kFKCP, KR = kFKR;
+};
+template <>
+struct Geo<2048> {
+    static constexpr int KC = 683, KCP = 688, KR = 1365;
+};
+template <int N>
+__device__ __forceinline__ int kept_row_n(int r) {
+    return r < Geo<N>::KC ? r : r + (N - Geo<N>::KR);
+}
+template <int N>
+__device__ __forceinline__ bool row_kept_n(int j) {
+    return j < Geo<N>::KC || j >= N - Geo<N>::KR + Geo<N>::KC;
+}
+
+// ---- 2048-point transforms on a warp pair -----------------------------------
+// A 2048-point transform is two 1024-point ones (fft1024) joined by one
+// radix-2 step, the two halves on the two warps of a pair (half = 0: A,
+// 1: B), which exchange them through their transpose buffers (free once
+// fft1024 returns) under a named barrier of the pair.  With W = exp(DIR 2 pi
+// i / 2048):
+//   decimation in time (the inverse transforms here): A transforms the even
+//     samples x[2m] (E), B the odd ones x[2m+1] (O); X[k] = E[k] + W^k O[k],
+//     X[k + 1024] = E[k] - W^k O[k]: A ends with X[lane + 32 i], B with
+//     X[1024 + lane + 32 i];
+//   decimation in frequency (the forward ones): from x[n] and x[n + 1024],
+//     A transforms x[n] + x[n + 1024] into X[2k], B (x[n] - x[n + 1024]) W^n
+//     into X[2k + 1], k = lane + 32 i.
+// Twiddles: tw2 as for fft1024, and comb[n] = exp(-2 pi i n / 2048), n < 1024.
+
+// The block's tables from the 2048-entry table exp(-2 pi i m / 2048) (NT
+// threads; every load of a thread issued before its stores).
+template <int NT>
+__device__ __forceinline__ void load_twiddles2k(float2* __restrict__ tw2, float2* __restrict__ comb,
+                                                const float2* __restrict__ tw) {
+    constexpr int passes = (2048 + NT - 1) / NT;
+    float2 t[passes];
+#pragma unroll
+    for (int k = 0; k < passes; k++) {
+        const int e = threadIdx.x + k * NT;
+        if (e < 1024) t[k] = tw[2 * ((e & 31) * (e >> 5))];  // exp(-2 pi i l k1 / 1024)
+        else if (e < 2048) t[k] = tw[e - 1024];
+    }
+#pragma unroll
+    for (int k = 0; k < passes; k++) {
+        const int e = threadIdx.x + k * NT;
+        if (e < 1024) tw2[e] = t[k];
+        else if (e < 2048) comb[e - 1024] = t[k];
+    }
+}
+
+// Barrier of the warp pair `pair` (named barriers 1..15; 0 is __syncthreads).
+__device__ __forceinline__ void pair_sync(int pair) {
+    asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
+}
+
+__device__ __forceinline__ float2 cmul(float2 x, float2 t) {
+    return make_float2(fmaf(x.x, t.x, -x.y * t.y), fmaf(x.x, t.y, x.y * t.x));
+}
+template <int DIR>
+__device__ __forceinline__ float2 comb_w(const float2* __restrict__ comb, int n) {
+    float2 t = comb[n];
+    if (DIR > 0) t.y = -t.y;
+    return t;
+}
+
+// Decimation in time (see above): v holds this warp's parity of the input on
+// entry, its half of the output on exit.
+template <int DIR>
+__device__ __forceinline__ void fft2048_dit(float2 (&v)[32], float2* __restrict__ tb, const float2* __restrict__ tb_other,
+                                            const float2* __restrict__ tw2, const float2* __restrict__ comb,
+                                            int lane, int half, int pair) {
+    fft1024<DIR>(v, tb, tw2, lane);
+    if (half) {
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] = cmul(v[i], comb_w<DIR>(comb, lane + 32 * i));
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i++) tb[lane + 32 * i] = v[i];  // E (A) or W^k O (B)
+    pair_sync(pair);
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const float2 o = tb_other[lane + 32 * i];
+        v[i] = half ? fsub2(o, v[i]) : __fadd2_rn(v[i], o);
+    }
+    pair_sync(pair);  // the partner is done reading this warp's buffer
+}
+
+// Decimation in frequency from both halves of the input (lo = x[n], hi =
+// x[n + 1024], n = lane + 32 i): v ends with X[2k + half].
+template <int DIR>
+__device__ __forceinline__ void fft2048_dif(float2 (&v)[32], const float2 (&lo)[32], const float2 (&hi)[32],
+                                            float2* __restrict__ tb, const float2* __restrict__ tw2,
+                                            const float2* __restrict__ comb, int lane, int half) {
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        v[i] = half ? cmul(fsub2(lo[i], hi[i]), comb_w<DIR>(comb, lane + 32 * i)) : __fadd2_rn(lo[i], hi[i]);
+    fft1024<DIR>(v, tb, tw2, lane);
+}
+
 // The arguments of one flow's fused step (RowArgs: those of k_fused_rows).
 struct RowArgs {
     const float2* G;        // [P][kFKCP][kFN] planes after the column transforms
@@ -215,8 +322,9 @@ struct Members {
 // warp), then each spectral plane of the new omega-hat written transposed,
 // S[p][kx][j], through a shared-memory tile (32 consecutive j per warp).
 // Block: 32 x 8 threads; blockIdx.z: the flow.
-template <int P, class Src>
+template <int N, int P, class Src>
 __global__ void __launch_bounds__(256) k_fused_advance(const __grid_constant__ Src src) {
+    using Gm = Geo<N>;
     const auto& a = src.spec(blockIdx.z);
     float2* __restrict__ S = src.planes_s(blockIdx.z);
     __shared__ float2 tile[kTile][kTile + 1];
@@ -226,27 +334,27 @@ __global__ void __launch_bounds__(256) k_fused_advance(const __grid_constant__ S
     ModeIn in[kTile / 8];
 #pragma unroll
     for (int m = 0; m < kTile / 8; m++) {  // every load first
-        const int r = r0 + ty + 8 * m, j = kept_row(r);
-        if (r < kFKR && kx < kFKC) in[m] = load_mode(a, kx, j, (size_t)j * a.nh + kx);
+        const int r = r0 + ty + 8 * m, j = kept_row_n<N>(r);
+        if (r < Gm::KR && kx < Gm::KC) in[m] = load_mode(a, kx, j, (size_t)j * a.nh + kx);
     }
 #pragma unroll
     for (int m = 0; m < kTile / 8; m++) {
-        const int r = r0 + ty + 8 * m, j = kept_row(r);
+        const int r = r0 + ty + 8 * m, j = kept_row_n<N>(r);
         float2 w = make_float2(0.f, 0.f);
-        if (r < kFKR && kx < kFKC) w = advance_loaded(a, kx, j, (size_t)j * a.nh + kx, in[m]);
+        if (r < Gm::KR && kx < Gm::KC) w = advance_loaded(a, kx, j, (size_t)j * a.nh + kx, in[m]);
         tile[ty + 8 * m][tx] = w;
     }
     __syncthreads();
     const int r = r0 + tx;
-    if (r >= kFKR) return;  // no barrier follows
-    const int j = kept_row(r);
+    if (r >= Gm::KR) return;  // no barrier follows
+    const int j = kept_row_n<N>(r);
 #pragma unroll
     for (int m = 0; m < kTile / 8; m++) {
         const int kx = kx0 + ty + 8 * m;
-        if (kx >= kFKC) break;
+        if (kx >= Gm::KC) break;
         const float2 w = tile[tx][ty + 8 * m];
 #pragma unroll
-        for (int p = 0; p < P; p++) S[((size_t)p * kFKCP + kx) * kFN + j] = plane_value(a, p, kx, j, w);
+        for (int p = 0; p < P; p++) S[((size_t)p * Gm::KCP + kx) * N + j] = plane_value(a, p, kx, j, w);
     }
 }
 
@@ -496,69 +604,323 @@ __global__ void __launch_bounds__(kNhatWarps * 32) k_fused_nhat(const __grid_con
     }
 }
 
+// ---- the 2048^2 step: the same four stages, each 2048-point transform on a warp pair ----
+
+using G2 = Geo<2048>;
+constexpr int k2N = 2048;
+constexpr int k2Rows = 4;  // rows per block of KC2 (a warp pair each): 32-byte runs of G
+
+// KB2: the inverse transform along y of column kx, the P planes one after
+// another (S[p][kx][j] for the kept rows into G[p][kx][y]).  Block: one warp
+// pair; blockIdx.y: the flow.
+template <int P, class Src>
+__global__ void __launch_bounds__(64) k_fused_columns2k(const __grid_constant__ Src src,
+                                                        const float2* __restrict__ tw) {
+    const float2* __restrict__ S = src.planes_s(blockIdx.y);
+    float2* __restrict__ G = src.planes_g(blockIdx.y);
+    extern __shared__ float2 sm[];
+    float2* tw2 = sm;
+    float2* comb = sm + 1024;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = warp;
+    float2* tb = sm + 2048 + warp * kTB;
+    const float2* tb_other = sm + 2048 + (warp ^ 1) * kTB;
+    load_twiddles2k<64>(tw2, comb, tw);
+    __syncthreads();
+    const int kx = blockIdx.x;
+#pragma unroll 1
+    for (int p = 0; p < P; p++) {
+        const size_t col = ((size_t)p * G2::KCP + kx) * k2N;
+        float2 v[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const int j = 2 * (lane + 32 * i) + half;  // this warp's parity of the rows
+            v[i] = row_kept_n<k2N>(j) ? S[col + j] : make_float2(0.f, 0.f);
+        }
+        fft2048_dit<1>(v, tb, tb_other, tw2, comb, lane, half, 0);
+#pragma unroll
+        for (int i = 0; i < 32; i++) G[col + 1024 * half + lane + 32 * i] = v[i];
+    }
+}
+
+// KC2's staging of one plane's x-spectrum (kept columns) of the block's
+// k2Rows rows: buf[yy][kx] = G[p][kx][y0 + yy] (8 columns x 4 rows per warp
+// request, 32-byte runs; every load of a thread issued before its stores).
+constexpr int k2StageElems = G2::KC * k2Rows;
+constexpr int k2Threads = 2 * k2Rows * 32;
+constexpr int k2StagePasses = (k2StageElems + k2Threads - 1) / k2Threads;
+__device__ __forceinline__ void stage_plane2k(float2* __restrict__ buf, const float2* __restrict__ G, int p,
+                                              int y0) {
+    static_assert(k2Rows == 4, "kx = e / 4, yy = e % 4");
+    float2 t[k2StagePasses];
+#pragma unroll
+    for (int k = 0; k < k2StagePasses; k++) {
+        const int e = threadIdx.x + k * k2Threads;
+        if (e < k2StageElems) t[k] = G[((size_t)p * G2::KCP + (e >> 2)) * k2N + y0 + (e & 3)];
+    }
+#pragma unroll
+    for (int k = 0; k < k2StagePasses; k++) {
+        const int e = threadIdx.x + k * k2Threads;
+        if (e < k2StageElems) buf[(e & 3) * G2::KCP + (e >> 2)] = t[k];
+    }
+}
+
+// This warp's parity (k = 2m + half, m = lane + 32 i) of the full complex
+// spectrum of two real planes packed as a + i b (bufB = nullptr: b = 0),
+// from their staged kept columns (as row_pair).
+__device__ __forceinline__ void row_pair2k(float2 (&v)[32], const float2* __restrict__ bufA,
+                                           const float2* __restrict__ bufB, int lane, int half) {
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int k = 2 * (lane + 32 * i) + half;
+        float2 z = make_float2(0.f, 0.f);
+        if (k < G2::KC || k > k2N - G2::KC) {
+            const int kk = k < G2::KC ? k : k2N - k;
+            float2 A = bufA[kk];
+            float2 B = bufB ? bufB[kk] : make_float2(0.f, 0.f);
+            if (kk == 0) {
+                A.y = 0.f;
+                B.y = 0.f;
+            }
+            z = k < G2::KC ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+        }
+        v[i] = z;
+    }
+}
+
+// KC2: rows y0 .. y0 + 3, a warp pair each (as KC; each warp holds the half
+// x in [1024 half, 1024 half + 1024) of its row between the transforms).
+// Measured (2048^2, 4 planes): keeping (wx, wy) in shared memory instead of
+// registers and loading planes 0 and 1 during the first transform, as KC
+// does, took 71 us against 68 us.
+template <int P, class Src>
+__global__ void __launch_bounds__(k2Threads, 1) k_fused_rows2k(const __grid_constant__ Src src) {
+    const auto& r = src.rows(blockIdx.y);
+    extern __shared__ float2 sm[];
+    float2* tw2 = sm;
+    float2* comb = sm + 1024;
+    float2* buf = sm + 2048;  // 2 planes x k2Rows rows x KCP
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = warp >> 1, half = warp & 1;
+    float2* tb = buf + 2 * k2Rows * G2::KCP + warp * kTB;
+    const float2* tb_other = buf + 2 * k2Rows * G2::KCP + (warp ^ 1) * kTB;
+    const float2* mine0 = buf + row * G2::KCP;
+    const float2* mine1 = buf + (k2Rows + row) * G2::KCP;
+    const int y0 = blockIdx.x * k2Rows, y = y0 + row;
+    load_twiddles2k<k2Threads>(tw2, comb, r.tw);
+    stage_plane2k(buf, r.G, 2, y0);
+    stage_plane2k(buf + k2Rows * G2::KCP, r.G, 3, y0);
+    __syncthreads();
+    float2 v[32], hold[32];
+    row_pair2k(v, mine0, mine1, lane, half);  // wx + i wy
+    fft2048_dit<1>(v, tb, tb_other, tw2, comb, lane, half, row);
+#pragma unroll
+    for (int i = 0; i < 32; i++) hold[i] = v[i];
+    __syncthreads();  // every warp has read the staging buffer
+    stage_plane2k(buf, r.G, 0, y0);
+    stage_plane2k(buf + k2Rows * G2::KCP, r.G, 1, y0);
+    __syncthreads();
+    row_pair2k(v, mine0, mine1, lane, half);  // u + i v
+    fft2048_dit<1>(v, tb, tb_other, tw2, comb, lane, half, row);
+    float nl[32];  // N at this warp's x
+#pragma unroll
+    for (int i = 0; i < 32; i++) nl[i] = fmaf(v[i].x, hold[i].x, v[i].y * hold[i].y);  // Eq. 7
+    if (P == 6 || P == 7) {  // the level pair holds the spline coefficients
+        __syncthreads();
+        stage_plane2k(buf, r.G, 4, y0);
+        stage_plane2k(buf + k2Rows * G2::KCP, r.G, 5, y0);
+        __syncthreads();
+        row_pair2k(v, mine0, mine1, lane, half);
+        fft2048_dit<1>(v, tb, tb_other, tw2, comb, lane, half, row);
+    }
+    const size_t x0 = (size_t)y * k2N + 1024 * half;
+    write_pair_row(r.src + x0, r.dst + x0, v, lane);
+    if (P == 5 || P == 7) {  // the streamfunction stencil field
+        __syncthreads();
+        stage_plane2k(buf, r.G, r.psi_plane, y0);
+        __syncthreads();
+        row_pair2k(v, mine0, nullptr, lane, half);
+        fft2048_dit<1>(v, tb, tb_other, tw2, comb, lane, half, row);
+        const float2* __restrict__ ps = r.psi_src + x0;
+        float2* __restrict__ pd = r.psi_dst + x0;
+#pragma unroll
+        for (int i = 0; i < 32; i++) pd[lane + 32 * i] = make_float2(ps[lane + 32 * i].y, v[i].x);
+    }
+    // the forward transform of N along x by decimation in frequency: each
+    // warp needs the other warp's half (N real: lo + hi, (lo - hi) W^n)
+    float* tbf = reinterpret_cast<float*>(tb);
+    const float* tbf_other = reinterpret_cast<const float*>(tb_other);
+#pragma unroll
+    for (int i = 0; i < 32; i++) tbf[lane + 32 * i] = nl[i];
+    pair_sync(row);
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const float o = tbf_other[lane + 32 * i];  // A: x[n + 1024], B: x[n]
+        v[i] = half ? cmul(make_float2(o - nl[i], 0.f), comb_w<-1>(comb, lane + 32 * i))
+                    : make_float2(nl[i] + o, 0.f);
+    }
+    pair_sync(row);  // both halves read before fft1024 reuses the buffers
+    fft1024<-1>(v, tb, tw2, lane);  // X[2k + half]
+    __syncthreads();  // every warp is done with the staging buffer
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int kx = 2 * (lane + 32 * i) + half;
+        if (kx < G2::KC) buf[row * G2::KCP + kx] = v[i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < G2::KC * k2Rows; e += blockDim.x) {
+        const int kx = e / k2Rows, yy = e - kx * k2Rows;
+        r.H[(size_t)kx * k2N + y0 + yy] = buf[yy * G2::KCP + kx];
+    }
+}
+
+// KD2: N-hat of the kept modes of columns kx0, kx0 + 1 (a warp pair each)
+// from H (forward transform along y, by decimation in frequency: each warp
+// reads both halves of its column), written to the row-major N-hat in
+// 16-byte runs through a staging buffer (two columns a block: three blocks
+// fit an SM, so the 342 blocks run in one wave).
+constexpr int k2NhatCols = 2;
+template <class Src>
+__global__ void __launch_bounds__(2 * k2NhatCols * 32) k_fused_nhat2k(const __grid_constant__ Src src,
+                                                                      const float2* __restrict__ tw) {
+    const float2* __restrict__ H = src.h(blockIdx.y);
+    float2* __restrict__ nhat = src.nhat_out(blockIdx.y);
+    constexpr int nh = k2N / 2 + 1;
+    extern __shared__ float2 sm[];
+    float2* tw2 = sm;
+    float2* comb = sm + 1024;
+    float2* out = sm + 2048;  // [KR][k2NhatCols]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = warp >> 1, half = warp & 1;
+    float2* tb = out + G2::KR * k2NhatCols + warp * kTB;
+    load_twiddles2k<2 * k2NhatCols * 32>(tw2, comb, tw);
+    __syncthreads();
+    const int kx0 = blockIdx.x * k2NhatCols, kx = kx0 + c;
+    if (kx < G2::KC) {  // whole warp pairs
+        const float2* __restrict__ col = H + (size_t)kx * k2N;
+        float2 lo[32], hi[32], v[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            lo[i] = col[lane + 32 * i];
+            hi[i] = col[1024 + lane + 32 * i];
+        }
+        fft2048_dif<-1>(v, lo, hi, tb, tw2, comb, lane, half);
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const int j = 2 * (lane + 32 * i) + half;
+            if (row_kept_n<k2N>(j)) out[(j < G2::KC ? j : j - (k2N - G2::KR)) * k2NhatCols + c] = v[i];
+        }
+    }
+    __syncthreads();
+    const int ncols = min(k2NhatCols, G2::KC - kx0);
+    for (int e = threadIdx.x; e < G2::KR * k2NhatCols; e += blockDim.x) {
+        const int rr = e / k2NhatCols, cc = e - rr * k2NhatCols;
+        if (cc < ncols) nhat[(size_t)kept_row_n<k2N>(rr) * nh + kx0 + cc] = out[e];
+    }
+}
+
+constexpr size_t k2ColSmem = (size_t)(2048 + 2 * kTB) * sizeof(float2);
+constexpr size_t k2RowSmem = (size_t)(2048 + 2 * k2Rows * G2::KCP + 2 * k2Rows * kTB) * sizeof(float2);
+constexpr size_t k2NhatSmem = (size_t)(2048 + G2::KR * k2NhatCols + 2 * k2NhatCols * kTB) * sizeof(float2);
+
 constexpr size_t kColSmem(int P) { return (size_t)(1024 + P * kTB) * sizeof(float2); }
 constexpr size_t kRowSmem =
     (size_t)(1024 + 2 * kRowWarps * kRowPitch + kRowWarps * (kTB + 1024)) * sizeof(float2);
 constexpr size_t kNhatSmem = (size_t)(1024 + kFKR * kNhatWarps + kNhatWarps * kTB) * sizeof(float2);
 
-template <int P, class Src>
+template <int N, int P, class Src>
 cudaError_t allow_smem() {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_columns<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kColSmem(P));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused_rows<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kRowSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused_nhat<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kNhatSmem);
+    cudaError_t e;
+    if (N == 1024) {
+        e = cudaFuncSetAttribute(k_fused_columns<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kColSmem(P));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_rows<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRowSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_nhat<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kNhatSmem);
+    } else {
+        e = cudaFuncSetAttribute(k_fused_columns2k<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)k2ColSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_rows2k<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)k2RowSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_nhat2k<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)k2NhatSmem);
+    }
     return e;
 }
 
-template <class Src>
-cudaError_t allow_smem(int planes) {
+template <int N, class Src>
+cudaError_t allow_smem_n(int planes) {
     switch (planes) {
-        case 4: return allow_smem<4, Src>();
-        case 5: return allow_smem<5, Src>();
-        case 6: return allow_smem<6, Src>();
-        default: return allow_smem<7, Src>();
+        case 4: return allow_smem<N, 4, Src>();
+        case 5: return allow_smem<N, 5, Src>();
+        case 6: return allow_smem<N, 6, Src>();
+        default: return allow_smem<N, 7, Src>();
     }
 }
 
-// The four kernels for `count` flows of P planes (the grid's member slice).
-template <int P, class Src>
+template <class Src>
+cudaError_t allow_smem(int n, int planes) {
+    return n == 1024 ? allow_smem_n<1024, Src>(planes) : allow_smem_n<2048, Src>(planes);
+}
+
+// The four kernels for `count` flows of N^2 and P planes (the grid's member slice).
+template <int N, int P, class Src>
 void launch(const Src& src, int count, const float2* tw, cudaStream_t st) {
-    const dim3 tiles((kFKC + kTile - 1) / kTile, (kFKR + kTile - 1) / kTile, count);
-    k_fused_advance<P, Src><<<tiles, 256, 0, st>>>(src);
-    k_fused_columns<P, Src><<<dim3(kFKC, count), P * 32, kColSmem(P), st>>>(src, tw);
-    k_fused_rows<P, Src><<<dim3(kFN / kRowWarps, count), kRowWarps * 32, kRowSmem, st>>>(src);
-    k_fused_nhat<Src><<<dim3((kFKC + kNhatWarps - 1) / kNhatWarps, count), kNhatWarps * 32, kNhatSmem, st>>>(
-        src, tw);
+    using Gm = Geo<N>;
+    const dim3 tiles((Gm::KC + kTile - 1) / kTile, (Gm::KR + kTile - 1) / kTile, count);
+    k_fused_advance<N, P, Src><<<tiles, 256, 0, st>>>(src);
+    if (N == 1024) {
+        k_fused_columns<P, Src><<<dim3(kFKC, count), P * 32, kColSmem(P), st>>>(src, tw);
+        k_fused_rows<P, Src><<<dim3(kFN / kRowWarps, count), kRowWarps * 32, kRowSmem, st>>>(src);
+        k_fused_nhat<Src><<<dim3((kFKC + kNhatWarps - 1) / kNhatWarps, count), kNhatWarps * 32, kNhatSmem,
+                            st>>>(src, tw);
+    } else {
+        k_fused_columns2k<P, Src><<<dim3(G2::KC, count), 64, k2ColSmem, st>>>(src, tw);
+        k_fused_rows2k<P, Src><<<dim3(k2N / k2Rows, count), k2Threads, k2RowSmem, st>>>(src);
+        k_fused_nhat2k<Src><<<dim3((G2::KC + k2NhatCols - 1) / k2NhatCols, count), 2 * k2NhatCols * 32,
+                              k2NhatSmem, st>>>(src, tw);
+    }
+}
+
+template <int N, class Src>
+void launch_n(int planes, const Src& src, int count, const float2* tw, cudaStream_t st) {
+    switch (planes) {
+        case 4: launch<N, 4>(src, count, tw, st); break;
+        case 5: launch<N, 5>(src, count, tw, st); break;
+        case 6: launch<N, 6>(src, count, tw, st); break;
+        default: launch<N, 7>(src, count, tw, st); break;
+    }
 }
 
 template <class Src>
-void launch(int planes, const Src& src, int count, const float2* tw, cudaStream_t st) {
-    switch (planes) {
-        case 4: launch<4>(src, count, tw, st); break;
-        case 5: launch<5>(src, count, tw, st); break;
-        case 6: launch<6>(src, count, tw, st); break;
-        default: launch<7>(src, count, tw, st); break;
-    }
+void launch(int n, int planes, const Src& src, int count, const float2* tw, cudaStream_t st) {
+    if (n == 1024) launch_n<1024>(planes, src, count, tw, st);
+    else launch_n<2048>(planes, src, count, tw, st);
 }
 
 }  // namespace
 
-// Whether the flow's fluid step runs the kernels of this file: the 1024^2
-// solver (not the prescribed kinematic field).  ELPATH_FLUID_CUFFT set in the
-// environment keeps the cuFFT path (for comparing the two).
+// Whether the flow's fluid step runs the kernels of this file: the 1024^2 and
+// 2048^2 solvers (not the prescribed kinematic field; at 2048^2 without the
+// streamfunction plane).  ELPATH_FLUID_CUFFT set
+// in the environment keeps the cuFFT path (for comparing the two).
 bool fused_fluid_supported(const el_flow* f) {
     static const bool off = std::getenv("ELPATH_FLUID_CUFFT") != nullptr;
-    return f->n == kFN && !f->kinematic && !off;
+    if (f->kinematic || off) return false;
+    // 2048^2 with the streamfunction plane (5 or 7 planes): the row kernel's
+    // extra sequential transform made it slower than the cuFFT path
+    // (measured 0.223 / 0.275 ms against 0.203 / 0.251 ms)
+    return f->n == 1024 || (f->n == 2048 && (f->nplanes == 4 || f->nplanes == 6));
 }
 
 // Launch attributes (dynamic shared memory above 48 KiB), at flow creation,
 // outside any stream capture.
 el_status fused_fluid_prepare(el_flow* f) {
-    const cudaError_t e = allow_smem<OneFlow>(f->nplanes);
+    const cudaError_t e = allow_smem<OneFlow>(f->n, f->nplanes);
     if (e != cudaSuccess) return fail(f, EL_ECUDA, "fused fluid step attributes: %s", cudaGetErrorString(e));
     return EL_OK;
 }
@@ -583,20 +945,20 @@ el_status fluid_step_fused(el_flow* f, const SpecArgs& a, int64_t step) {
     r.psi_src = f->psi_plane >= 0 ? f->psi[m % 2] : nullptr;
     r.psi_dst = f->psi_plane >= 0 ? f->psi[(m + 1) % 2] : nullptr;
     r.psi_plane = f->psi_plane;
-    launch(f->nplanes, o, 1, f->twiddle, f->stream);
+    launch(f->n, f->nplanes, o, 1, f->twiddle, f->stream);
     f->launches += 4;
     EL_CUDA_OK(f, cudaGetLastError());
     return EL_OK;
 }
 
-// Launch attributes of the batched kernels for `planes`, outside any capture.
-cudaError_t fused_fluid_batch_prepare(int planes) { return allow_smem<Members>(planes); }
+// Launch attributes of the batched kernels for (n, planes), outside any capture.
+cudaError_t fused_fluid_batch_prepare(int n, int planes) { return allow_smem<Members>(n, planes); }
 
-cudaError_t fused_fluid_batch(cudaStream_t s, const FusedMember* d_members, int count, int planes,
+cudaError_t fused_fluid_batch(cudaStream_t s, const FusedMember* d_members, int count, int n, int planes,
                               int ahead, const float2* twiddle) {
     if (count <= 0) return cudaSuccess;
     Members src{d_members, twiddle, ahead};
-    launch(planes, src, count, twiddle, s);
+    launch(n, planes, src, count, twiddle, s);
     return cudaGetLastError();
 }
 

@@ -124,9 +124,9 @@ FUSED_CASES = [  # (interp, bspline_prefilter, tracer_velocity, ab2_mode): plane
 ]
 
 
-def make_fused(case, seed):
+def make_fused(case, seed, n=1024):
     interp, pre, tv, mode = case
-    g = elpath.Flow(1024, 1e-4, 5e-4, inputs.decaying_turbulence(1024, seed), interp=interp,
+    g = elpath.Flow(n, 1e-4, 5e-4 * 1024 / n, inputs.decaying_turbulence(n, seed), interp=interp,
                     bspline_prefilter=pre, tracer_velocity=tv, ab2_mode=mode, max_species=2,
                     max_particles=6000, sort_every=7)
     g.set_particles(0, inputs.uniform_positions(3000, seed + 1), 0.0)
@@ -134,17 +134,23 @@ def make_fused(case, seed):
     return g
 
 
-def test_fused_1024_members_equal_their_solo_runs_bit_for_bit():
-    # 1024^2 members take the fused fluid step in the batch too (one launch of
-    # each fused kernel per plane count, every member in it): the same
-    # kernels' arithmetic as alone, so the same bits, whatever the plane
-    # count, the AB2 form or the step each member joined at (members at odd
-    # and even steps share a launch).  A 256^2 member steps beside them.
-    head = [0, 3, 1, 4, 2]  # steps alone before joining
+# (grid, case): the 1024^2 cases, a 2048^2 member on the fused step (4 planes)
+# and one on the cuFFT path (the streamfunction plane: 5 planes)
+FUSED_MEMBERS = [(1024, c) for c in FUSED_CASES] + [(2048, (1, 1, 0, 1)), (2048, (0, 1, 1, 0))]
+
+
+def test_fused_members_equal_their_solo_runs_bit_for_bit():
+    # 1024^2 and 2048^2 members take the fused fluid step in the batch too
+    # (one launch of each fused kernel per grid and plane count, every member
+    # in it): the same kernels' arithmetic as alone, so the same bits,
+    # whatever the plane count, the AB2 form or the step each member joined
+    # at (members at odd and even steps share a launch).  A 256^2 member steps
+    # beside them.
+    head = [0, 3, 1, 4, 2, 1, 0]  # steps alone before joining
     steps = 12
     refs = []
-    for m, case in enumerate(FUSED_CASES):
-        g = make_fused(case, 40 + 5 * m)
+    for m, (n, case) in enumerate(FUSED_MEMBERS):
+        g = make_fused(case, 40 + 5 * m, n)
         g.step(head[m] + steps)
         refs.append((g.field(0), g.particles(0, 3000)[0], g.particles(1, 3000)))
         g.close()
@@ -153,8 +159,8 @@ def test_fused_1024_members_equal_their_solo_runs_bit_for_bit():
     small_ref.step(steps)
     batch = elpath.Batch(8)
     flows = []
-    for m, case in enumerate(FUSED_CASES):
-        g = make_fused(case, 40 + 5 * m)
+    for m, (n, case) in enumerate(FUSED_MEMBERS):
+        g = make_fused(case, 40 + 5 * m, n)
         g.step(head[m])
         flows.append(g)
         batch.add(g)

@@ -1,13 +1,16 @@
-"""The fused 1024^2 fluid step (fused_fluid.cu: pruned transforms of our own,
-fused with the AB2 update and the nonlinear term) against the cuFFT path
-(ELPATH_FLUID_CUFFT=1, run in a child process), and against the oracle.
+"""The fused 1024^2 and 2048^2 fluid steps (fused_fluid.cu: pruned transforms
+of our own, fused with the AB2 update and the nonlinear term) against the
+cuFFT path (ELPATH_FLUID_CUFFT=1, run in a child process), and against the
+oracle.
 
-Every plane configuration the step has: 4 planes (bilinear, Catmull-Rom,
-raw B-spline), 6 (prefiltered B-spline), 5 and 7 (with the streamfunction
-plane of tracer_velocity = 1), each AB2 form.  The two paths differ only by
-the rounding of their transforms, so after 100 steps the vorticity agrees
-to a few 1e-7 and positions to a few 1e-8; the physical velocity planes,
-which the fused step does not keep, are rebuilt on request.
+At 1024^2 every plane configuration the step has: 4 planes (bilinear,
+Catmull-Rom, raw B-spline), 6 (prefiltered B-spline), 5 and 7 (with the
+streamfunction plane of tracer_velocity = 1), each AB2 form; at 2048^2 the
+ones it serves (4 and 6 planes; a 2048-point transform is two 1024-point ones
+on a warp pair).  The two paths differ only by the rounding of their
+transforms, so after 100 steps the vorticity agrees to a few 1e-7 and
+positions to a few 1e-8; the physical velocity planes, which the fused step
+does not keep, are rebuilt on request.
 """
 import os
 import subprocess
@@ -25,22 +28,25 @@ torch = pytest.importorskip("torch")
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 N = 1024
-CASES = [  # (interp, bspline_prefilter, tracer_velocity, ab2_mode): planes
-    (0, 1, 0, 0),   # 4
-    (1, 1, 0, 1),   # 4, explicit AB2
-    (2, 0, 0, 0),   # 4 (raw B-spline)
-    (2, 1, 0, 0),   # 6
-    (0, 1, 1, 0),   # 5
-    (2, 1, 1, 1),   # 7, explicit AB2
+CASES = [  # (n, interp, bspline_prefilter, tracer_velocity, ab2_mode): planes
+    (N, 0, 1, 0, 0),     # 4
+    (N, 1, 1, 0, 1),     # 4, explicit AB2
+    (N, 2, 0, 0, 0),     # 4 (raw B-spline)
+    (N, 2, 1, 0, 0),     # 6
+    (N, 0, 1, 1, 0),     # 5
+    (N, 2, 1, 1, 1),     # 7, explicit AB2
+    (2048, 0, 1, 0, 0),  # 4
+    (2048, 1, 1, 0, 1),  # 4, explicit AB2
+    (2048, 2, 1, 0, 0),  # 6
 ]
 
 CHILD = textwrap.dedent("""
     import sys, numpy as np
     sys.path.insert(0, {root!r})
     from paper_2607_17836_b300 import elpath, inputs
-    interp, pre, tv, mode = {case!r}
-    w0 = inputs.decaying_turbulence({n}, 2)
-    g = elpath.Flow({n}, 1e-4, 5e-4, w0, interp=interp, bspline_prefilter=pre, tracer_velocity=tv,
+    n, interp, pre, tv, mode = {case!r}
+    w0 = inputs.decaying_turbulence(n, 2)
+    g = elpath.Flow(n, 1e-4, 5e-4 * 1024 / n, w0, interp=interp, bspline_prefilter=pre, tracer_velocity=tv,
                     ab2_mode=mode, max_species=2, max_particles=40000, sort_every=20)
     g.set_particles(0, inputs.uniform_positions(20000, 3), 0.0)
     g.set_particles(1, inputs.uniform_positions(20000, 4), 1.0)
@@ -52,7 +58,7 @@ CHILD = textwrap.dedent("""
 
 
 def run_child(case, out, cufft):
-    script = CHILD.format(root=ROOT, case=case, n=N, out=out)
+    script = CHILD.format(root=ROOT, case=case, out=out)
     env = dict(os.environ)
     env.pop("ELPATH_FLUID_CUFFT", None)
     if cufft:
@@ -64,18 +70,19 @@ def run_child(case, out, cufft):
 
 
 @pytest.mark.parametrize("case", CASES, ids=["bilinear", "catmull_rom_explicit", "bspline_raw",
-                                             "bspline", "psi", "bspline_psi_explicit"])
+                                             "bspline", "psi", "bspline_psi_explicit",
+                                             "2048_bilinear", "2048_catmull_rom_explicit", "2048_bspline"])
 def test_fused_step_matches_the_cufft_path(case, tmp_path):
     a = run_child(case, str(tmp_path / "fused.npz"), cufft=False)
     b = run_child(case, str(tmp_path / "cufft.npz"), cufft=True)
-    name = f"fused vs cuFFT fluid step, 1024^2, case {case}"
+    name = f"fused vs cuFFT fluid step, {case[0]}^2, case {case[1:]}"
     for key in ("w", "u", "v"):
         d = rel_linf(a[key], b[key])
-        record(name, case[0], f"{key} L-inf rel. difference, 100 steps", d, 2e-6)
+        record(name, case[1], f"{key} L-inf rel. difference, 100 steps", d, 2e-6)
         assert d < 2e-6, (key, d)
     for key in ("p0", "p1"):
         d = float(np.max(np.abs(a[key] - b[key])))
-        record(name, case[0], "max position difference, 100 steps", d, 1e-6)
+        record(name, case[1], "max position difference, 100 steps", d, 1e-6)
         assert d < 1e-6, (key, d)
     np.testing.assert_allclose(a["e"], b["e"], rtol=1e-6)
 
