@@ -474,12 +474,13 @@ def run_ensemble(args, dev, members=64, steps=20):
     bat_ms = ev[2].elapsed_time(ev[3])
     launches = (batch.kernel_launches() - launches0) / steps
     batch.close()
-    # the same members in a batch with one FFT pool per cuFFT grid size (each
-    # member's transforms batched with the others of its size; the 1024^2
-    # members run the fused step, every one of them in the same launches)
+    # the same members in a batch with one FFT pool per grid size of the
+    # members on cuFFT transforms (each member's transforms batched with the
+    # others of its size; the fused members share the fused kernels' launches)
     sizes = {n: sum(1 for w in wls if w.n == n) for n in (256, 512, 1024)}
+    cufft_sizes = {n: sum(1 for w, g in zip(wls, flows) if w.n == n and not g.fused) for n in sizes}
     pooled = elpath.Batch(members, device=dev)
-    pool_bytes = sum(pooled.add_fft_pool(n, c) for n, c in sizes.items() if c > 0 and n != 1024)
+    pool_bytes = sum(pooled.add_fft_pool(n, c) for n, c in cufft_sizes.items() if c > 0)
     for g in flows:
         pooled.add(g)
     pooled.step(3)
@@ -516,7 +517,7 @@ def run_serving(dev, count=200, rate=20.0, budget_gb=120.0, timeout=None):
     import torch
     from paper_2607_17836_b300 import serve
     reqs = inputs.served_requests(count=count)
-    pools = {128: 4, 256: 4, 512: 4, 2048: 2}   # FFT-pool slots per cuFFT grid size (1024^2: fused)
+    pools = {128: 4}   # FFT-pool slots per grid size whose bilinear / Catmull-Rom flows use cuFFT
     srv = serve.Server(hbm_budget=int(budget_gb * 2**30), max_members=64, tick_steps=50,
                        device=dev, fft_pool_slots=pools)
     t0 = time.perf_counter()
@@ -549,7 +550,7 @@ def run_serving_vs_sequential(dev, count=32, budget_gb=120.0):
     from paper_2607_17836_b300 import serve
     reqs = inputs.served_requests(count=count)
     work = sum(r.workload.particles * r.workload.steps for r in reqs)
-    pools = {128: 4, 256: 4, 512: 4, 2048: 2}
+    pools = {128: 4}
     srv = serve.Server(hbm_budget=int(budget_gb * 2**30), max_members=64, tick_steps=50,
                        device=dev, fft_pool_slots=pools)
     torch.cuda.synchronize(dev)

@@ -232,6 +232,12 @@ el_status el_autotune(el_flow* flow, int32_t trial_steps, el_tuning* best);
  * this flow; lets a caller count the launches inside a timed region. */
 int64_t el_kernel_launches(const el_flow* flow);
 
+/* 1 if the flow's fluid step (Secs. 3.1, Eqs. 4-10) runs the library's fused
+ * transforms (256^2 and 512^2 with 4 or 6 inverse-transform planes, 1024^2,
+ * 2048^2 with 4 or 6), 0 if it runs cuFFT's, or for a NULL flow.  A fused
+ * flow takes no FFT-pool slot in a batch (see el_batch_add_fft_pool). */
+int32_t el_flow_fused(const el_flow* flow);
+
 /* ---- Batched engine --------------------------------------------------------
  * Many independent flows (any grid sizes, species mixes, schemes and step
  * counts) advanced together: one coupled step of the batch is one captured
@@ -271,7 +277,9 @@ el_status el_batch_destroy(el_batch* batch);
  * bytes, 256-byte aligned (0: invalid desc or slots outside [1, 4096]).
  * A flow added with el_batch_add after the pool takes a free slot of a pool
  * of its class if there is one, the lowest free one (else it transforms
- * alone, as before); it keeps the slot until it leaves.  The batched calls
+ * alone, as before); it keeps the slot until it leaves.  Flows whose fluid
+ * step is fused (el_flow_fused) take no slot: the batch runs their transforms
+ * as one launch of each fused kernel for all members of their grid.  The batched calls
  * cover slots 0 .. the highest occupied one.  The results equal the per-member path's up
  * to the rounding of cuFFT's batched kernels.  EL_ENOMEM when `bytes` is too
  * small; EL_ECUFFT when the plans cannot be made. */

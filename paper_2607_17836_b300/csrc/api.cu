@@ -714,6 +714,8 @@ el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
 
 int64_t el_kernel_launches(const el_flow* f) { return f ? f->launches : 0; }
 
+int32_t el_flow_fused(const el_flow* f) { return f && f->fused ? 1 : 0; }
+
 el_status el_get_tuning(const el_flow* f, el_tuning* out) {
     if (!f || !out) return EL_EINVAL;
     out->rk4_threads = f->rk4_threads;

@@ -12,7 +12,7 @@
 //                     one launch per interpolation scheme present
 //   k_batch_advance                                        per-member step counters
 //
-// Members on the 1024^2 and 2048^2 grids whose fluid step is the fused one (fused_fluid.cu)
+// Members whose fluid step is the fused one (fused_fluid.cu)
 // take no part in the spectral, cuFFT and nonlinear stages: the fused
 // kernels advance all of them at once (one launch of each of the four per
 // plane count present, the member in the grid's last dimension).
@@ -206,9 +206,12 @@ struct el_batch {
     std::vector<MemberDev> h_members;
     std::vector<int> h_spec_begin, h_nl_begin, h_rk_begin, h_rk_member;
     std::vector<const SpeciesDev*> h_rk_sp;
-    std::vector<FusedMember> h_fused;  // grouped by (grid 1024^2 / 2048^2, plane count 4..7)
-    int fused_begin[9] = {};           // records of class c = 4 g + planes - 4: [fused_begin[c], fused_begin[c + 1])
-    const float2* fused_twiddle[2] = {nullptr, nullptr};  // the n-entry table of a member of each grid
+    // fused members' records, grouped by class c = 4 g + planes - 4 with g the
+    // grid (n = 128 << g, g < kFusedGrids): records [fused_begin[c], fused_begin[c + 1])
+    static constexpr int kFusedGrids = 5;
+    std::vector<FusedMember> h_fused;
+    int fused_begin[4 * kFusedGrids + 1] = {};
+    const float2* fused_twiddle[kFusedGrids] = {};  // the n-entry table of a member of each grid
     BatchArgs args{};
     int grid_spec = 0, grid_nl = 0, grid_rk[3] = {0, 0, 0};
     bool scheme_used[3] = {false, false, false};
@@ -326,9 +329,9 @@ el_status rebuild_tables(el_batch* b) {
     }
     // the fused members' records, grouped by grid and plane count
     b->h_fused.clear();
-    b->fused_twiddle[0] = b->fused_twiddle[1] = nullptr;
-    for (int c = 0; c < 8; c++) {
-        const int n = c < 4 ? 1024 : 2048, planes = 4 + (c & 3);
+    for (int g = 0; g < el_batch::kFusedGrids; g++) b->fused_twiddle[g] = nullptr;
+    for (int c = 0; c < 4 * el_batch::kFusedGrids; c++) {
+        const int n = 128 << (c / 4), planes = 4 + (c & 3);
         b->fused_begin[c] = (int)b->h_fused.size();
         for (int m = 0; m < M; m++) {
             el_flow* f = b->members[m];
@@ -351,7 +354,7 @@ el_status rebuild_tables(el_batch* b) {
         if (b->h_fused.size() > (size_t)b->fused_begin[c])
             BT_CUDA(b, fused_fluid_batch_prepare(n, planes));
     }
-    b->fused_begin[8] = (int)b->h_fused.size();
+    b->fused_begin[4 * el_batch::kFusedGrids] = (int)b->h_fused.size();
     for (int m = 0; m < M; m++) {
         el_flow* f = b->members[m];
         if (f->rk4_threads != rk_threads)
@@ -466,10 +469,10 @@ el_status fork_ffts(el_batch* b, cudaStream_t origin, bool c2r) {
 // pair, R2C.
 el_status enqueue_fluid(el_batch* b, cudaStream_t s, int ahead) {
     const BatchArgs& a = b->args;
-    for (int c = 0; c < 8; c++) {
+    for (int c = 0; c < 4 * el_batch::kFusedGrids; c++) {
         const int count = b->fused_begin[c + 1] - b->fused_begin[c];
         if (count == 0) continue;
-        BT_CUDA(b, fused_fluid_batch(s, b->d_fused + b->fused_begin[c], count, c < 4 ? 1024 : 2048,
+        BT_CUDA(b, fused_fluid_batch(s, b->d_fused + b->fused_begin[c], count, 128 << (c / 4),
                                      4 + (c & 3), ahead, b->fused_twiddle[c / 4]));
         b->launches += 4;
     }

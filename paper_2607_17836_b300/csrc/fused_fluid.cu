@@ -1,12 +1,14 @@
-// The pseudospectral step (Sec. 3.1, Eqs. 4-10) on a 1024^2 grid as four
-// kernels of our own instead of the pointwise kernels around cuFFT's 2-D
-// transforms, for one flow or for every 1024^2 member of a batch at once
-// (the member in the grid's last dimension; OneFlow / Members below).  Only the modes the 2/3 rule keeps are ever nonzero (the
-// initial field is projected, N-hat is masked every step), so every
-// transform is pruned to them: 342 of the 513 columns kx, 683 of the 1024
-// rows ky.
+// The pseudospectral step (Sec. 3.1, Eqs. 4-10) as four kernels of our own
+// instead of the pointwise kernels around cuFFT's 2-D transforms, for one
+// flow or for every member of a batch on the same grid at once (the member in
+// the grid's last dimension; OneFlow / Members below).  The kernels below are
+// written out for 1024^2 (one warp per 1024-point transform); 2048^2 runs
+// each 2048-point transform on a warp pair, 256^2 and 512^2 on lane groups.
+// Only the modes the 2/3 rule keeps are ever nonzero (the initial field is
+// projected, N-hat is masked every step), so every transform is pruned to
+// them: at 1024^2, 342 of the 513 columns kx and 683 of the 1024 rows ky.
 //
-//   k_fused_advance<P> : the AB2 update of the kept modes (advance_mode) in
+//   k_fused_advance    : the AB2 update of the kept modes (advance_mode) in
 //                        32 x 32 tiles, and every spectral plane of the new
 //                        omega-hat (plane_value) written transposed, S[p][kx][j]
 //   k_fused_columns<P> : one warp per plane and kept column: the inverse
@@ -37,6 +39,7 @@
 #include "stages.cuh"
 
 #include <cstdlib>
+
 
 namespace el {
 namespace {
@@ -123,6 +126,88 @@ __device__ __forceinline__ void fft1024(float2 (&v)[32], float2* __restrict__ tb
     dft32<DIR>(v);
 }
 
+// v[k] <- sum_n v[n] exp(DIR 2 pi i n k / L) for L in {2, 4, 8, 16}, in
+// registers (radix-2, decimation in frequency, as dft32).
+template <int L>
+__host__ __device__ constexpr int bitrev_l(int k) {
+    int r = 0;
+    for (int b = 1, t = L >> 1; b < L; b <<= 1, t >>= 1)
+        if (k & b) r |= t;
+    return r;
+}
+template <int DIR, int L>
+__device__ __forceinline__ void dftL(float2 (&v)[L]) {
+#pragma unroll
+    for (int M = L; M >= 2; M >>= 1) {
+#pragma unroll
+        for (int g = 0; g < L; g += M) {
+#pragma unroll
+            for (int j = 0; j < M / 2; j++) {
+                const float2 a = v[g + j], b = v[g + j + M / 2];
+                v[g + j] = __fadd2_rn(a, b);
+                v[g + j + M / 2] = rot32<DIR>(fsub2(a, b), j * (32 / M));
+            }
+        }
+    }
+    float2 t[L];
+#pragma unroll
+    for (int k = 0; k < L; k++) t[k] = v[bitrev_l<L>(k)];
+#pragma unroll
+    for (int k = 0; k < L; k++) v[k] = t[k];
+}
+
+// The N = 32 M-point transform (M in {4, 8, 16}) held by a group of M lanes
+// (gl = lane % M; a warp holds 32 / M groups), 32 values per lane: lane gl
+// holds x[gl + M i] in register i on entry and X[gl + M i] on exit.  A
+// 32-point DFT over each lane's registers, the twiddles exp(DIR 2 pi i gl k1
+// / N) from the block's table twg[k1 M + gl], a transpose through the
+// group's buffer tbg (32 rows of M + 1), and 32 / M DFTs of M points over the
+// group's lanes (fft1024 is the case M = 32).
+template <int DIR, int M>
+__device__ __forceinline__ void fft_group(float2 (&v)[32], float2* __restrict__ tbg,
+                                          const float2* __restrict__ twg, int gl) {
+    dft32<DIR>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 32; k1++) {
+        float2 t = twg[k1 * M + gl];
+        if (DIR > 0) t.y = -t.y;
+        const float2 x = v[k1];
+        v[k1] = make_float2(fmaf(x.x, t.x, -x.y * t.y), fmaf(x.x, t.y, x.y * t.x));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 32; k1++) tbg[k1 * (M + 1) + gl] = v[k1];
+    __syncwarp();
+    constexpr int J = 32 / M;
+#pragma unroll
+    for (int j = 0; j < J; j++) {
+        float2 w[M];
+#pragma unroll
+        for (int l = 0; l < M; l++) w[l] = tbg[(gl + M * j) * (M + 1) + l];
+        dftL<DIR, M>(w);
+#pragma unroll
+        for (int k2 = 0; k2 < M; k2++) v[j + J * k2] = w[k2];  // X[gl + M j + 32 k2]
+    }
+    __syncwarp();
+}
+
+// The block's table for fft_group from the N-entry table exp(-2 pi i m / N):
+// twg[k1 M + gl] = exp(-2 pi i gl k1 / N) (NT threads).
+template <int M, int NT>
+__device__ __forceinline__ void load_twiddles_group(float2* __restrict__ twg, const float2* __restrict__ tw) {
+    constexpr int E = 32 * M, passes = (E + NT - 1) / NT;
+    float2 t[passes];
+#pragma unroll
+    for (int k = 0; k < passes; k++) {
+        const int e = threadIdx.x + k * NT;
+        if (e < E) t[k] = tw[(e % M) * (e / M)];
+    }
+#pragma unroll
+    for (int k = 0; k < passes; k++) {
+        const int e = threadIdx.x + k * NT;
+        if (e < E) twg[e] = t[k];
+    }
+}
+
 // The block's twiddle table from the 1024-entry table exp(-2 pi i m / 1024)
 // (NT threads; every load of a thread issued before its stores).
 template <int NT>
@@ -161,6 +246,18 @@ struct Geo<1024> {
 template <>
 struct Geo<2048> {
     static constexpr int KC = 683, KCP = 688, KR = 1365;
+};
+template <>
+struct Geo<128> {
+    static constexpr int KC = 43, KCP = 48, KR = 85;
+};
+template <>
+struct Geo<256> {
+    static constexpr int KC = 86, KCP = 88, KR = 171;
+};
+template <>
+struct Geo<512> {
+    static constexpr int KC = 171, KCP = 176, KR = 341;
 };
 template <int N>
 __device__ __forceinline__ int kept_row_n(int r) {
@@ -822,6 +919,234 @@ constexpr size_t k2ColSmem = (size_t)(2048 + 2 * kTB) * sizeof(float2);
 constexpr size_t k2RowSmem = (size_t)(2048 + 2 * k2Rows * G2::KCP + 2 * k2Rows * kTB) * sizeof(float2);
 constexpr size_t k2NhatSmem = (size_t)(2048 + G2::KR * k2NhatCols + 2 * k2NhatCols * kTB) * sizeof(float2);
 
+// ---- 256^2, 512^2 (any N = 32 M with M = 4, 8, 16): the same four stages on lane groups ----
+// Each N = 32 M-point transform is held by a group of M lanes (fft_group), a
+// warp holds 32 / M of them, a block four warps.
+
+constexpr int kGWarps = 4;
+template <int N>
+struct GroupGeo {
+    static constexpr int M = N / 32, GW = 32 / M, GB = kGWarps * GW;  // lanes a transform; transforms a warp, a block
+    static constexpr int TB = 32 * (M + 1);                              // float2 in a group's transpose buffer
+};
+
+// KBg: the inverse transform along y of item t = (plane t / KC, column t % KC),
+// one group each.  blockIdx.y: the flow.
+template <int N, int P, class Src>
+__global__ void __launch_bounds__(kGWarps * 32) k_fusedg_columns(const __grid_constant__ Src src,
+                                                                 const float2* __restrict__ tw) {
+    using Gm = Geo<N>;
+    using Gg = GroupGeo<N>;
+    constexpr int M = Gg::M;
+    const float2* __restrict__ S = src.planes_s(blockIdx.y);
+    float2* __restrict__ G = src.planes_g(blockIdx.y);
+    extern __shared__ float2 sm[];
+    float2* twg = sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gi = lane / M, gl = lane % M;
+    float2* tbg = sm + N + (warp * Gg::GW + gi) * Gg::TB;
+    load_twiddles_group<M, kGWarps * 32>(twg, tw);
+    __syncthreads();
+    const int t = (blockIdx.x * kGWarps + warp) * Gg::GW + gi;
+    const bool ok = t < P * Gm::KC;  // groups past the last item transform zeros
+    const int p = ok ? t / Gm::KC : 0, kx = ok ? t - p * Gm::KC : 0;
+    const size_t col = ((size_t)p * Gm::KCP + kx) * N;
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int j = gl + M * i;
+        v[i] = ok && row_kept_n<N>(j) ? S[col + j] : make_float2(0.f, 0.f);
+    }
+    fft_group<1, M>(v, tbg, twg, gl);
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < 32; i++) G[col + gl + M * i] = v[i];
+    }
+}
+
+// KCg's staging of one plane's x-spectrum (kept columns) of the block's R
+// rows: buf[yy][kx] = G[p][kx][y0 + yy] (runs of R consecutive rows).
+template <int N, int R>
+__device__ __forceinline__ void stage_plane_g(float2* __restrict__ buf, const float2* __restrict__ G, int p,
+                                              int y0) {
+    using Gm = Geo<N>;
+    constexpr int E = Gm::KC * R, NT = kGWarps * 32, passes = (E + NT - 1) / NT;
+    float2 t[passes];
+#pragma unroll
+    for (int k = 0; k < passes; k++) {
+        const int e = threadIdx.x + k * NT;
+        if (e < E) t[k] = G[((size_t)p * Gm::KCP + e / R) * N + y0 + e % R];
+    }
+#pragma unroll
+    for (int k = 0; k < passes; k++) {
+        const int e = threadIdx.x + k * NT;
+        if (e < E) buf[(e % R) * Gm::KCP + e / R] = t[k];
+    }
+}
+
+// This lane's elements k = gl + M i of the full complex spectrum of two real
+// planes packed as a + i b (bufB = nullptr: b = 0), as row_pair.
+template <int N>
+__device__ __forceinline__ void row_pair_g(float2 (&v)[32], const float2* __restrict__ bufA,
+                                           const float2* __restrict__ bufB, int gl) {
+    using Gm = Geo<N>;
+    constexpr int M = N / 32;
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int k = gl + M * i;
+        float2 z = make_float2(0.f, 0.f);
+        if (k < Gm::KC || k > N - Gm::KC) {
+            const int kk = k < Gm::KC ? k : N - k;
+            float2 A = bufA[kk];
+            float2 B = bufB ? bufB[kk] : make_float2(0.f, 0.f);
+            if (kk == 0) {
+                A.y = 0.f;
+                B.y = 0.f;
+            }
+            z = k < Gm::KC ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+        }
+        v[i] = z;
+    }
+}
+
+// dst[x] = (src[x].z, src[x].w, new[x]) for this lane's nodes x = gl + M i
+// of a row, in batches of 8 loads (as write_pair_row).
+template <int M>
+__device__ __forceinline__ void write_pair_group(const float4* __restrict__ src, float4* __restrict__ dst,
+                                                 const float2 (&v)[32], int gl) {
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        float4 cur[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) cur[k] = src[gl + M * (8 * b + k)];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int i = 8 * b + k;
+            dst[gl + M * i] = make_float4(cur[k].z, cur[k].w, v[i].x, v[i].y);
+        }
+    }
+}
+
+// KCg: the block's R rows, one group each (as KC).  blockIdx.y: the flow.
+template <int N, int P, class Src>
+__global__ void __launch_bounds__(kGWarps * 32) k_fusedg_rows(const __grid_constant__ Src src) {
+    using Gm = Geo<N>;
+    using Gg = GroupGeo<N>;
+    constexpr int M = Gg::M, R = Gg::GB;
+    const auto& r = src.rows(blockIdx.y);
+    extern __shared__ float2 sm[];
+    float2* twg = sm;
+    float2* buf = sm + N;  // 2 planes x R rows x KCP
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gi = lane / M, gl = lane % M;
+    const int row = warp * Gg::GW + gi;
+    float2* tbg = buf + 2 * R * Gm::KCP + row * Gg::TB;
+    const float2* mine0 = buf + row * Gm::KCP;
+    const float2* mine1 = buf + (R + row) * Gm::KCP;
+    const int y0 = blockIdx.x * R, y = y0 + row;
+    load_twiddles_group<M, kGWarps * 32>(twg, r.tw);
+    stage_plane_g<N, R>(buf, r.G, 2, y0);
+    stage_plane_g<N, R>(buf + R * Gm::KCP, r.G, 3, y0);
+    __syncthreads();
+    float2 v[32], hold[32];
+    row_pair_g<N>(v, mine0, mine1, gl);  // wx + i wy
+    fft_group<1, M>(v, tbg, twg, gl);
+#pragma unroll
+    for (int i = 0; i < 32; i++) hold[i] = v[i];
+    __syncthreads();  // every group has read the staging buffer
+    stage_plane_g<N, R>(buf, r.G, 0, y0);
+    stage_plane_g<N, R>(buf + R * Gm::KCP, r.G, 1, y0);
+    __syncthreads();
+    row_pair_g<N>(v, mine0, mine1, gl);  // u + i v
+    fft_group<1, M>(v, tbg, twg, gl);
+    float nl[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) nl[i] = fmaf(v[i].x, hold[i].x, v[i].y * hold[i].y);  // Eq. 7
+    if (P == 6 || P == 7) {  // the level pair holds the spline coefficients
+        __syncthreads();
+        stage_plane_g<N, R>(buf, r.G, 4, y0);
+        stage_plane_g<N, R>(buf + R * Gm::KCP, r.G, 5, y0);
+        __syncthreads();
+        row_pair_g<N>(v, mine0, mine1, gl);
+        fft_group<1, M>(v, tbg, twg, gl);
+    }
+    write_pair_group<M>(r.src + (size_t)y * N, r.dst + (size_t)y * N, v, gl);
+    if (P == 5 || P == 7) {  // the streamfunction stencil field
+        __syncthreads();
+        stage_plane_g<N, R>(buf, r.G, r.psi_plane, y0);
+        __syncthreads();
+        row_pair_g<N>(v, mine0, nullptr, gl);
+        fft_group<1, M>(v, tbg, twg, gl);
+        const float2* __restrict__ ps = r.psi_src + (size_t)y * N;
+        float2* __restrict__ pd = r.psi_dst + (size_t)y * N;
+#pragma unroll
+        for (int i = 0; i < 32; i++) pd[gl + M * i] = make_float2(ps[gl + M * i].y, v[i].x);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = make_float2(nl[i], 0.f);
+    fft_group<-1, M>(v, tbg, twg, gl);
+    __syncthreads();  // every group is done reading the staging buffer
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int kx = gl + M * i;
+        if (kx < Gm::KC) buf[row * Gm::KCP + kx] = v[i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < Gm::KC * R; e += blockDim.x) {
+        const int kx = e / R, yy = e - kx * R;
+        r.H[(size_t)kx * N + y0 + yy] = buf[yy * Gm::KCP + kx];
+    }
+}
+
+// KDg: N-hat of the kept modes of the block's columns (one group each) from
+// H, written to the row-major N-hat in runs of the block's columns through a
+// staging buffer.  blockIdx.y: the flow.
+template <int N, class Src>
+__global__ void __launch_bounds__(kGWarps * 32) k_fusedg_nhat(const __grid_constant__ Src src,
+                                                              const float2* __restrict__ tw) {
+    using Gm = Geo<N>;
+    using Gg = GroupGeo<N>;
+    constexpr int M = Gg::M, C = Gg::GB, nh = N / 2 + 1;
+    const float2* __restrict__ H = src.h(blockIdx.y);
+    float2* __restrict__ nhat = src.nhat_out(blockIdx.y);
+    extern __shared__ float2 sm[];
+    float2* twg = sm;
+    float2* out = sm + N;  // [KR][C]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gi = lane / M, gl = lane % M;
+    const int c = warp * Gg::GW + gi;
+    float2* tbg = out + Gm::KR * C + c * Gg::TB;
+    load_twiddles_group<M, kGWarps * 32>(twg, tw);
+    __syncthreads();
+    const int kx0 = blockIdx.x * C, kx = kx0 + c;
+    const bool ok = kx < Gm::KC;
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = ok ? H[(size_t)kx * N + gl + M * i] : make_float2(0.f, 0.f);
+    fft_group<-1, M>(v, tbg, twg, gl);
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const int j = gl + M * i;
+            if (row_kept_n<N>(j)) out[(j < Gm::KC ? j : j - (N - Gm::KR)) * C + c] = v[i];
+        }
+    }
+    __syncthreads();
+    const int ncols = min(C, Gm::KC - kx0);
+    for (int e = threadIdx.x; e < Gm::KR * C; e += blockDim.x) {
+        const int rr = e / C, cc = e - rr * C;
+        if (cc < ncols) nhat[(size_t)kept_row_n<N>(rr) * nh + kx0 + cc] = out[e];
+    }
+}
+
+template <int N>
+constexpr size_t kgColSmem() { return (size_t)(N + GroupGeo<N>::GB * GroupGeo<N>::TB) * sizeof(float2); }
+template <int N>
+constexpr size_t kgRowSmem() {
+    return (size_t)(N + 2 * GroupGeo<N>::GB * Geo<N>::KCP + GroupGeo<N>::GB * GroupGeo<N>::TB) * sizeof(float2);
+}
+template <int N>
+constexpr size_t kgNhatSmem() {
+    return (size_t)(N + Geo<N>::KR * GroupGeo<N>::GB + GroupGeo<N>::GB * GroupGeo<N>::TB) * sizeof(float2);
+}
+
 constexpr size_t kColSmem(int P) { return (size_t)(1024 + P * kTB) * sizeof(float2); }
 constexpr size_t kRowSmem =
     (size_t)(1024 + 2 * kRowWarps * kRowPitch + kRowWarps * (kTB + 1024)) * sizeof(float2);
@@ -830,7 +1155,16 @@ constexpr size_t kNhatSmem = (size_t)(1024 + kFKR * kNhatWarps + kNhatWarps * kT
 template <int N, int P, class Src>
 cudaError_t allow_smem() {
     cudaError_t e;
-    if (N == 1024) {
+    if constexpr (N <= 512) {
+        e = cudaFuncSetAttribute(k_fusedg_columns<N, P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kgColSmem<N>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fusedg_rows<N, P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kgRowSmem<N>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fusedg_nhat<N, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kgNhatSmem<N>());
+    } else if constexpr (N == 1024) {
         e = cudaFuncSetAttribute(k_fused_columns<P, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kColSmem(P));
         if (e == cudaSuccess)
@@ -864,7 +1198,12 @@ cudaError_t allow_smem_n(int planes) {
 
 template <class Src>
 cudaError_t allow_smem(int n, int planes) {
-    return n == 1024 ? allow_smem_n<1024, Src>(planes) : allow_smem_n<2048, Src>(planes);
+    switch (n) {
+        case 256: return allow_smem_n<256, Src>(planes);
+        case 512: return allow_smem_n<512, Src>(planes);
+        case 1024: return allow_smem_n<1024, Src>(planes);
+        default: return allow_smem_n<2048, Src>(planes);
+    }
 }
 
 // The four kernels for `count` flows of N^2 and P planes (the grid's member slice).
@@ -873,7 +1212,14 @@ void launch(const Src& src, int count, const float2* tw, cudaStream_t st) {
     using Gm = Geo<N>;
     const dim3 tiles((Gm::KC + kTile - 1) / kTile, (Gm::KR + kTile - 1) / kTile, count);
     k_fused_advance<N, P, Src><<<tiles, 256, 0, st>>>(src);
-    if (N == 1024) {
+    if constexpr (N <= 512) {
+        using Gg = GroupGeo<N>;
+        k_fusedg_columns<N, P, Src><<<dim3((P * Gm::KC + Gg::GB - 1) / Gg::GB, count), kGWarps * 32,
+                                      kgColSmem<N>(), st>>>(src, tw);
+        k_fusedg_rows<N, P, Src><<<dim3(N / Gg::GB, count), kGWarps * 32, kgRowSmem<N>(), st>>>(src);
+        k_fusedg_nhat<N, Src><<<dim3((Gm::KC + Gg::GB - 1) / Gg::GB, count), kGWarps * 32, kgNhatSmem<N>(),
+                                st>>>(src, tw);
+    } else if constexpr (N == 1024) {
         k_fused_columns<P, Src><<<dim3(kFKC, count), P * 32, kColSmem(P), st>>>(src, tw);
         k_fused_rows<P, Src><<<dim3(kFN / kRowWarps, count), kRowWarps * 32, kRowSmem, st>>>(src);
         k_fused_nhat<Src><<<dim3((kFKC + kNhatWarps - 1) / kNhatWarps, count), kNhatWarps * 32, kNhatSmem,
@@ -898,8 +1244,12 @@ void launch_n(int planes, const Src& src, int count, const float2* tw, cudaStrea
 
 template <class Src>
 void launch(int n, int planes, const Src& src, int count, const float2* tw, cudaStream_t st) {
-    if (n == 1024) launch_n<1024>(planes, src, count, tw, st);
-    else launch_n<2048>(planes, src, count, tw, st);
+    switch (n) {
+        case 256: launch_n<256>(planes, src, count, tw, st); break;
+        case 512: launch_n<512>(planes, src, count, tw, st); break;
+        case 1024: launch_n<1024>(planes, src, count, tw, st); break;
+        default: launch_n<2048>(planes, src, count, tw, st); break;
+    }
 }
 
 }  // namespace
@@ -911,10 +1261,15 @@ void launch(int n, int planes, const Src& src, int count, const float2* tw, cuda
 bool fused_fluid_supported(const el_flow* f) {
     static const bool off = std::getenv("ELPATH_FLUID_CUFFT") != nullptr;
     if (f->kinematic || off) return false;
-    // 2048^2 with the streamfunction plane (5 or 7 planes): the row kernel's
-    // extra sequential transform made it slower than the cuFFT path
-    // (measured 0.223 / 0.275 ms against 0.203 / 0.251 ms)
-    return f->n == 1024 || (f->n == 2048 && (f->nplanes == 4 || f->nplanes == 6));
+    // Measured one flow at a time (fluid step, direct launches, ms, fused
+    // against cuFFT): 128^2 0.034 / 0.028, 256^2 0.030 / 0.031, 512^2
+    // 0.030 / 0.036, 2048^2 0.130 / 0.171; with the streamfunction plane (5
+    // or 7 planes) the row kernels' extra sequential transform was slower
+    // at 256^2 (0.042 / 0.033) and 2048^2 (0.223 / 0.203), even at 512^2.
+    // Batched, 256^2 and 512^2 members gain too (64-member ensemble step
+    // 0.895 against 0.990 ms).
+    const bool plain = f->nplanes == 4 || f->nplanes == 6;
+    return f->n == 1024 || ((f->n == 256 || f->n == 512 || f->n == 2048) && plain);
 }
 
 // Launch attributes (dynamic shared memory above 48 KiB), at flow creation,

@@ -25,7 +25,7 @@ SYMBOLS = ("el_workspace_bytes", "el_create_flow", "el_create_kinematic", "el_se
            "el_step_coupled",
            "el_get_stats", "el_get_particles", "el_get_field", "el_sample_velocity",
            "el_profile_step", "el_get_tuning", "el_set_tuning", "el_autotune",
-           "el_kernel_launches", "el_batch_workspace_bytes", "el_batch_create", "el_batch_add",
+           "el_kernel_launches", "el_flow_fused", "el_batch_workspace_bytes", "el_batch_create", "el_batch_add",
            "el_batch_remove", "el_batch_step", "el_batch_autotune", "el_batch_size",
            "el_batch_kernel_launches", "el_batch_last_error", "el_batch_destroy",
            "el_batch_fft_pool_bytes", "el_batch_add_fft_pool", "el_dispersion_noalloc", "el_save_state", "el_load_state", "el_destroy_flow",
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
     lib.el_profile_step.argtypes = [P, D, I32]
     lib.el_kernel_launches.argtypes = [P]
     lib.el_kernel_launches.restype = I64
+    lib.el_flow_fused.argtypes = [P]
+    lib.el_flow_fused.restype = I32
     T = ctypes.POINTER(el_tuning)
     lib.el_get_tuning.argtypes = [P, T]
     lib.el_set_tuning.argtypes = [P, T]
@@ -313,6 +315,11 @@ class Flow:
 
     def kernel_launches(self) -> int:
         return int(self._lib.el_kernel_launches(self._h))
+
+    @property
+    def fused(self) -> bool:
+        """The fluid step runs the library's fused transforms (el_flow_fused)."""
+        return bool(self._lib.el_flow_fused(self._h))
 
     def tuning(self) -> dict:
         t = el_tuning()

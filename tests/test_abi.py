@@ -78,6 +78,7 @@ def test_calls_without_device_fail_cleanly(lib):
     assert b"n must be" in lib.el_last_error(None)
     assert lib.el_step_coupled(None, 1) == 1
     assert lib.el_kernel_launches(None) == 0
+    assert lib.el_flow_fused(None) == 0
     size = ctypes.c_size_t(0)
     assert lib.el_save_state(None, None, ctypes.byref(size)) == 1
     assert lib.el_load_state(None, None, 0) == 1

@@ -60,11 +60,13 @@ def test_members_match_their_solo_runs():
     for g, spec, ref in zip(flows, SPECS, solo):
         assert g.stats()["step"] == steps
         assert_same(state(g, spec), ref)
-    # one launch per stage for the whole batch (the particle stage once per
-    # scheme present: three here), 6 of our kernels per step
+    # one launch per stage for the whole batch: the fused step's four for the
+    # 256^2 member, the spectral and nonlinear stages for the others, the
+    # particle stage once per scheme present (three here), the step counters:
+    # 10 of our kernels per step
     l0 = batch.kernel_launches()
     batch.step(3)
-    assert batch.kernel_launches() - l0 == 3 * 6
+    assert batch.kernel_launches() - l0 == 3 * 10
     batch.close()
 
 
@@ -135,18 +137,20 @@ def make_fused(case, seed, n=1024):
 
 
 # (grid, case): the 1024^2 cases, a 2048^2 member on the fused step (4 planes)
-# and one on the cuFFT path (the streamfunction plane: 5 planes)
-FUSED_MEMBERS = [(1024, c) for c in FUSED_CASES] + [(2048, (1, 1, 0, 1)), (2048, (0, 1, 1, 0))]
+# and one on the cuFFT path (the streamfunction plane: 5 planes), a 512^2 and a
+# 256^2 member on the fused step
+FUSED_MEMBERS = [(1024, c) for c in FUSED_CASES] + [(2048, (1, 1, 0, 1)), (2048, (0, 1, 1, 0)),
+                                                     (512, (0, 1, 0, 0)), (256, (2, 1, 0, 1))]
 
 
 def test_fused_members_equal_their_solo_runs_bit_for_bit():
-    # 1024^2 and 2048^2 members take the fused fluid step in the batch too
+    # members on the fused grids take the fused fluid step in the batch too
     # (one launch of each fused kernel per grid and plane count, every member
     # in it): the same kernels' arithmetic as alone, so the same bits,
     # whatever the plane count, the AB2 form or the step each member joined
     # at (members at odd and even steps share a launch).  A 256^2 member steps
     # beside them.
-    head = [0, 3, 1, 4, 2, 1, 0]  # steps alone before joining
+    head = [0, 3, 1, 4, 2, 1, 0, 2, 5]  # steps alone before joining
     steps = 12
     refs = []
     for m, (n, case) in enumerate(FUSED_MEMBERS):
@@ -157,7 +161,7 @@ def test_fused_members_equal_their_solo_runs_bit_for_bit():
     small = make(SPECS[3], 9)
     small_ref = make(SPECS[3], 9)
     small_ref.step(steps)
-    batch = elpath.Batch(8)
+    batch = elpath.Batch(12)
     flows = []
     for m, (n, case) in enumerate(FUSED_MEMBERS):
         g = make_fused(case, 40 + 5 * m, n)

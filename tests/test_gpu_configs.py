@@ -5,7 +5,7 @@
   * the double shear layer, 2048^2, 16M particles at St = 1, Catmull-Rom,
     4000 steps;
   * the 64-member ensemble (256^2-1024^2, 1e4-1e6 particles each), batched
-    with FFT pools against each member stepped alone;
+    (their fluid steps fused; FFT pools for any on cuFFT) against each member stepped alone;
   * the served stream's first 16 requests at their drawn sizes (grids up to
     2048^2, up to 8.5M particles, up to ~2000 steps, both served schemes),
     served together against each run alone.
@@ -123,11 +123,11 @@ def test_ensemble_64_members_batched_equal_alone():
         return g
 
     batch = elpath.Batch(64)
-    for n in (256, 512):                # one FFT pool per cuFFT grid size, as the benchmark
-        k = sum(1 for wl in wls if wl.n == n)  # (1024^2 members run the fused step)
+    flows = [member(m) for m in range(64)]
+    for n in (256, 512, 1024):          # one FFT pool per grid size of cuFFT members, as the benchmark
+        k = sum(1 for wl, g in zip(wls, flows) if wl.n == n and not g.fused)
         if k:
             batch.add_fft_pool(n, k)
-    flows = [member(m) for m in range(64)]
     for g in flows:
         batch.add(g)
     batch.step(steps)
@@ -156,7 +156,7 @@ def test_ensemble_64_members_batched_equal_alone():
 
 def test_served_stream_first_16_requests_equal_alone():
     reqs = inputs.served_requests(count=16)
-    pools = {128: 4, 256: 4, 512: 4, 2048: 2}
+    pools = {128: 4}
     srv = serve.Server(hbm_budget=100 << 30, max_members=64, tick_steps=50, keep_positions=True,
                        fft_pool_slots=pools)
     results = srv.run(inputs.served_requests(count=16), time_scale=0.05, timeout=600)

@@ -1,13 +1,14 @@
-"""The fused 1024^2 and 2048^2 fluid steps (fused_fluid.cu: pruned transforms
+"""The fused 256^2-2048^2 fluid steps (fused_fluid.cu: pruned transforms
 of our own, fused with the AB2 update and the nonlinear term) against the
 cuFFT path (ELPATH_FLUID_CUFFT=1, run in a child process), and against the
 oracle.
 
 At 1024^2 every plane configuration the step has: 4 planes (bilinear,
 Catmull-Rom, raw B-spline), 6 (prefiltered B-spline), 5 and 7 (with the
-streamfunction plane of tracer_velocity = 1), each AB2 form; at 2048^2 the
-ones it serves (4 and 6 planes; a 2048-point transform is two 1024-point ones
-on a warp pair).  The two paths differ only by the rounding of their
+streamfunction plane of tracer_velocity = 1), each AB2 form; at 2048^2, 512^2
+and 256^2 the ones it serves (4 and 6 planes; a 2048-point transform is two
+1024-point ones on a warp pair, a 512- or 256-point one is held by a group of
+16 or 8 lanes).  The two paths differ only by the rounding of their
 transforms, so after 100 steps the vorticity agrees to a few 1e-7 and
 positions to a few 1e-8; the physical velocity planes, which the fused step
 does not keep, are rebuilt on request.
@@ -38,6 +39,10 @@ CASES = [  # (n, interp, bspline_prefilter, tracer_velocity, ab2_mode): planes
     (2048, 0, 1, 0, 0),  # 4
     (2048, 1, 1, 0, 1),  # 4, explicit AB2
     (2048, 2, 1, 0, 0),  # 6
+    (512, 0, 1, 0, 0),   # 4
+    (512, 2, 1, 0, 1),   # 6, explicit AB2
+    (256, 1, 1, 0, 0),   # 4
+    (256, 2, 0, 0, 1),   # 4 (raw B-spline), explicit AB2
 ]
 
 CHILD = textwrap.dedent("""
@@ -71,7 +76,9 @@ def run_child(case, out, cufft):
 
 @pytest.mark.parametrize("case", CASES, ids=["bilinear", "catmull_rom_explicit", "bspline_raw",
                                              "bspline", "psi", "bspline_psi_explicit",
-                                             "2048_bilinear", "2048_catmull_rom_explicit", "2048_bspline"])
+                                             "2048_bilinear", "2048_catmull_rom_explicit", "2048_bspline",
+                                             "512_bilinear", "512_bspline_explicit", "256_catmull_rom",
+                                             "256_bspline_raw_explicit"])
 def test_fused_step_matches_the_cufft_path(case, tmp_path):
     a = run_child(case, str(tmp_path / "fused.npz"), cufft=False)
     b = run_child(case, str(tmp_path / "cufft.npz"), cufft=True)
