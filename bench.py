@@ -894,25 +894,27 @@ def run_profile_launch(args, wl, scheme):
 
 def run_profile_ensemble(args):
     """A fixed run of the 64-member ensemble for ncu: the batch as the bench
-    builds it (one FFT pool per cuFFT grid size, no autotuning), 3 steps, then
-    2 more.  Its steps run inside the NVTX range el_batch_step, so
-    `ncu --nvtx --nvtx-include "el_batch_step/"` captures only their kernels."""
+    builds it (one FFT pool per grid size of members on cuFFT transforms, no
+    autotuning), 3 steps, then 2 more.  Its steps run inside the NVTX range
+    el_batch_step, so `ncu --nvtx --nvtx-include "el_batch_step/"` captures
+    only their kernels."""
     import torch
     from paper_2607_17836_b300 import elpath
     wls = inputs.ensemble_members(64)
     batch = elpath.Batch(64)
-    for n in (256, 512):
-        k = sum(1 for w in wls if w.n == n)
-        if k:
-            batch.add_fft_pool(n, k)
     flows = []
     for wl in wls:
         sp = wl.species[0]
         g = elpath.Flow(wl.n, wl.nu, wl.dt, wl.omega0(), interp=0, max_species=1,
                         max_particles=sp.count, sort_every=SORT_EVERY)
         g.set_particles(0, inputs.uniform_positions(sp.count, sp.seed), sp.st)
-        batch.add(g)
         flows.append(g)
+    for n in (256, 512, 1024):
+        k = sum(1 for w, g in zip(wls, flows) if w.n == n and not g.fused)
+        if k:
+            batch.add_fft_pool(n, k)
+    for g in flows:
+        batch.add(g)
     batch.step(3)
     batch.synchronize()
     batch.step(2)

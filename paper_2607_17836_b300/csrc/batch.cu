@@ -476,6 +476,7 @@ el_status enqueue_fluid(el_batch* b, cudaStream_t s, int ahead) {
                                      4 + (c & 3), ahead, b->fused_twiddle[c / 4]));
         b->launches += 4;
     }
+    if (a.spec_tasks == 0) return EL_OK;  // every member is fused
     k_batch_spectral<<<b->grid_spec, kBSpecThreads, 0, s>>>(a, ahead);
     b->launches++;
     EL_TRY(fork_ffts(b, s, true));
