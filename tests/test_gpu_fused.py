@@ -94,18 +94,21 @@ def test_fused_step_matches_the_cufft_path(case, tmp_path):
     np.testing.assert_allclose(a["e"], b["e"], rtol=1e-6)
 
 
-def test_fused_step_against_the_oracle_with_the_velocity_planes():
-    # the fused path is the default at 1024^2: vorticity and the rebuilt
-    # physical velocity against the FP64 oracle after 100 steps
-    w0 = inputs.decaying_turbulence(N, 2)
-    g = elpath.Flow(N, 1e-4, 5e-4, w0, interp=1, max_species=0)
-    o = OracleRun(N, 1e-4, 5e-4, w0)
+@pytest.mark.parametrize("n", [256, 512, 1024])
+def test_fused_step_against_the_oracle_with_the_velocity_planes(n):
+    # the fused path is the default at these sizes (4 planes): vorticity and
+    # the rebuilt physical velocity against the FP64 oracle after 100 steps
+    w0 = inputs.decaying_turbulence(n, 2)
+    dt = 5e-4 * 1024 / n
+    g = elpath.Flow(n, 1e-4, dt, w0, interp=1, max_species=0)
+    assert g.fused
+    o = OracleRun(n, 1e-4, dt, w0)
     g.step(100)
     o.step(100)
     f = o.flow.fields(("u", "v", "w"))
     for which, key in ((0, "w"), (1, "u"), (2, "v")):
         d = rel_linf(g.field(which), f[key])
-        record("fused fluid step, decaying 1024^2", None, f"{key} L-inf rel., 100 steps", d, OMEGA_RTOL)
+        record(f"fused fluid step, decaying {n}^2", None, f"{key} L-inf rel., 100 steps", d, OMEGA_RTOL)
         assert d < OMEGA_RTOL, (key, d)
     g.close()
 
