@@ -71,9 +71,7 @@ CHILD = textwrap.dedent("""
 
 def test_debug_build_counts_invariant_violations(tmp_path):
     lib = str(tmp_path / "libelpath_check.so")
-    r = subprocess.run(build.nvcc_command(lib, ["-DEL_CHECK_BOUNDS=1"]), capture_output=True,
-                       text=True)
-    assert r.returncode == 0, r.stderr[-2000:]
+    build.build_to(lib, ["-DEL_CHECK_BOUNDS=1"])  # raises on a compile error
     script = tmp_path / "child.py"
     script.write_text(CHILD.format(root=ROOT, lib=lib))
     out = subprocess.run([sys.executable, str(script)], capture_output=True, text=True,
