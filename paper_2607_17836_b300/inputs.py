@@ -10,6 +10,7 @@ PCG64 generator seeded explicitly per call.
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -51,20 +52,34 @@ def decaying_turbulence(n: int, seed: int, k0: float = 10.0, energy: float = 1.0
     the AB2 scheme: the FP64 solve overflows within ~200 steps.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
+    band, amp_band, k2_band = _shell_spectrum(n, float(k0))
+    phase = rng.uniform(0.0, TWO_PI, size=(n, n))
+    z = np.zeros((n, n), dtype=np.complex128)  # zero outside the band
+    z[band] = amp_band * np.exp(1j * phase[band])
+    # Coefficients of the real part: (z_k + conj(z_{-k})) / 2, with
+    # z_{-k}[j][i] = z[-j mod n][-i mod n].
+    zneg = np.roll(z[::-1, ::-1], 1, axis=(0, 1))
+    zr = 0.5 * (z + np.conj(zneg))
+    e_mean = 0.5 * np.sum(np.abs(zr[band]) ** 2 / k2_band)
+    zr *= math.sqrt(energy / (TWO_PI * TWO_PI) / e_mean)
+    omega = np.real(np.fft.ifft2(zr)) * (n * n)
+    return np.ascontiguousarray(omega)
+
+
+@functools.lru_cache(maxsize=8)
+def _shell_spectrum(n: int, k0: float):
+    """The parts of decaying_turbulence that depend on (n, k0) only, computed
+    once per grid: the drawn band (3|kx| < n, 3|ky| < n, k != 0), the mode
+    amplitudes |k| sqrt(E(|k|) / (pi |k|)) on it and |k|^2 on it (read-only)."""
     KX, KY = _wavenumbers(n)
     kmag = np.hypot(KX, KY)
     band = (3 * np.abs(KX) < n) & (3 * np.abs(KY) < n) & (kmag > 0)
     shell = np.where(band, kmag ** 4 * np.exp(-(kmag / k0) ** 2), 0.0)
     amp = np.where(band, kmag * np.sqrt(shell / (np.pi * np.maximum(kmag, 1.0))), 0.0)
-    phase = rng.uniform(0.0, TWO_PI, size=(n, n))
-    z = amp * np.exp(1j * phase)
-    # Coefficients of the real part: (z_k + conj(z_{-k})) / 2.
-    zneg = z[(-np.arange(n)) % n][:, (-np.arange(n)) % n]
-    zr = 0.5 * (z + np.conj(zneg))
-    e_mean = 0.5 * np.sum(np.abs(zr[band]) ** 2 / kmag[band] ** 2)
-    zr *= math.sqrt(energy / (TWO_PI * TWO_PI) / e_mean)
-    omega = np.real(np.fft.ifft2(zr)) * (n * n)
-    return np.ascontiguousarray(omega)
+    out = (band, amp[band], kmag[band] ** 2)
+    for a in out:
+        a.setflags(write=False)
+    return out
 
 
 def kelvin_helmholtz(n: int, seed: int, delta: float = math.pi / 50, amp: float = 1e-3,

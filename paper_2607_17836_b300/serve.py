@@ -17,7 +17,9 @@ needs), so a request finishes exactly at its step count.  Time-to-result is
 measured from the request's arrival to the moment its result is on the host.
 A request's host inputs (initial vorticity, particle positions) are prepared
 on a thread pool from the moment it arrives, so the device loop never waits
-for them; requests are admitted oldest first once their inputs are ready.
+for them; the oldest request whose inputs are ready is admitted first (one
+still being prepared does not hold back the requests behind it, and one that
+is ready but does not fit the memory left does).
 Everything numerical runs in the CUDA library; this module only schedules.
 """
 from __future__ import annotations
@@ -141,13 +143,17 @@ class Server:
     def _admit(self):
         self._prepare_ahead()
         while self.waiting and len(self.active) < self.max_members:
-            req, prep = self.waiting[0]
-            if prep is None or not prep.done():
-                break                                # oldest first: its inputs are not ready
+            # the oldest request whose inputs are ready (one whose inputs are
+            # still being prepared does not hold back those behind it)
+            k = next((k for k, (_, prep) in enumerate(self.waiting)
+                      if prep is not None and prep.done()), None)
+            if k is None:
+                break
+            req, prep = self.waiting[k]
             need = elpath.workspace_bytes(request_desc(req))
             if self.used + need > self.hbm_budget:
-                break                                # oldest first: wait for memory
-            self.waiting.popleft()
+                break                                # oldest ready first: wait for memory
+            del self.waiting[k]
             self._prepare_ahead()
             g = build_flow(req, None, self.device, prep.result())
             self.batch.add(g)
