@@ -8,8 +8,8 @@
 //   cuFFT R2C per member, on forked branches
 //     (members in a slot of an FFT pool: one batched C2R and one batched R2C
 //     per pool instead, over the pool's contiguous slots)
-//   k_batch_rk4<S>    (persistent, every member's species) RK4 particle step,
-//                     one launch per interpolation scheme present
+//   k_batch_rk4<S,G>  (every member's species) RK4 particle step, one launch
+//                     per scheme and stencil gather present
 //   k_batch_advance                                        per-member step counters
 //
 // Members whose fluid step is the fused one (fused_fluid.cu)
@@ -55,6 +55,11 @@ struct BatchArgs {
     const SpeciesDev* const* rk_sp;   // that member's device species descriptor
     int nmembers, nentries;
     int spec_tasks, nl_tasks, rk_tasks;
+    // entries grouped by class c = 2 scheme + gather (gather 1: the
+    // warp-shared patch): entries [rk_class_entry[c], rk_class_entry[c + 1]),
+    // their tasks [rk_class_task[c], rk_class_task[c + 1]), and the class's
+    // state-prefetch distance in particles
+    int rk_class_entry[7], rk_class_task[7], rk_prefetch[6];
 };
 
 namespace {
@@ -62,6 +67,7 @@ namespace {
 constexpr int kBSpecThreads = 128;
 constexpr int kBNlThreads = 256;
 constexpr int kSideStreams = 4;
+constexpr int kRkClasses = 6;  // (scheme, gather) classes of the particle entries
 
 // Largest k in [0, count) with begin[k] <= t (begin ascending, begin[0] = 0).
 __device__ __forceinline__ int owner_of(const int* __restrict__ begin, int count, int t) {
@@ -116,34 +122,55 @@ __global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_co
 // One kernel per interpolation scheme (each with its own register budget);
 // the entries of the other schemes are skipped.
 // SHARED: the warp-shared stencil patch of the cubic schemes (as k_rk4).
+// K6 for task t (a run of one entry's particles) of class c = 2 SCHEME + SHARED.
 template <int SCHEME, bool SHARED>
-__global__ void __launch_bounds__(512, SCHEME == 0 ? 3 : 1) k_batch_rk4(const __grid_constant__ BatchArgs b) {
-    for (int t = blockIdx.x; t < b.rk_tasks; t += gridDim.x) {
-        const int e = owner_of(b.rk_begin, b.nentries, t);
-        const MemberDev& md = b.members[b.rk_member[e]];
-        if (md.scheme != SCHEME) continue;
-        const SpeciesDev& sd = *b.rk_sp[e];
-        const int p = (t - b.rk_begin[e]) * (int)blockDim.x + (int)threadIdx.x;
-        if constexpr (SHARED) {
-            // warp-shared stencils (as in the single-flow kernel): every
-            // lane of the warp takes part; the branches are block-uniform
-            extern __shared__ float2 el_patch[];
-            const bool active = p < sd.np;
-            if (md.psi_plane >= 0 && !sd.inertial) {
-                if (active) rk4_psi_tracer<SCHEME>(md.psi[md.step % 2], md.n, md.log2n, md.h, sd, p);
-                continue;
-            }
-            rk4_particle_coop<SCHEME>(md.snap[md.step % 2], md.n, md.log2n, md.dt, md.h, sd, p,
-                                      active, el_patch + (threadIdx.x >> 5) * (3 * kPatchCap));
-            continue;
+__device__ __forceinline__ void batch_rk4_task(const BatchArgs& b, int c, int t, int prefetch) {
+    const int e0 = b.rk_class_entry[c];
+    const int e = e0 + owner_of(b.rk_begin + e0, b.rk_class_entry[c + 1] - e0, t);
+    const MemberDev& md = b.members[b.rk_member[e]];
+    const SpeciesDev& sd = *b.rk_sp[e];
+    const int first = (t - b.rk_begin[e]) * (int)blockDim.x;
+    prefetch_state(sd, first, prefetch);
+    const int p = first + (int)threadIdx.x;
+    const int k = (int)(md.step % 2);
+    if constexpr (SHARED) {
+        // warp-shared stencils (as in the single-flow kernel): every lane of
+        // the warp takes part; the branches are block-uniform
+        extern __shared__ float2 el_patch[];
+        const bool active = p < sd.np;
+        if (md.psi_plane >= 0 && !sd.inertial) {
+            if (active) rk4_psi_tracer<SCHEME>(md.psi[k], md.n, md.log2n, md.h, sd, p);
+            return;
         }
-        if (p >= sd.np) continue;
-        if (md.psi_plane >= 0)
-            rk4_particle<SCHEME, true>(md.snap[md.step % 2], md.psi[md.step % 2], md.n, md.log2n,
-                                       md.dt, md.h, sd, p);
-        else
-            rk4_particle<SCHEME, false>(md.snap[md.step % 2], nullptr, md.n, md.log2n, md.dt, md.h,
-                                        sd, p);
+        rk4_particle_coop<SCHEME>(md.snap[k], md.n, md.log2n, md.dt, md.h, sd, p, active,
+                                  el_patch + (threadIdx.x >> 5) * (3 * kPatchCap));
+        return;
+    }
+    if (p >= sd.np) return;
+    if (md.psi_plane >= 0)
+        rk4_particle<SCHEME, true>(md.snap[k], md.psi[k], md.n, md.log2n, md.dt, md.h, sd, p);
+    else
+        rk4_particle<SCHEME, false>(md.snap[k], nullptr, md.n, md.log2n, md.dt, md.h, sd, p);
+}
+
+// K6 for every entry of one (scheme, gather) class, with the single-flow
+// kernel's register caps (stages.cuh).  The cubic classes: one block per task
+// with the L2 state prefetch, as in the single-flow kernel (a grid-stride loop
+// costs the capped kernels spills; persistent, a batch of one ran 1.2-1.5x
+// slower than the flow alone).  The bilinear class (40 registers): a
+// persistent grid of one resident wave looping over the tasks, without the
+// prefetch; one block per task slowed the 64-member ensemble step, whose
+// particle launch runs beside the fluid branch, from 0.910 to 0.977 ms.
+template <int SCHEME, bool SHARED>
+__global__ void __launch_bounds__(512, SCHEME == 0 ? 3 : 1)
+    __maxnreg__(SHARED ? EL_RK4_SHARED_MAXNREG : (SCHEME == 1 || SCHEME == 2 ? EL_RK4_CUBIC_MAXNREG : 128))
+    k_batch_rk4(const __grid_constant__ BatchArgs b) {
+    constexpr int c = 2 * SCHEME + (SHARED ? 1 : 0);
+    if constexpr (SCHEME == 0) {
+        for (int t = b.rk_class_task[c] + (int)blockIdx.x; t < b.rk_class_task[c + 1]; t += gridDim.x)
+            batch_rk4_task<SCHEME, SHARED>(b, c, t, 0);
+    } else {
+        batch_rk4_task<SCHEME, SHARED>(b, c, b.rk_class_task[c] + (int)blockIdx.x, b.rk_prefetch[c]);
     }
 }
 
@@ -213,9 +240,8 @@ struct el_batch {
     int fused_begin[4 * kFusedGrids + 1] = {};
     const float2* fused_twiddle[kFusedGrids] = {};  // the n-entry table of a member of each grid
     BatchArgs args{};
-    int grid_spec = 0, grid_nl = 0, grid_rk[3] = {0, 0, 0};
-    bool scheme_used[3] = {false, false, false};
-    bool rk_shared[3] = {false, false, false};  // warp-shared stencil patch per scheme
+    int grid_spec = 0, grid_nl = 0;
+    unsigned grid_bilinear = 1;  // the persistent bilinear particle grid (one resident wave)
     bool tables_valid = false;
     // one coupled step of every member in three captured forms (fluid of
     // step s, particles of s alongside fluid of s + 1, particles of the last
@@ -355,19 +381,33 @@ el_status rebuild_tables(el_batch* b) {
             BT_CUDA(b, fused_fluid_batch_prepare(n, planes));
     }
     b->fused_begin[4 * el_batch::kFusedGrids] = (int)b->h_fused.size();
-    for (int m = 0; m < M; m++) {
-        el_flow* f = b->members[m];
-        if (f->rk4_threads != rk_threads)
+    BatchArgs& a = b->args;
+    for (int m = 0; m < M; m++)
+        if (b->members[m]->rk4_threads != rk_threads)
             return bfail(b, EL_EINVAL, "batch members must share one rk4 block size");
-        for (int s = 0; s < f->d.max_species; s++) {
-            if (f->sp[s].np == 0) continue;
-            b->h_rk_member.push_back(m);
-            b->h_rk_sp.push_back(f->table + s);
-            b->h_rk_begin.push_back(b->h_rk_begin.back() +
-                                    (int)((f->sp[s].np + rk_threads - 1) / rk_threads));
+    // the (member, species) entries, class by class; each entry's own
+    // density picks its gather (a sparse member beside a dense one keeps its
+    // register stencils)
+    for (int c = 0; c < kRkClasses; c++) {
+        a.rk_class_entry[c] = (int)b->h_rk_member.size();
+        a.rk_class_task[c] = b->h_rk_begin.back();
+        for (int m = 0; m < M; m++) {
+            el_flow* f = b->members[m];
+            if (f->d.interp < 0 || f->d.interp > 2) continue;
+            for (int s = 0; s < f->d.max_species; s++) {
+                if (f->sp[s].np == 0) continue;
+                const bool shared = rk4_shared_gather(f->d.interp, f->gather,
+                                                      (double)f->sp[s].np / (double)f->n2);
+                if (2 * f->d.interp + (shared ? 1 : 0) != c) continue;
+                b->h_rk_member.push_back(m);
+                b->h_rk_sp.push_back(f->table + s);
+                b->h_rk_begin.push_back(b->h_rk_begin.back() +
+                                        (int)((f->sp[s].np + rk_threads - 1) / rk_threads));
+            }
         }
     }
-    BatchArgs& a = b->args;
+    a.rk_class_entry[kRkClasses] = (int)b->h_rk_member.size();
+    a.rk_class_task[kRkClasses] = b->h_rk_begin.back();
     a.members = b->d_members;
     a.spec_begin = b->d_spec_begin;
     a.nl_begin = b->d_nl_begin;
@@ -404,27 +444,22 @@ el_status rebuild_tables(el_batch* b) {
     b->grid_spec = std::max(1, std::min(a.spec_tasks, occ * b->sms));
     BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_nonlinear, kBNlThreads, 0));
     b->grid_nl = std::max(1, std::min(a.nl_tasks, occ * b->sms));
-    void (*rk_kernels[3][2])(BatchArgs) = {{k_batch_rk4<0, false>, k_batch_rk4<0, false>},
-                                           {k_batch_rk4<1, false>, k_batch_rk4<1, true>},
-                                           {k_batch_rk4<2, false>, k_batch_rk4<2, true>}};
-    const int gather = b->members.empty() ? EL_GATHER_AUTO : b->members[0]->gather;
-    for (int sc = 0; sc < 3; sc++) {
-        b->scheme_used[sc] = false;
-        double density = 0.0;  // particles per cell of the densest species of the scheme
-        for (el_flow* f : b->members) {
-            if (f->d.interp != sc) continue;
-            b->scheme_used[sc] = true;
-            for (int s = 0; s < f->d.max_species; s++)
-                density = std::max(density, (double)f->sp[s].np / (double)f->n2);
-        }
-        b->rk_shared[sc] = rk4_shared_gather(sc, gather, density);
-        const size_t smem = rk4_patch_bytes(b->rk_shared[sc], rk_threads);
-        auto kern = rk_kernels[sc][b->rk_shared[sc] ? 1 : 0];
+    // each class's prefetch distance (EL_RK4_PREFETCH_WAVES resident waves;
+    // the cubic classes) and the bilinear class's persistent grid
+    void (*rk_kernels[kRkClasses])(BatchArgs) = {k_batch_rk4<0, false>, nullptr,
+                                                  k_batch_rk4<1, false>, k_batch_rk4<1, true>,
+                                                  k_batch_rk4<2, false>, k_batch_rk4<2, true>};
+    for (int c = 0; c < kRkClasses; c++) {
+        a.rk_prefetch[c] = 0;
+        if (a.rk_class_task[c + 1] == a.rk_class_task[c] || !rk_kernels[c]) continue;
+        const size_t smem = rk4_patch_bytes(c & 1, rk_threads);
         if (smem > 0)
-            BT_CUDA(b, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            BT_CUDA(b, cudaFuncSetAttribute(rk_kernels[c], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)rk4_patch_bytes(true, 512)));
-        BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, rk_threads, smem));
-        b->grid_rk[sc] = std::max(1, std::min(a.rk_tasks, std::max(1, occ) * b->sms));
+        BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rk_kernels[c], rk_threads, smem));
+        const int wave = std::max(1, occ) * b->sms;
+        if (c == 0) b->grid_bilinear = (unsigned)wave;
+        else a.rk_prefetch[c] = (int)((double)wave * EL_RK4_PREFETCH_WAVES + 0.5) * rk_threads;
     }
     for (FftPool& p : b->pools) ensure_prefix_plans(b, p, p.span());
     b->tables_valid = true;
@@ -490,18 +525,15 @@ el_status enqueue_fluid(el_batch* b, cudaStream_t s, int ahead) {
 el_status enqueue_particles(el_batch* b) {
     const BatchArgs& a = b->args;
     if (a.rk_tasks > 0) {
-        int threads = b->members.empty() ? 256 : b->members[0]->rk4_threads;
+        const int threads = b->members.empty() ? 256 : b->members[0]->rk4_threads;
         const size_t smem = rk4_patch_bytes(true, threads);
-        if (b->scheme_used[0]) k_batch_rk4<0, false><<<b->grid_rk[0], threads, 0, b->stream>>>(a);
-        if (b->scheme_used[1]) {
-            if (b->rk_shared[1]) k_batch_rk4<1, true><<<b->grid_rk[1], threads, smem, b->stream>>>(a);
-            else k_batch_rk4<1, false><<<b->grid_rk[1], threads, 0, b->stream>>>(a);
-        }
-        if (b->scheme_used[2]) {
-            if (b->rk_shared[2]) k_batch_rk4<2, true><<<b->grid_rk[2], threads, smem, b->stream>>>(a);
-            else k_batch_rk4<2, false><<<b->grid_rk[2], threads, 0, b->stream>>>(a);
-        }
-        b->launches += (int)b->scheme_used[0] + (int)b->scheme_used[1] + (int)b->scheme_used[2];
+        auto tasks = [&](int c) { return (unsigned)(a.rk_class_task[c + 1] - a.rk_class_task[c]); };
+        if (tasks(0)) k_batch_rk4<0, false><<<std::min(tasks(0), b->grid_bilinear), threads, 0, b->stream>>>(a);
+        if (tasks(2)) k_batch_rk4<1, false><<<tasks(2), threads, 0, b->stream>>>(a);
+        if (tasks(3)) k_batch_rk4<1, true><<<tasks(3), threads, smem, b->stream>>>(a);
+        if (tasks(4)) k_batch_rk4<2, false><<<tasks(4), threads, 0, b->stream>>>(a);
+        if (tasks(5)) k_batch_rk4<2, true><<<tasks(5), threads, smem, b->stream>>>(a);
+        for (int c = 0; c < kRkClasses; c++) b->launches += tasks(c) > 0;
     }
     return EL_OK;
 }

@@ -21,17 +21,8 @@ constexpr int kRK4MaxThreads = 512;
 #ifndef EL_RK4_CUBIC_MIN_BLOCKS
 #define EL_RK4_CUBIC_MIN_BLOCKS 1
 #endif
-// The cubic kernels' register caps.  Register-cached stencils: 96 (4-8 B of
-// spills) fits 5 blocks of 128 threads per SM against 4 at their natural 120,
-// 8-10 % faster at 1024^2 (4 and 16 particles per cell); 80 spills 250 B and
-// is slower.  Warp-shared stencils (PatchStencil: nothing large stays in
-// registers): 56, measured against 48 and 64 at 16 particles per cell.
-#ifndef EL_RK4_CUBIC_MAXNREG
-#define EL_RK4_CUBIC_MAXNREG 96
-#endif
-#ifndef EL_RK4_SHARED_MAXNREG
-#define EL_RK4_SHARED_MAXNREG 56
-#endif
+// The cubic kernels' register caps, EL_RK4_CUBIC_MAXNREG and
+// EL_RK4_SHARED_MAXNREG, are in stages.cuh (the batched kernels take them too).
 // EL_GATHER_AUTO takes the warp-shared patch from this many particles per
 // cell (of the densest species) on.  Measured (Catmull-Rom, St = 1): 1 per
 // cell (1024^2, 1M a species) registers 0.110 ms, shared 0.175 ms; 4 per
@@ -39,9 +30,6 @@ constexpr int kRK4MaxThreads = 512;
 // 0.344 ms.
 #ifndef EL_RK4_SHARED_DENSITY
 #define EL_RK4_SHARED_DENSITY 2.0
-#endif
-#ifndef EL_RK4_PREFETCH_WAVES
-#define EL_RK4_PREFETCH_WAVES 1.0
 #endif
 
 struct RK4Args {
@@ -55,26 +43,6 @@ struct RK4Args {
     uint32_t* check;          // EL_CHECK_BOUNDS builds: the flow's violation words
     int prefetch;             // particles ahead whose state a block prefetches into L2 (0: none)
 };
-
-// Bulk prefetch into L2 of the state of the block `ahead` particles later in
-// the same species (its cell, offset and velocity rows), issued by thread 0.
-// The state stream is latency-bound: a block that waits on its own loads and
-// then on its L2 gathers keeps few HBM requests in flight, so the block about
-// one resident wave earlier asks for them.  Only whole 16-byte units inside
-// [q0, np) are prefetched (start aligned: q0 is a multiple of the block size,
-// the arrays 256-byte aligned); a prefetch changes no data and waits for
-// nothing.
-__device__ __forceinline__ void prefetch_state(const SpeciesDev& sd, int first, int ahead) {
-    const int q0 = first + ahead;
-    if (threadIdx.x != 0 || ahead <= 0 || q0 >= sd.np) return;
-    const unsigned cnt = (unsigned)min((int)blockDim.x, sd.np - q0);
-    const unsigned b4 = (cnt * 4u) & ~15u, b8 = (cnt * 8u) & ~15u;
-    const int cur = sd.cur;
-    if (b4) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.cell[cur] + q0), "r"(b4) : "memory");
-    if (b8) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.off[cur] + q0), "r"(b8) : "memory");
-    if (b8 && sd.inertial)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.vel[cur] + q0), "r"(b8) : "memory");
-}
 
 // The species of block b: the largest k with block_begin[k] <= b (ascending;
 // slots past the last species hold UINT_MAX), by a three-step binary search.
@@ -180,8 +148,7 @@ static int rk4_wave_blocks(int threads) {
 
 // The prefetch distance of k_rk4 in particles, cached per block size and
 // gather: EL_RK4_PREFETCH_WAVES resident waves (SMs x resident blocks), a
-// whole number of blocks.  Measured at 1024^2: 0.5, 1 and 2 waves time alike,
-// 4-5 % faster than no prefetch for every scheme and particle count.
+// whole number of blocks.
 static int rk4_prefetch_distance(el_flow* f, bool shared) {
     const int T = f->rk4_threads;
     const int key = T + (shared ? 1024 : 0);

@@ -9,6 +9,26 @@
 #ifndef EL_STREAMING_STATE
 #define EL_STREAMING_STATE 1
 #endif
+
+// Register caps of the cubic schemes' particle kernels (single-flow k_rk4 and
+// batched k_batch_rk4).  Register-cached stencils: 96 (4-8 B of spills) fits
+// 5 blocks of 128 threads per SM against 4 at their natural 120, 8-10 %
+// faster at 1024^2 (4 and 16 particles per cell); 80 spills 250 B and is
+// slower.  Warp-shared stencils (PatchStencil: nothing large stays in
+// registers): 56, measured against 48 and 64 at 16 particles per cell.
+#ifndef EL_RK4_CUBIC_MAXNREG
+#define EL_RK4_CUBIC_MAXNREG 96
+#endif
+#ifndef EL_RK4_SHARED_MAXNREG
+#define EL_RK4_SHARED_MAXNREG 56
+#endif
+// The L2 prefetch distance of the particle kernels in resident waves (SMs x
+// resident blocks).  Measured at 1024^2: 0.5, 1 and 2 waves time alike, 4-5 %
+// faster than no prefetch for every scheme and particle count.
+#ifndef EL_RK4_PREFETCH_WAVES
+#define EL_RK4_PREFETCH_WAVES 1.0
+#endif
+
 #if EL_STREAMING_STATE
 #define EL_STATE_LD(ptr) __ldcs(ptr)
 #define EL_STATE_ST(ptr, v) __stcs(ptr, v)
@@ -441,6 +461,26 @@ __device__ __forceinline__ void rk4_particle(const float4* __restrict__ snap,
     q.st.bind(kin);  // the prescribed field of EL_ANALYTIC; unused by the grid schemes
     q.st.load(snap, n, q.ci, q.cj);
     rk4_finish(snap, n, log2n, dt, h, sd, q);
+}
+
+// Bulk prefetch into L2 of the state of the block `ahead` particles later in
+// the same species (its cell, offset and velocity rows), issued by thread 0.
+// The state stream is latency-bound: a block that waits on its own loads and
+// then on its L2 gathers keeps few HBM requests in flight, so the block about
+// one resident wave earlier asks for them.  Only whole 16-byte units inside
+// [q0, np) are prefetched (start aligned: q0 is a multiple of the block size,
+// the arrays 256-byte aligned); a prefetch changes no data and waits for
+// nothing.
+__device__ __forceinline__ void prefetch_state(const SpeciesDev& sd, int first, int ahead) {
+    const int q0 = first + ahead;
+    if (threadIdx.x != 0 || ahead <= 0 || q0 >= sd.np) return;
+    const unsigned cnt = (unsigned)min((int)blockDim.x, sd.np - q0);
+    const unsigned b4 = (cnt * 4u) & ~15u, b8 = (cnt * 8u) & ~15u;
+    const int cur = sd.cur;
+    if (b4) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.cell[cur] + q0), "r"(b4) : "memory");
+    if (b8) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.off[cur] + q0), "r"(b8) : "memory");
+    if (b8 && sd.inertial)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sd.vel[cur] + q0), "r"(b8) : "memory");
 }
 
 }  // namespace el
