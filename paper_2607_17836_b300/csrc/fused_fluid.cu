@@ -1183,6 +1183,21 @@ cudaError_t allow_smem() {
             e = cudaFuncSetAttribute(k_fused_nhat2k<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)k2NhatSmem);
     }
+    constexpr int cv = EL_SMEM_CARVEOUT_FLUID;
+    if (e == cudaSuccess) e = set_carveout(k_fused_advance<N, P, Src>, cv);
+    if constexpr (N <= 512) {
+        if (e == cudaSuccess) e = set_carveout(k_fusedg_columns<N, P, Src>, cv);
+        if (e == cudaSuccess) e = set_carveout(k_fusedg_rows<N, P, Src>, cv);
+        if (e == cudaSuccess) e = set_carveout(k_fusedg_nhat<N, Src>, cv);
+    } else if constexpr (N == 1024) {
+        if (e == cudaSuccess) e = set_carveout(k_fused_columns<P, Src>, cv);
+        if (e == cudaSuccess) e = set_carveout(k_fused_rows<P, Src>, cv);
+        if (e == cudaSuccess) e = set_carveout(k_fused_nhat<Src>, cv);
+    } else {
+        if (e == cudaSuccess) e = set_carveout(k_fused_columns2k<P, Src>, cv);
+        if (e == cudaSuccess) e = set_carveout(k_fused_rows2k<P, Src>, cv);
+        if (e == cudaSuccess) e = set_carveout(k_fused_nhat2k<Src>, cv);
+    }
     return e;
 }
 

@@ -124,13 +124,29 @@ static cudaError_t rk4_allow_smem() {
 
 // Launch attributes of the flow's particle kernels, set when the flow is
 // created (outside any stream capture) on its device.
+template <int SCHEME>
+static cudaError_t rk4_set_carveout() {
+    constexpr int cv = EL_SMEM_CARVEOUT_PARTICLES;
+    cudaError_t e = set_carveout(k_rk4<SCHEME, false, false>, cv);
+    if (e == cudaSuccess) e = set_carveout(k_rk4<SCHEME, true, false>, cv);
+    if constexpr (SCHEME == 1 || SCHEME == 2) {
+        if (e == cudaSuccess) e = set_carveout(k_rk4<SCHEME, false, true>, cv);
+        if (e == cudaSuccess) e = set_carveout(k_rk4<SCHEME, true, true>, cv);
+    }
+    return e;
+}
+
 el_status rk4_prepare(el_flow* f) {
     if (f->d.interp == EL_CATMULL_ROM) {
         EL_CUDA_OK(f, (rk4_allow_smem<1, false>()));
         EL_CUDA_OK(f, (rk4_allow_smem<1, true>()));
+        EL_CUDA_OK(f, rk4_set_carveout<1>());
     } else if (f->d.interp == EL_BSPLINE) {
         EL_CUDA_OK(f, (rk4_allow_smem<2, false>()));
         EL_CUDA_OK(f, (rk4_allow_smem<2, true>()));
+        EL_CUDA_OK(f, rk4_set_carveout<2>());
+    } else if (f->d.interp == EL_BILINEAR) {
+        EL_CUDA_OK(f, rk4_set_carveout<0>());
     }
     return EL_OK;
 }
