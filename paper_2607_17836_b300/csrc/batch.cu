@@ -456,7 +456,7 @@ el_status rebuild_tables(el_batch* b) {
         if (smem > 0)
             BT_CUDA(b, cudaFuncSetAttribute(rk_kernels[c], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)rk4_patch_bytes(true, 512)));
-        BT_CUDA(b, set_carveout(rk_kernels[c], EL_SMEM_CARVEOUT_PARTICLES));
+        BT_CUDA(b, set_carveout(rk_kernels[c], c < 2 ? EL_SMEM_CARVEOUT_BILINEAR : EL_SMEM_CARVEOUT_CUBIC));
         BT_CUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rk_kernels[c], rk_threads, smem));
         const int wave = std::max(1, occ) * b->sms;
         if (c == 0) b->grid_bilinear = (unsigned)wave;

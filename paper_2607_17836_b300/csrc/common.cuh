@@ -161,19 +161,24 @@ inline unsigned blocks_for(int64_t work, int threads) {
 el_status fail(el_flow* f, el_status s, const char* fmt, ...);
 
 // Preferred shared-memory carve-out (percent of the SM's unified L1 / shared
-// memory) of the particle kernels and of the fused fluid kernels, single-flow
-// and batched; -1 leaves it to the driver.  An SM changes its split only when
-// it is empty, so the fluid branch's blocks start beside running particle
-// blocks only where the particle kernel left a carve-out large enough for
-// them.  Single flow, 1024^2 with 4 x 1M bilinear particles, coupled step:
-// 75 / 75 (a 196 KB carve-out) 0.0745 ms against 0.0771 ms with the driver's
-// choice; 65 / 65 0.0756, 50 / 50 0.0757, 75 / 65 0.0765, 100 / 100 slower
-// (the particle kernel alone loses ~5 % at 75, from fewer L1 hits; the
-// overlap gains more).  Batched: the 64-member ensemble step unchanged
-// (0.889-0.893 ms), the overloaded served stream 1.46e10 -> 1.55e10
-// particle-steps/s; 50 / 50 slowed the ensemble to 0.976 ms.
-#ifndef EL_SMEM_CARVEOUT_PARTICLES
-#define EL_SMEM_CARVEOUT_PARTICLES 75
+// memory) of the particle kernels (bilinear; cubic schemes) and of the fused
+// fluid kernels, single-flow and batched; -1 leaves it to the driver.  An SM
+// changes its split only when it is empty, so the fluid branch's blocks start
+// beside running particle blocks only where the particle kernel left a
+// carve-out large enough for them.  Single flow, 1024^2 with 4 x 1M bilinear
+// particles, coupled step: 75 / 75 (a 196 KB carve-out) 0.0745 ms against
+// 0.0771 ms with the driver's choice; 65 / 65 0.0756, 50 / 50 0.0757, 75 / 65
+// 0.0765, 100 / 100 slower (the particle kernel alone loses ~5 % at 75, from
+// fewer L1 hits; the overlap gains more).  The cubic kernels lean on L1 for
+// their gathers: 2048^2 shear layer (16M Catmull-Rom, patch gather) particle
+// launch 0.383 ms with the driver's choice against 0.411 ms at 75, coupled
+// step 0.493-0.501 ms with only the fluid kernels at 75 against 0.521-0.530
+// with both.
+#ifndef EL_SMEM_CARVEOUT_BILINEAR
+#define EL_SMEM_CARVEOUT_BILINEAR 75
+#endif
+#ifndef EL_SMEM_CARVEOUT_CUBIC
+#define EL_SMEM_CARVEOUT_CUBIC -1
 #endif
 #ifndef EL_SMEM_CARVEOUT_FLUID
 #define EL_SMEM_CARVEOUT_FLUID 75

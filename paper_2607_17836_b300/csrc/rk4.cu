@@ -126,7 +126,7 @@ static cudaError_t rk4_allow_smem() {
 // created (outside any stream capture) on its device.
 template <int SCHEME>
 static cudaError_t rk4_set_carveout() {
-    constexpr int cv = EL_SMEM_CARVEOUT_PARTICLES;
+    constexpr int cv = SCHEME == 0 ? EL_SMEM_CARVEOUT_BILINEAR : EL_SMEM_CARVEOUT_CUBIC;
     cudaError_t e = set_carveout(k_rk4<SCHEME, false, false>, cv);
     if (e == cudaSuccess) e = set_carveout(k_rk4<SCHEME, true, false>, cv);
     if constexpr (SCHEME == 1 || SCHEME == 2) {
