@@ -304,11 +304,11 @@ el_status el_batch_add_fft_pool(el_batch* batch, const el_flow_desc* desc, int32
  * cuda_stream and the call returns without waiting.  Scratch: one fixed
  * device array of about 4 MiB inside the library, present on every GPU that
  * loads it until the process exits, shared by all calls: calls whose work
- * overlaps on the GPU race.  The first call on a device looks up the array's
- * device address with that device current and keeps it for the process;
- * make that first call before any stream capture, and do not call this
- * entry point after a cudaDeviceReset of that device (the reset unloads the
- * library's device array, and the kept address would be stale).
+ * overlaps on the GPU race.  Every call looks up the array's device address
+ * in the current device's context (nothing is kept across calls, so a call
+ * after a cudaDeviceReset finds the reloaded array); the call may be captured
+ * into a CUDA graph after a first plain call on that device (which loads the
+ * library's module).
  * Errors: el_last_error(NULL). */
 #define EL_NOALLOC_MAX_PARTICLES 262144
 el_status el_dispersion_noalloc(const double* d_xy, const double* d_xy0, int64_t np,

@@ -12,15 +12,15 @@
 // The scratch is a file-scope __device__ array: every GPU that loads the
 // library holds its kNoAllocScratchBytes (about 4 MiB) until the process
 // exits.  In host code the array's name is only a host-side handle, not a
-// device address; the device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// device address; the device address is looked up on every call with
+// cudaGetSymbolAddress (in the current device's context, so a context made
+// again after a cudaDeviceReset gets its own array's address; the lookup
+// allocates nothing) and passed to the kernels.
 // All calls share the array and it keeps the last call's contents: the box
 // counters are cleared at the start of every call, the other parts are fully
 // overwritten before they are read.  Calls whose work overlaps on the GPU
 // (different streams, no ordering between them) race on the array.
 #include "common.cuh"
-
-#include <mutex>
 
 namespace el {
 
@@ -39,27 +39,10 @@ constexpr size_t kNoAllocScratchBytes = kTermsBytes + kPartialBytes + kBoxBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up on
-// the first call per device and kept for the process: a cudaDeviceReset
-// unloads the array, so the entry point is not usable after one).
+// Device address of the scratch array in the current device's context.
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> g(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
-    return cudaSuccess;
+    *out = nullptr;
+    return cudaGetSymbolAddress(out, g_noalloc_scratch);
 }
 
 // Squared displacement per particle, unwrapped FP64 positions.

@@ -53,6 +53,29 @@ def test_noalloc_matches_get_stats_on_two_calls():
     g.close()
 
 
+def test_noalloc_replayed_from_a_captured_graph():
+    """Called inside a stream capture (torch's default, global mode), after a
+    first plain call: the graph's replay gives the plain call's bits (the
+    scratch address is looked up in the capturing context, nothing is
+    allocated)."""
+    g, counts, xys = _run_flow()
+    pos, _ = g.particles(0, counts[0])
+    g.close()
+    xy = torch.from_numpy(pos).cuda()
+    xy0 = torch.from_numpy(np.ascontiguousarray(xys[0])).cuda()
+    ref = elpath.dispersion_noalloc(xy, xy0).clone()
+    torch.cuda.synchronize()
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        elpath.dispersion_noalloc(xy, xy0, out=out)
+    for _ in range(2):
+        out.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+
+
 def test_noalloc_empty_set_gives_zeros():
     out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
     xy = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
