@@ -241,8 +241,9 @@ int32_t el_flow_fused(const el_flow* flow);
 /* ---- Batched engine --------------------------------------------------------
  * Many independent flows (any grid sizes, species mixes, schemes and step
  * counts) advanced together: one coupled step of the batch is one captured
- * graph with one persistent kernel per stage over all members and every
- * member's transforms on concurrent branches.  A member's arithmetic is the
+ * graph with one kernel per stage over all members (the fused fluid kernels
+ * once per grid size and plane count, the particle kernel once per scheme and
+ * stencil gather) and the other members' transforms on concurrent branches.  A member's arithmetic is the
  * same as when it is stepped alone.  While in a batch a flow uses the batch's
  * stream, el_step_coupled on it returns EL_ESTATE, and the other calls on it
  * (particles, statistics, fields) work as usual.  Members join and leave at

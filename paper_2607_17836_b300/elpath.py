@@ -357,7 +357,7 @@ class Flow:
 
 
 class Batch:
-    """el_batch: flows advanced together by one persistent kernel per stage."""
+    """el_batch: flows advanced together by one kernel per stage over all of them."""
 
     def __init__(self, max_members, stream=None, device=None):
         import torch

@@ -3,8 +3,8 @@
 Requests (a grid size, a particle species, an interpolation scheme and a
 step count; see ``inputs.served_requests``) arrive over time.  The server
 keeps every admitted simulation's fields and particles on the device and
-advances all of them together in one ``el_batch`` (one persistent kernel per
-stage).  Between batch ticks it
+advances all of them together in one ``el_batch`` (one kernel per stage over
+all of them).  Between batch ticks it
 
   * admits waiting requests while their device footprint
     (``el_workspace_bytes``) fits the HBM budget and a batch slot is free,
