@@ -926,6 +926,35 @@ def run_profile_ensemble(args):
         g.close()
 
 
+def run_profile_served(args):
+    """A fixed batch of the served stream's first 32 requests for ncu: their
+    flows as the server builds them, one FFT pool of 4 slots for the 128^2
+    members (as the server holds it), 3 steps, then 2 more.  The steps run
+    inside the NVTX range el_batch_step, so `ncu --nvtx --nvtx-include
+    "el_batch_step/"` captures only their kernels."""
+    import torch
+    from paper_2607_17836_b300 import elpath, serve
+    reqs = inputs.served_requests(count=32)
+    dev = torch.device("cuda:0")
+    batch = elpath.Batch(64)
+    batch.add_fft_pool(128, 4)
+    flows = [serve.build_flow(r, None, dev) for r in reqs]
+    for g in flows:
+        batch.add(g)
+    batch.step(3)
+    batch.synchronize()
+    batch.step(2)
+    batch.synchronize()
+    print(json.dumps({"members": len(flows), "steps": 5,
+                      "grids": {str(n): sum(1 for r in reqs if r.workload.n == n)
+                                for n in (128, 256, 512, 1024, 2048)},
+                      "schemes": {str(k): sum(1 for r in reqs if r.scheme == k) for k in (0, 1)},
+                      "particles": sum(r.workload.particles for r in reqs)}))
+    batch.close()
+    for g in flows:
+        g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -946,9 +975,10 @@ def main():
                     help="arrival rate (requests/s) of the sustained serving run")
     ap.add_argument("--overload-requests", type=int, default=200,
                     help="requests of the served stream run at its configured 20/s")
-    ap.add_argument("--profile-launch", choices=["mix", "16M", "shear", "ensemble"], default=None,
-                    help="only a fixed k_rk4 launch for ncu (see run_profile_launch), or the "
-                         "64-member ensemble's batched steps (run_profile_ensemble)")
+    ap.add_argument("--profile-launch", choices=["mix", "16M", "shear", "ensemble", "served"], default=None,
+                    help="only a fixed k_rk4 launch for ncu (see run_profile_launch), the "
+                         "64-member ensemble's batched steps (run_profile_ensemble), or a batch "
+                         "of the served stream's first 32 requests (run_profile_served)")
     ap.add_argument("--gather", choices=["auto", "registers", "shared"], default="auto",
                     help="stencil gather of the cubic schemes in --profile-launch")
     args = ap.parse_args()
@@ -965,6 +995,8 @@ def main():
         torch.cuda.set_device(local)
         if args.profile_launch == "ensemble":
             run_profile_ensemble(args)
+        elif args.profile_launch == "served":
+            run_profile_served(args)
         else:
             run_profile_launch(args, wl, scheme)
         return
