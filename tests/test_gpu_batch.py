@@ -182,3 +182,60 @@ def test_fused_members_equal_their_solo_runs_bit_for_bit():
         g.close()
     small_ref.close()
     batch.close()
+
+
+# (n, scheme, tracer_velocity, [(count, St)]): per species, at least 2
+# particles per cell takes the warp-shared stencil patch (automatic gather),
+# fewer the per-thread register stencils
+CLASS_SPECS = [
+    (64, 1, 0, [(20000, 1.0), (800, 0.0)]),    # Catmull-Rom: patch and registers in one member
+    (64, 2, 1, [(12000, 0.0), (9000, 10.0)]),  # B-spline, streamfunction tracers: patch
+    (32, 0, 0, [(3000, 0.1)]),                 # bilinear (persistent class)
+    (128, 2, 0, [(1500, 1.0)]),                # B-spline: registers
+]
+
+
+def make_class(spec, seed):
+    n, scheme, tv, species = spec
+    g = elpath.Flow(n, 1e-3, 1e-3 * 64 / n, inputs.decaying_turbulence(n, seed), interp=scheme,
+                    tracer_velocity=tv, max_species=len(species),
+                    max_particles=sum(c for c, _ in species), sort_every=5)
+    for k, (c, st) in enumerate(species):
+        g.set_particles(k, inputs.uniform_positions(c, seed * 10 + k), st)
+    return g
+
+
+def test_gather_classes_equal_their_solo_runs_bit_for_bit():
+    # The batched particle step launches once per (scheme, stencil gather)
+    # class present, each entry (a member's species) taking the gather its
+    # own density picks; a flow alone picks one gather for all its species by
+    # the densest.  Both gathers do the same arithmetic on the same values,
+    # so every member ends bit for bit as alone.
+    steps = 15
+    refs = []
+    for m, spec in enumerate(CLASS_SPECS):
+        g = make_class(spec, 70 + m)
+        g.step(steps)
+        refs.append([g.field(0)] + [a for k, (c, _) in enumerate(spec[3]) for a in g.particles(k, c)])
+        g.close()
+    batch = elpath.Batch(8)
+    flows = [make_class(spec, 70 + m) for m, spec in enumerate(CLASS_SPECS)]
+    for g in flows:
+        batch.add(g)
+    batch.step(steps)
+    for g, spec, ref in zip(flows, CLASS_SPECS, refs):
+        got = [g.field(0)] + [a for k, (c, _) in enumerate(spec[3]) for a in g.particles(k, c)]
+        for x, y in zip(got, ref):
+            np.testing.assert_array_equal(x, y)
+    # classes present: bilinear, Catmull-Rom registers and patch, B-spline
+    # registers and patch (5 particle launches); the fluid step: the 64^2 and
+    # 32^2 and 128^2 members on the batched spectral / cuFFT / nonlinear
+    # stages (not fused grids); the step counters
+    l0 = batch.kernel_launches()
+    batch.step(2)
+    per_step = (batch.kernel_launches() - l0) / 2
+    assert per_step == 5 + 2 + 1
+    for g in flows:
+        batch.remove(g)
+        g.close()
+    batch.close()
