@@ -230,7 +230,7 @@ enum { kFluidStep = 0, kParticleStep = 1, kOverlapStep = 2 };
 
 el_status enqueue_step(el_flow* f, int kind, int64_t step) {
     if (kind == kFluidStep) return fluid_step(f, step);
-    if (kind == kParticleStep) return particles_step_all(f, step);
+    if (kind == kParticleStep) return particles_step_all(f, step, false);
     EL_CUDA_OK(f, cudaEventRecord(f->ev_fork, f->stream));
     EL_CUDA_OK(f, cudaStreamWaitEvent(f->side, f->ev_fork, 0));
     cudaStream_t main = f->stream;
@@ -238,7 +238,7 @@ el_status enqueue_step(el_flow* f, int kind, int64_t step) {
     // The fluid chain (several short kernels) goes on the high-priority side
     // branch, so its blocks are dispatched as soon as the particle kernel's
     // blocks free an SM instead of after the particle kernel.
-    EL_TRY(particles_step_all(f, step));
+    EL_TRY(particles_step_all(f, step, true));
     f->stream = f->side;
     cufftSetStream(f->plan_c2r, f->side);
     cufftSetStream(f->plan_r2c, f->side);
@@ -249,7 +249,7 @@ el_status enqueue_step(el_flow* f, int kind, int64_t step) {
     EL_TRY(s);
 #else
     f->stream = f->side;
-    el_status s = particles_step_all(f, step);
+    el_status s = particles_step_all(f, step, true);
     f->stream = main;
     EL_TRY(s);
     EL_TRY(fluid_step(f, step + 1));
@@ -693,7 +693,8 @@ el_status el_profile_step(el_flow* f, double* stage_ms, int32_t nstage) {
     cudaEventRecord(ev[1], f->stream);
     if (st == EL_OK) st = fluid_step(f, f->step);
     cudaEventRecord(ev[2], f->stream);
-    if (st == EL_OK) st = particles_step_all(f, f->step);
+    // the particle kernel the overlapped step runs (its carve-out variant)
+    if (st == EL_OK) st = particles_step_all(f, f->step, true);
     cudaEventRecord(ev[3], f->stream);
     cudaError_t e = cudaStreamSynchronize(f->stream);
     if (st == EL_OK && e != cudaSuccess) st = fail(f, EL_ECUDA, "profile: %s", cudaGetErrorString(e));

@@ -244,7 +244,7 @@ int flow_planes(const el_flow_desc& d);                // spectral planes of the
 // ---- particles (particles.cu; the RK4 step in rk4.cu) ----------------------------
 el_status particles_set(el_flow* f, int s, int64_t np, double st, const double* xy,
                         const double* vxy);
-el_status particles_step_all(el_flow* f, int64_t step);  // K6 (rk4.cu), every species in one launch
+el_status particles_step_all(el_flow* f, int64_t step, bool beside);  // K6 (rk4.cu), every species in one launch
 // K6 with the warp-shared stencil patch?  For scheme `interp` under setting
 // `gather`, with `density` = the largest particles-per-cell of a species (rk4.cu).
 bool rk4_shared_gather(int interp, int gather, double density);

@@ -64,7 +64,13 @@ __device__ __forceinline__ int species_of(const unsigned (&begin)[kMaxSpecies], 
 // SHARED (cubic schemes only): the warp-shared stencil patch (PatchStencil)
 // instead of each thread's register copy of its cell's stencil; the same
 // arithmetic on the same values, so the same bits.
-template <int SCHEME, bool PSI, bool SHARED>
+//
+// BESIDE (bilinear only): the instantiation launched beside the fluid branch
+// of the overlapped step, which carries the bilinear carve-out preference
+// (EL_SMEM_CARVEOUT_BILINEAR); the particle-only step (a single step, the
+// last step of a call) launches the other, which keeps the driver's choice
+// and with it the larger L1.  The same code, so the same bits.
+template <int SCHEME, bool PSI, bool SHARED, bool BESIDE = false>
 __global__ void __launch_bounds__(kRK4MaxThreads, SCHEME == 0 ? EL_RK4_BILINEAR_MIN_BLOCKS : EL_RK4_CUBIC_MIN_BLOCKS)
     __maxnreg__(SHARED ? EL_RK4_SHARED_MAXNREG : (SCHEME == 1 || SCHEME == 2 ? EL_RK4_CUBIC_MAXNREG : 128))
     k_rk4(const __grid_constant__ RK4Args a) {
@@ -126,7 +132,13 @@ static cudaError_t rk4_allow_smem() {
 // created (outside any stream capture) on its device.
 template <int SCHEME>
 static cudaError_t rk4_set_carveout() {
-    constexpr int cv = SCHEME == 0 ? EL_SMEM_CARVEOUT_BILINEAR : EL_SMEM_CARVEOUT_CUBIC;
+    if constexpr (SCHEME == 0) {
+        constexpr int cv = EL_SMEM_CARVEOUT_BILINEAR;
+        cudaError_t e = set_carveout(k_rk4<0, false, false, true>, cv);
+        if (e == cudaSuccess) e = set_carveout(k_rk4<0, true, false, true>, cv);
+        return e;
+    }
+    constexpr int cv = EL_SMEM_CARVEOUT_CUBIC;
     cudaError_t e = set_carveout(k_rk4<SCHEME, false, false>, cv);
     if (e == cudaSuccess) e = set_carveout(k_rk4<SCHEME, true, false>, cv);
     if constexpr (SCHEME == 1 || SCHEME == 2) {
@@ -191,8 +203,9 @@ static int rk4_prefetch_distance(el_flow* f, bool shared) {
 }
 
 // K6 for every species of the flow in one launch, step number `step`
-// (levels step and step + 1: pair snap[step % 2]).
-el_status particles_step_all(el_flow* f, int64_t step) {
+// (levels step and step + 1: pair snap[step % 2]); `beside`: launched beside
+// the fluid branch (the bilinear kernel's carve-out variant).
+el_status particles_step_all(el_flow* f, int64_t step, bool beside) {
     NvtxRange range("particles_step");
     RK4Args a{};
     a.snap = f->snap[step % 2];
@@ -229,8 +242,13 @@ el_status particles_step_all(el_flow* f, int64_t step) {
         a.kin = kinematic_stage_args(f, step);
         k_rk4<3, false, false><<<blocks, T, 0, st>>>(a);
     } else if (f->d.interp == EL_BILINEAR) {
-        if (psi) k_rk4<0, true, false><<<blocks, T, 0, st>>>(a);
-        else k_rk4<0, false, false><<<blocks, T, 0, st>>>(a);
+        if (beside) {
+            if (psi) k_rk4<0, true, false, true><<<blocks, T, 0, st>>>(a);
+            else k_rk4<0, false, false, true><<<blocks, T, 0, st>>>(a);
+        } else {
+            if (psi) k_rk4<0, true, false><<<blocks, T, 0, st>>>(a);
+            else k_rk4<0, false, false><<<blocks, T, 0, st>>>(a);
+        }
     } else if (f->d.interp == EL_CATMULL_ROM) {
         if (shared) {
             if (psi) k_rk4<1, true, true><<<blocks, T, smem, st>>>(a);
