@@ -119,10 +119,9 @@ __global__ void __launch_bounds__(kBNlThreads) k_batch_nonlinear(const __grid_co
     }
 }
 
-// One kernel per interpolation scheme (each with its own register budget);
-// the entries of the other schemes are skipped.
+// K6 for task t (a run of one entry's particles) of class c = 2 SCHEME +
+// SHARED; the class's entries are [rk_class_entry[c], rk_class_entry[c + 1]).
 // SHARED: the warp-shared stencil patch of the cubic schemes (as k_rk4).
-// K6 for task t (a run of one entry's particles) of class c = 2 SCHEME + SHARED.
 template <int SCHEME, bool SHARED>
 __device__ __forceinline__ void batch_rk4_task(const BatchArgs& b, int c, int t, int prefetch) {
     const int e0 = b.rk_class_entry[c];
