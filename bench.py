@@ -870,9 +870,12 @@ def run_profile_launch(args, wl, scheme):
     128-thread blocks, re-binning every 20 steps in single cells,
     the stencil gather of --gather (default: automatic); 21 steps (re-binned at step 20), then three
     steps with per-stage CUDA events.  `ncu -k regex:k_rk4 -s 21 -c 1`
-    captures the first of those three particle launches."""
+    captures the first of those three particle launches.  "batch16M": the
+    16M flow alone in a batch (el_batch), 21 batched steps, then 3 more;
+    `ncu -k regex:k_batch_rk4 -s 21 -c 1` captures the batched kernel at
+    the same point."""
     from paper_2607_17836_b300 import elpath
-    if args.profile_launch == "16M":
+    if args.profile_launch in ("16M", "batch16M"):
         species = [(16_000_000, 1.0, 99)]
     elif args.profile_launch == "shear":  # the 2048^2 shear layer, 16M at St = 1
         wl = inputs.kelvin_helmholtz_2048()
@@ -886,6 +889,17 @@ def run_profile_launch(args, wl, scheme):
     gather = {"auto": elpath.GATHER_AUTO, "registers": elpath.GATHER_REGISTERS,
               "shared": elpath.GATHER_SHARED}[args.gather]
     g.set_tuning(128, SORT_EVERY, 0, gather)
+    if args.profile_launch == "batch16M":
+        batch = elpath.Batch(2)
+        batch.add(g)
+        batch.step(21)
+        batch.step(3)
+        batch.synchronize()
+        print(json.dumps({"batched_steps": 24, "particles": sum(c for c, _, _ in species)}), flush=True)
+        batch.remove(g)
+        batch.close()
+        g.close()
+        return
     g.step(21)
     for _ in range(3):
         print(json.dumps(g.profile_step()), flush=True)
@@ -975,7 +989,7 @@ def main():
                     help="arrival rate (requests/s) of the sustained serving run")
     ap.add_argument("--overload-requests", type=int, default=200,
                     help="requests of the served stream run at its configured 20/s")
-    ap.add_argument("--profile-launch", choices=["mix", "16M", "shear", "ensemble", "served"], default=None,
+    ap.add_argument("--profile-launch", choices=["mix", "16M", "batch16M", "shear", "ensemble", "served"], default=None,
                     help="only a fixed k_rk4 launch for ncu (see run_profile_launch), the "
                          "64-member ensemble's batched steps (run_profile_ensemble), or a batch "
                          "of the served stream's first 32 requests (run_profile_served)")
