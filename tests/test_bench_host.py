@@ -44,3 +44,27 @@ def test_oracle_timing_of_the_taylor_green_case_in_full():
     assert t["seconds"] > 0 and t["cores"] >= 1
     assert t["particle_steps_per_s"] == pytest.approx(4096 * 200 / t["seconds"])
     assert t["fluid_steps_per_s"] > t["particle_steps_per_s"] / 4096
+
+
+def test_profile_commands_name_existing_bench_modes():
+    """Every `bench.py --profile-launch X` (and `--scheme`, `--gather`) that
+    a committed ncu summary cites is one the benchmark still accepts, so the
+    summaries' commands stay runnable."""
+    import re
+    src = open(os.path.join(os.path.dirname(bench.__file__), "bench.py")).read()
+    modes = set(re.search(r'"--profile-launch", choices=\[([^\]]*)\]', src).group(1).replace('"', "").replace(" ", "").split(","))
+    gathers = set(re.search(r'"--gather", choices=\[([^\]]*)\]', src).group(1).replace('"', "").replace(" ", "").split(","))
+    prof = os.path.join(os.path.dirname(bench.__file__), "profiles")
+    cited = 0
+    for name in sorted(os.listdir(prof)):
+        text = open(os.path.join(prof, name)).read().replace("\\\n", " ")
+        for m in re.finditer(r"bench\.py([^\n]*)", text):
+            args = m.group(1)
+            for mode in re.findall(r"--profile-launch (\S+)", args):
+                assert mode in modes, (name, mode)
+                cited += 1
+            for scheme in re.findall(r"--scheme (\S+)", args):
+                assert scheme in bench.SCHEMES, (name, scheme)
+            for gather in re.findall(r"--gather (\S+)", args):
+                assert gather in gathers, (name, gather)
+    assert cited >= 5
